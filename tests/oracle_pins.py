@@ -1,0 +1,294 @@
+"""Pins for the CPU oracle: checks against what the paper and the mathematics
+fix, independent of the oracle's own code.
+
+Every pin is a function ``pin(L)`` taking a loaded oracle library and raising
+AssertionError when the library disagrees.  ``test_oracle_pins.py`` runs them
+on the real oracle; ``test_oracle_mutants.py`` runs them on copies of the
+oracle with one plausible mistake planted each, and requires every mistake to
+be caught by at least one pin.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import oracle
+from paper_2208_08795_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+INIT = np.float32(1e10)  # Algorithm 1's initial distance
+
+
+# --------------------------------------------------------------------------
+# independent helpers (no code shared with the oracle)
+# --------------------------------------------------------------------------
+def sectors(N, C, M):
+    """Reading of Sec. III-B: storage-order sectors, floor boundaries."""
+    lo = [(s * N) // M for s in range(M + 1)]
+    off = [(s * C) // M for s in range(M + 1)]
+    return lo, off
+
+
+def sqdist32(P, j, q):
+    """fp32 squared distances from points j (array) to point q, each product
+    and sum rounded on its own: (dx*dx + dy*dy) + dz*dz."""
+    d = P[j] - P[q]
+    dx, dy, dz = d[..., 0], d[..., 1], d[..., 2]
+    return (dx * dx + dy * dy) + dz * dz
+
+
+def brute_force(P, C, M, k, start):
+    """From-scratch restatement: at every step, each point's distance is the
+    minimum over the 1e10 of Algorithm 1 and its distances to the earlier
+    samples of its sector whose update reached it (the whole sector without
+    NPDU, the window [p - k//2, p + k - k//2] with it).  No running array is
+    kept; the next sample is the lowest-index maximum."""
+    P = np.asarray(P, dtype=np.float32)
+    N = P.shape[0]
+    lo, off = sectors(N, C, M)
+    s0 = max(s for s in range(M) if lo[s] <= start)
+    r = start - lo[s0]
+    out = []
+    for s in range(M):
+        n, c = lo[s + 1] - lo[s], off[s + 1] - off[s]
+        Q = P[lo[s]:lo[s + 1]]
+        sel = [min(r, n - 1)]
+        while len(sel) < c:
+            D = np.full(n, INIT, dtype=np.float32)
+            for p in sel:
+                js = np.arange(n)
+                if k > 0:
+                    js = js[(js >= p - k // 2) & (js <= p + (k - k // 2))]
+                D[js] = np.minimum(D[js], sqdist32(Q, js, p))
+            sel.append(int(np.argmax(D)))  # first maximum = lowest index
+        out += [lo[s] + p for p in sel]
+    return np.array(out, dtype=np.int32)
+
+
+def grid_closed_form(m):
+    """FPS order on x = 0..2^m from 0: 0, 2^m, then for each level l the odd
+    multiples of 2^(m-l) in ascending order (all tie at that level)."""
+    seq = [0, 1 << m]
+    for l in range(1, m + 1):
+        step = 1 << (m - l)
+        seq += list(range(step, 1 << m, 2 * step))
+    return seq
+
+
+def read_golden(name):
+    fields = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, _, rest = line.partition(" ")
+            fields[key] = rest.split()
+    N = int(fields["N"][0])
+    if fields["points"] == ["grid1d"]:
+        P = np.zeros((N, 3), dtype=np.float32)
+        P[:, 0] = np.arange(N)
+    else:
+        P = np.array([float(v) for v in fields["points"]], dtype=np.float32).reshape(N, 3)
+    args = {key: int(fields[key][0]) for key in ("C", "M", "k", "start")}
+    expect = np.array([int(v) for v in fields["expect"]], dtype=np.int32)
+    return P, args, expect
+
+
+GOLDEN_FILES = sorted(f for f in os.listdir(GOLDEN) if f.endswith(".txt"))
+
+
+# --------------------------------------------------------------------------
+# pins
+# --------------------------------------------------------------------------
+def pin_golden(L):
+    """Hand-worked examples of Algorithm 1 / Sec. III-B / III-C."""
+    for name in GOLDEN_FILES:
+        P, a, expect = read_golden(name)
+        for prec in ("f32", "f64"):
+            got = oracle.afps(P, a["C"], a["M"], a["k"], a["start"], precision=prec, library=L)
+            assert np.array_equal(got, expect), (name, prec, got, expect)
+
+
+def pin_grid_closed_form(L):
+    """Closed form of FPS on a 1-D integer grid, along each axis in turn;
+    squared distances are exact integers, so fp32 and fp64 agree exactly."""
+    for m in range(1, 9):
+        expect = np.array(grid_closed_form(m), dtype=np.int32)
+        for axis in range(3):
+            P = np.zeros(((1 << m) + 1, 3), dtype=np.float32)
+            P[:, axis] = np.arange(P.shape[0])
+            for prec in ("f32", "f64"):
+                got = oracle.afps(P, P.shape[0], 1, 0, 0, precision=prec, library=L)
+                assert np.array_equal(got, expect), (m, axis, prec)
+
+
+def pin_npdu_stride_law(L):
+    """Under NPDU read literally (no first full pass), untouched points keep
+    1e10 and the lowest one wins, so from start 0 a sector's first
+    ceil(n/(r+1)) samples are 0, r+1, 2(r+1), ... with r = k - k//2."""
+    P = synth.uniform_cloud(11, 256)
+    for k in (1, 2, 4, 8, 9, 16, 31):
+        for M in (1, 4):
+            n = 256 // M
+            r = k - k // 2
+            head = -(-n // (r + 1))
+            C = M * n  # sample every point
+            got = oracle.afps(P, C, M, k, 0, library=L)
+            for s in range(M):
+                seg = got[s * n: s * n + head] - s * n
+                assert np.array_equal(seg, np.arange(head) * (r + 1)), (k, M, s)
+
+
+def pin_brute_force(L):
+    """The oracle equals the from-scratch restatement on tiny clouds."""
+    cases = [(17, 17, 1, 0, 0), (40, 20, 1, 0, 5), (40, 20, 4, 0, 0), (48, 24, 3, 4, 7),
+             (64, 32, 2, 8, 0), (64, 64, 4, 2, 63), (33, 11, 5, 1, 12), (50, 30, 1, 3, 49)]
+    for i, (N, C, M, k, start) in enumerate(cases):
+        for axis in (0, None):
+            P = synth.uniform_cloud(100 + i, N, axis)
+            got = oracle.afps(P, C, M, k, start, library=L)
+            ref = brute_force(P, C, M, k, start)
+            assert np.array_equal(got, ref), (N, C, M, k, start, axis)
+
+
+def pin_brute_force_f64(L):
+    """fp64 route: on coordinates that are multiples of 1/4 below 16 every
+    squared distance is exact in both fp32 and fp64, so both routes must
+    equal the brute force exactly (odd and even NPDU windows included)."""
+    g = np.random.Generator(np.random.PCG64(7))
+    for i in range(4):
+        P = (g.integers(0, 64, (48, 3)) / 4.0).astype(np.float32)
+        P = P[np.unique(P, axis=0, return_index=True)[1]]
+        P = P[np.argsort(P[:, 0], kind="stable")]
+        for (M, k) in ((1, 0), (3, 0), (2, 4), (2, 3), (1, 5)):
+            C = 3 * (P.shape[0] // 4) // M * M
+            a = oracle.afps(P, C, M, k, 0, precision="f32", library=L)
+            b = oracle.afps(P, C, M, k, 0, precision="f64", library=L)
+            ref = brute_force(P, C, M, k, 0)
+            assert np.array_equal(a, ref) and np.array_equal(b, ref), (i, M, k)
+
+
+def pin_reductions(L):
+    """Special cases of Sec. III-B/C: a window of 2n covers the whole sector
+    (NPDU = AFPS); M = C gives exactly the sector starts ("equivalent to
+    RPS"); AFPS is FPS run on each sector's sub-cloud on its own."""
+    P = synth.uniform_cloud(21, 300)
+    for M in (1, 3, 7):
+        lo, off = sectors(300, 90, M)
+        full = oracle.afps(P, 90, M, 0, 0, library=L)
+        n_max = max(lo[s + 1] - lo[s] for s in range(M))
+        assert np.array_equal(oracle.afps(P, 90, M, 2 * n_max, 0, library=L), full)
+        for s in range(M):
+            sub = oracle.afps(P[lo[s]:lo[s + 1]], off[s + 1] - off[s], 1, 0, 0, library=L)
+            assert np.array_equal(full[off[s]:off[s + 1]], sub + lo[s]), (M, s)
+    for start in (0, 5, 299):
+        got = oracle.afps(P, 60, 60, 0, start, library=L)
+        lo, _ = sectors(300, 60, 60)
+        r = start - lo[start * 60 // 300]
+        starts = [lo[s] + min(r, lo[s + 1] - lo[s] - 1) for s in range(60)]
+        assert np.array_equal(got, np.array(starts)), start
+        lo_t, off_t, first_t = oracle.sector_table(300, 60, 60, start, library=L)
+        assert list(lo_t) == lo and list(first_t) == starts
+    # unequal sectors: N = 10, M = 3 gives sizes 3, 3, 4; start 9 is offset 3
+    # of the last sector, which the smaller sectors clip to their last point
+    Q = synth.uniform_cloud(22, 10)
+    assert list(oracle.sector_table(10, 3, 3, 9, library=L)[2]) == [2, 5, 9]
+    assert list(oracle.afps(Q, 3, 3, 0, 9, library=L)) == [2, 5, 9]
+
+
+def pin_invariants(L):
+    """Distinct samples inside their own sectors, c_s per sector, and every
+    non-NPDU sample is the lowest-index argmax of the fp32 distance to the
+    earlier samples of its sector; the selected distances never increase."""
+    for seed, (N, C, M) in enumerate([(512, 128, 1), (1000, 250, 4), (777, 300, 13)]):
+        P = synth.uniform_cloud(300 + seed, N)
+        got = oracle.afps(P, C, M, 0, 0, library=L)
+        lo, off = sectors(N, C, M)
+        assert len(set(got.tolist())) == C
+        for s in range(M):
+            seg = got[off[s]:off[s + 1]]
+            assert ((seg >= lo[s]) & (seg < lo[s + 1])).all()
+            Q = P[lo[s]:lo[s + 1]]
+            loc = seg - lo[s]
+            D = np.full(Q.shape[0], INIT, dtype=np.float32)
+            prev = np.inf
+            for t in range(1, len(loc)):
+                D = np.minimum(D, sqdist32(Q, np.arange(Q.shape[0]), loc[t - 1]))
+                assert int(np.argmax(D)) == loc[t], (seed, s, t)
+                assert D[loc[t]] <= prev
+                prev = D[loc[t]]
+
+
+def pin_every_point(L):
+    """C = N samples every point exactly once, each sector exactly its own
+    points, for any M (also when M does not divide N)."""
+    for (N, M, k) in ((7, 3, 0), (100, 7, 0), (100, 7, 4), (64, 5, 3)):
+        P = synth.uniform_cloud(60 + N + M, N)
+        got = oracle.afps(P, N, M, k, 0, library=L)
+        assert np.array_equal(np.sort(got), np.arange(N)), (N, M, k)
+        lo, off = sectors(N, N, M)
+        for s in range(M):
+            assert np.array_equal(np.sort(got[off[s]:off[s + 1]]), np.arange(lo[s], lo[s + 1]))
+
+
+def pin_metamorphic(L):
+    """Exact symmetries of the fp32 arithmetic: scaling by a power of two,
+    negating a coordinate, swapping x and y leave every index unchanged."""
+    P = synth.uniform_cloud(41, 400)
+    for (C, M, k) in ((100, 1, 0), (100, 4, 0), (120, 8, 8)):
+        base = oracle.afps(P, C, M, k, 3, library=L)
+        variants = [P * np.float32(8.0), P * np.float32(0.125)]
+        for ax in range(3):
+            Q = P.copy()
+            Q[:, ax] = -Q[:, ax]
+            variants.append(Q)
+        variants.append(P[:, [1, 0, 2]])
+        for V in variants:
+            got = oracle.afps(np.ascontiguousarray(V), C, M, k, 3, library=L)
+            assert np.array_equal(got, base), (C, M, k)
+
+
+def pin_errors(L):
+    """Argument checks: bad sizes, bad start, and a sector with more samples
+    than points (N = 8, C = 7, M = 5 gives sector 2 one point, two samples)."""
+    P = synth.uniform_cloud(1, 8)
+    bad = [(0, 1, 0, 0), (9, 1, 0, 0), (4, 5, 0, 0), (4, 0, 0, 0), (4, 2, -1, 0),
+           (4, 2, 0, 8), (4, 2, 0, -1)]
+    for (C, M, k, start) in bad:
+        try:
+            oracle.afps(P, C, M, k, start, library=L)
+        except oracle.OracleError as e:
+            assert e.code == oracle.ERR_INVALID_ARG
+        else:
+            raise AssertionError(("accepted", C, M, k, start))
+    try:
+        oracle.afps(P, 7, 5, 0, 0, library=L)
+    except oracle.OracleError as e:
+        assert e.code == oracle.ERR_SECTOR_TOO_SMALL
+    else:
+        raise AssertionError("sector too small accepted")
+
+
+def pin_coverage_radius(L):
+    """Coverage radius: closed form on the grid (after a full FPS level l on
+    x = 0..2^m the radius is 2^(m-l-1)) and numpy brute force on a cloud."""
+    m = 6
+    P = synth.grid_1d(m)
+    seq = grid_closed_form(m)
+    for l in range(0, m):
+        C = (1 << l) + 1
+        r = oracle.coverage_radius(P, np.array(seq[:C]), library=L)
+        assert r == 2.0 ** (m - l - 1), (l, r)
+    Q = synth.uniform_cloud(5, 300).astype(np.float64)
+    idx = np.array([0, 17, 99, 150, 299])
+    d = ((Q[:, None, :] - Q[None, idx, :]) ** 2).sum(-1)
+    ref = float(np.sqrt(d.min(axis=1).max()))
+    got = oracle.coverage_radius(Q.astype(np.float32), idx, library=L)
+    assert abs(got - ref) <= 1e-12 * ref, (got, ref)
+
+
+PINS = [pin_golden, pin_grid_closed_form, pin_npdu_stride_law, pin_brute_force,
+        pin_brute_force_f64, pin_reductions, pin_invariants, pin_every_point, pin_metamorphic,
+        pin_errors, pin_coverage_radius]
