@@ -1,0 +1,423 @@
+"""Benchmark: NPDU-AFPS vs plain FPS on one GB300, clouds/s and p99 ms.
+
+Workload (one step): a batch of 32 object-scale clouds of 2048 points
+(2-5 primitive surfaces, jitter 0.005, unit ball, sorted by x), C = 512
+samples each, NPDU-AFPS with M = 32 sectors and window k = 16, all clouds in
+one batched call (graph-replayed).  Beside it, in the same run: plain FPS
+(M = 1, no NPDU) on the same batch, the sweep M in {1, 4, 16, 32} with NPDU
+off/on, the end-to-end time through host buffers, the roofline of the
+sampling kernel, and the CPU oracle on the host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank samples its own
+batch (weak scaling, no collective on the data path); the time is the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "clouds/s & p99 ms, NPDU-AFPS vs plain FPS on 1 GB300, indices = FP32 oracle"
+UNIT = "clouds/s"
+B_CLOUDS, N_POINTS, C_SAMPLES, M_SECTORS, K_WINDOW = 32, 2048, 512, 32, 16
+WORKLOAD = (f"object batch {B_CLOUDS} x {N_POINTS} pts, C={C_SAMPLES}, "
+            f"NPDU-AFPS M={M_SECTORS} k={K_WINDOW}")
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def k_rule(M: int) -> int:
+    """NPDU window per sector count: k = 8 for M <= 8, 16 for M >= 16."""
+    return 8 if M <= 8 else 16
+
+
+# ------------------------------------------------------------------ ranks
+def rank_info():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+def batch_seed(rank: int) -> int:
+    """Each rank samples its own batch (weak scaling)."""
+    return 1 + rank
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampled every 50 ms while the benchmark runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(", ") for l in self.file.read().splitlines() if l.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ inputs
+def make_batch(seed: int):
+    from paper_2208_08795_gb300 import synth
+    clouds = synth.object_batch(seed, B_CLOUDS, N_POINTS)
+    xyz, off = synth.pack(clouds)
+    return clouds, xyz, off
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_batch(clouds, C, M, k, threads):
+    import oracle
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(lambda P: oracle.afps(P, C, M, k, 0), clouds))
+
+
+def time_oracle(clouds, C, M, k, budget_s: float, threads: int):
+    """The oracle as it stands, threads over clouds (ctypes releases the GIL),
+    repeated over whole batches until about budget_s of CPU time."""
+    outs = oracle_batch(clouds, C, M, k, threads)  # also warms the library
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle_batch(clouds, C, M, k, threads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 1000:
+            break
+    return reps * len(clouds) / el, reps, outs
+
+
+def cpu_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ GPU timing
+def time_device(sampler, x, ba, out, steps: int, warmup: int, flush):
+    """Per-step device time with CUDA events on the launching stream.  Each
+    step is preceded (outside its events) by a 256 MB write that flushes L2
+    and keeps the GPU busy while the host enqueues the step."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        sampler.sample_batched(x, ba, out=out, stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    n0 = sampler.launch_count
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        sampler.sample_batched(x, ba, out=out, stream=stream)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    sampler.sync()
+    return [a.elapsed_time(b) for a, b in evs], sampler.launch_count - n0
+
+
+def time_e2e(sampler, h_xyz, ba, h_out, steps: int, warmup: int):
+    """Host buffers in, host indices out, copies inside each timed call."""
+    for _ in range(warmup):
+        sampler.sample_batched_host(h_xyz, ba, h_out)
+    ts = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        sampler.sample_batched_host(h_xyz, ba, h_out)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return ts
+
+
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs), q))
+
+
+def npdu_work(out_idx, ba, k):
+    """Algorithmic work of one batch: distance evaluations (window sizes, or
+    whole sectors) and argmax compares, from the sector plan and the output."""
+    evals = compares = 0
+    for b in range(ba.B):
+        N = int(ba.pt_off[b + 1] - ba.pt_off[b])
+        C, M = int(ba.C[b]), int(ba.M[b])
+        idx = out_idx[ba.out_off[b]:ba.out_off[b] + C]
+        for s in range(M):
+            lo, hi = s * N // M, (s + 1) * N // M
+            o0, o1 = s * C // M, (s + 1) * C // M
+            n = hi - lo
+            compares += (o1 - o0 - 1) * n
+            for p in idx[o0:o1 - 1] - lo:
+                if k > 0:
+                    evals += min(n - 1, p + (k - k // 2)) - max(0, p - k // 2) + 1
+                else:
+                    evals += n
+    return evals, compares
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2208_08795_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM traffic of the headline kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch), valid only for the kernel sources it was
+# taken on (their hash); otherwise reported as null.
+NCU_TRAFFIC = {"source_hash": None, "bytes_per_launch": None}
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, rank: int, world: int) -> int:
+    """The oracle, as it stands, on the host cores: the reference arm."""
+    if rank != 0:
+        return 0
+    clouds, _, _ = make_batch(batch_seed(0))
+    threads = cpu_threads()
+    for _ in range(args.warmup):
+        oracle_batch(clouds, C_SAMPLES, M_SECTORS, K_WINDOW, threads)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_batch(clouds, C_SAMPLES, M_SECTORS, K_WINDOW, threads)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    ms = float(np.mean(ts))
+    value = B_CLOUDS / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "p99_ms": pct(ts, 99),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "clouds": B_CLOUDS, "N": N_POINTS, "C": C_SAMPLES,
+                   "M": M_SECTORS, "k": K_WINDOW, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} whole batches of {B_CLOUDS} clouds, "
+                                   f"threads over clouds"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args, rank: int, world: int, local: int) -> int:
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2208_08795_gb300 import afps as A
+    from paper_2208_08795_gb300 import build as build_mod
+    if local == 0:
+        build_mod.build()
+    if world > 1:
+        torch.distributed.barrier()
+
+    clouds, xyz, off = make_batch(batch_seed(rank))
+    sampler = A.Sampler(local, graph=True)
+    x = torch.from_numpy(xyz).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    def run(M, k, steps, warmup):
+        ba = A.BatchArgs(off, C_SAMPLES, M, k, 0)
+        out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
+        barrier()
+        ms, launches = time_device(sampler, x, ba, out, steps, warmup, flush)
+        barrier()
+        return ba, out, ms, launches
+
+    # headline: NPDU-AFPS M=32 k=16
+    ba, out, ms, launches = run(M_SECTORS, K_WINDOW, args.steps, args.warmup)
+    ms_step = max_over_ranks(float(np.mean(ms)), world, dev)
+    p99 = max_over_ranks(pct(ms, 99), world, dev)
+    p50 = max_over_ranks(pct(ms, 50), world, dev)
+    value = B_CLOUDS * world / (ms_step / 1e3)
+    head_out = out.cpu().numpy()
+
+    # plain FPS on the same batch, same protocol
+    _, _, ms_f, _ = run(1, 0, args.steps, args.warmup)
+    ms_fps = max_over_ranks(float(np.mean(ms_f)), world, dev)
+    fps_value = B_CLOUDS * world / (ms_fps / 1e3)
+
+    # sweep of the paper's M values, NPDU off / on
+    sweep = {}
+    sw_steps = max(3, min(args.steps, 50))
+    for M in (1, 4, 16, 32):
+        for npdu in (False, True):
+            k = k_rule(M) if npdu else 0
+            _, _, ms_s, _ = run(M, k, sw_steps, max(3, args.warmup // 2))
+            m = max_over_ranks(float(np.mean(ms_s)), world, dev)
+            sweep[f"M{M}_{'npdu' if npdu else 'full'}"] = round(B_CLOUDS * world / (m / 1e3), 1)
+
+    # end to end through host buffers
+    h_xyz = torch.from_numpy(xyz).pin_memory().numpy()
+    h_out = torch.empty(ba.total_out, dtype=torch.int32).pin_memory().numpy()
+    barrier()
+    ts = time_e2e(sampler, h_xyz, ba, h_out, args.steps, args.warmup)
+    barrier()
+    e2e_ms = max_over_ranks(float(np.mean(ts)), world, dev)
+    clk = clocks.stop()
+    e2e_ok = bool(np.array_equal(h_out, head_out))
+
+    # roofline of the sampling kernel (one launch per step)
+    peak, peak_kind = measured_hbm_peak()
+    hbm_bytes = 12 * int(off[-1]) + 4 * int(ba.total_out)
+    kernel_s = float(np.mean(ms)) / 1e3
+    achieved = hbm_bytes / kernel_s / 1e9
+    evals, compares = npdu_work(head_out, ba, K_WINDOW)
+    sm_mhz = clk["sm_mhz"] or 2070.0
+    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # FP32 lanes x clock, Tops/s
+    alu_ach = (9 * evals + compares) / kernel_s / 1e12
+    traffic = (NCU_TRAFFIC["bytes_per_launch"]
+               if NCU_TRAFFIC["source_hash"] == kernel_source_hash() else None)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "p50_ms": p50, "p99_ms": p99,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "clouds_per_gpu": B_CLOUDS, "N": N_POINTS,
+                   "C": C_SAMPLES, "M": M_SECTORS, "k": K_WINDOW,
+                   "l2": "flushed before every step (256 MB write)",
+                   "parallelism": f"replicas x{world}", "launch": "CUDA graph replay"},
+        "sampled_points_per_s": value * C_SAMPLES,
+        "fps_baseline": {"value": fps_value, "unit": UNIT, "ms_per_step": ms_fps,
+                         "speedup_npdu_afps": value / fps_value},
+        "sweep_clouds_per_s": sweep,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "algorithmic_bytes_per_launch": hbm_bytes,
+                     "kernel": "afps_warp_kernel<P=2,NPDU>"},
+        "roofline_alu": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
+                         "fp32_ops_per_launch": 9 * evals + compares},
+        "e2e": {"value": B_CLOUDS * world / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(h_xyz.nbytes), "d2h_bytes_per_step": int(h_out.nbytes),
+                "matches_device_path": e2e_ok},
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                   "reasons": clk["reasons"], "samples": clk["samples"]},
+    }
+
+    if rank == 0 and world == 1:
+        threads = cpu_threads()
+        rate, reps, ref = time_oracle(clouds, C_SAMPLES, M_SECTORS, K_WINDOW,
+                                      args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{reps} whole batches of {B_CLOUDS} clouds "
+                                          f"(about {args.cpu_seconds:.0f} s), threads over clouds"}
+        same = sum(int(np.array_equal(head_out[ba.out_off[b]:ba.out_off[b + 1]], ref[b]))
+                   for b in range(B_CLOUDS))
+        line["parity"] = f"{same}/{B_CLOUDS} clouds bit-exact vs the FP32 oracle"
+    else:
+        line["cpu_baseline"] = None
+    sampler.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--cpu-seconds", type=float, default=5.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    rank, world, local = rank_info()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * afps.h -- C ABI of the GB300 (sm_103a) NPDU-AFPS library, libafps.so.
+ *
+ * The method (arXiv 2208.08795):
+ *   - Farthest Point Sampling, Algorithm 1 (Sec. II-B): starting from one
+ *     sample, keep each point's distance to the nearest sample so far
+ *     (initially 1e10) and repeatedly take the farthest point;
+ *   - AFPS, Sec. III-B: cut the cloud by storage position into M contiguous
+ *     sectors and run FPS in each sector for C/M samples;
+ *   - NPDU, Sec. III-C and Fig. 3: after each new sample update only the k
+ *     points stored next to it, inside its own sector.
+ *
+ * Definitions fixed by this library where the paper leaves a choice:
+ *   - distance: squared Euclidean distance in fp32, (dx*dx + dy*dy) + dz*dz,
+ *     every product and sum rounded on its own (no fused multiply-add);
+ *   - sector s of a cloud of N points with C samples and M sectors covers
+ *     points [floor(s*N/M), floor((s+1)*N/M)) and takes
+ *     c_s = floor((s+1)*C/M) - floor(s*C/M) samples, written to output slots
+ *     [floor(s*C/M), floor((s+1)*C/M)) in the order they are selected;
+ *   - start: start_idx lies in sector s0 at offset r; every sector starts at
+ *     its own offset min(r, n_s - 1);
+ *   - NPDU window of a sample at sector offset p: offsets
+ *     [p - floor(k/2), p + k - floor(k/2)] clipped to the sector, i.e. k
+ *     neighbours plus the sample itself; k = 0 disables NPDU;
+ *   - no first full pass under NPDU: points never inside a window keep 1e10;
+ *   - ties in the argmax go to the lowest index.
+ * With M = 1 and k = 0 the result is plain FPS (Algorithm 1, fixed start).
+ *
+ * Conventions for every call:
+ *   - xyz is an array of points, 3 consecutive float32 per point (x, y, z),
+ *     4-byte aligned; coordinates must be finite.
+ *   - Output indices are int32, relative to the first point of their cloud,
+ *     sector-major (see above).
+ *   - "d_" pointers are device memory of the context's device, "h_" pointers
+ *     host memory.  The caller owns every buffer it passes; the context owns
+ *     its workspace, graphs and tuning cache.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless stated.
+ *   - Return value: AFPS_OK (0) or a negative AFPS_ERR_* code; the message of
+ *     the last error is afps_last_error(ctx).  Nothing is written to any
+ *     output on a validation error.
+ *   - A context may be used from one host thread at a time.  Calls on one
+ *     context are ordered on the device even across streams (the context's
+ *     workspace is reused only after the previous call using it finished).
+ */
+#ifndef AFPS_H
+#define AFPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AFPS_OK 0
+#define AFPS_ERR_INVALID_ARG (-1)      /* bad pointer, size or parameter */
+#define AFPS_ERR_SECTOR_TOO_SMALL (-2) /* some sector has c_s > n_s */
+#define AFPS_ERR_NO_MEMORY (-3)        /* device or host allocation failed */
+#define AFPS_ERR_TIMEOUT (-4)          /* a device-side wait ran out of time */
+#define AFPS_ERR_CUDA (-5)             /* a CUDA runtime call failed */
+#define AFPS_ERR_UNSUPPORTED (-6)      /* sector larger than AFPS_MAX_SECTOR_POINTS */
+
+/* Largest sector (points) any kernel handles: 16 CTAs x 1024 threads x 8. */
+#define AFPS_MAX_SECTOR_POINTS 131072
+
+/* afps_config.flags */
+#define AFPS_FLAG_GRAPH 1u     /* replay afps_sample_batched from cached CUDA graphs */
+#define AFPS_FLAG_AUTOTUNE 2u  /* time kernel variants on first use of a shape class */
+/* Fault injection for tests of failure detection: the stage-in arms its
+ * shared-memory barrier but never issues the bulk copy, so every bounded
+ * wait runs out (after timeout_ns) and afps_sync returns AFPS_ERR_TIMEOUT.
+ * Outputs of such calls are meaningless; the context stays usable. */
+#define AFPS_FLAG_TEST_STALL_COPY 0x100u
+
+typedef struct afps_ctx afps_ctx;
+
+typedef struct afps_config {
+    int32_t device;         /* CUDA device ordinal */
+    uint32_t flags;         /* AFPS_FLAG_* */
+    int64_t timeout_ns;     /* bound on each device-side wait; <= 0: 2 s */
+    const char* tune_cache; /* autotuner cache file (read at create, written
+                               by afps_save_tuning), or NULL */
+} afps_config;
+
+/*
+ * Create a context on cfg->device (cfg may be NULL: device 0, no flags).
+ * Allocates a small device status word and host staging.  On success *out
+ * owns the context; free it with afps_destroy.
+ */
+int afps_create(afps_ctx** out, const afps_config* cfg);
+
+/* Synchronise the context's device work and free everything it owns. */
+void afps_destroy(afps_ctx* ctx);
+
+/*
+ * NPDU-AFPS of one cloud (Algorithm 1 + Sec. III-B + Sec. III-C).
+ *   d_xyz        N points (device, read only)
+ *   N            points, 1 <= N <= 2^31 - 1
+ *   C            samples, 1 <= C <= N
+ *   M            sectors, 1 <= M <= C; every sector needs c_s <= n_s
+ *   npdu_window  k >= 0 (0 = no NPDU)
+ *   start_idx    0 <= start_idx < N (Algorithm 1 draws it at random; the
+ *                caller passes it)
+ *   d_out        C int32 (device, written)
+ * Sectors above AFPS_MAX_SECTOR_POINTS return AFPS_ERR_UNSUPPORTED.
+ */
+int afps_sample(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int32_t M,
+                int32_t npdu_window, int64_t start_idx, int32_t* d_out, void* stream);
+
+/*
+ * A ragged batch of B clouds in one call: cloud b is points
+ * [h_pt_off[b], h_pt_off[b+1]) of d_xyz and writes h_C[b] indices at
+ * d_out[h_out_off[b]], relative to its own first point.  Each cloud has its
+ * own C, M, k and start (h_* arrays of B entries; h_pt_off and h_out_off of
+ * B+1 nondecreasing entries with h_out_off[b+1] - h_out_off[b] >= h_C[b]).
+ * All (cloud, sector) work items run in one launch per kernel shape class;
+ * with AFPS_FLAG_GRAPH the launches are captured once per distinct argument
+ * set (pointers included) and replayed.  Host arrays are read before return.
+ */
+int afps_sample_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_off,
+                        int32_t B, const int32_t* h_C, const int32_t* h_M,
+                        const int32_t* h_win, const int64_t* h_start,
+                        const int64_t* h_out_off, int32_t* d_out, void* stream);
+
+/*
+ * afps_sample_batched on HOST buffers: copies h_xyz (h_pt_off[B] points) to
+ * context-owned device memory, samples, copies the h_out_off[B] indices back
+ * to h_out and waits for the stream.  Pinned host memory makes the copies
+ * asynchronous DMA; pageable memory works but is slower.  Synchronous.
+ */
+int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off,
+                             int32_t B, const int32_t* h_C, const int32_t* h_M,
+                             const int32_t* h_win, const int64_t* h_start,
+                             const int64_t* h_out_off, int32_t* h_out, void* stream);
+
+/*
+ * Gather for chained sampling levels (the PointNet++ set-abstraction
+ * hierarchy the paper targets, Sec. I-II): for each of B clouds, take the
+ * samples d_sel[h_sel_off[b] .. h_sel_off[b+1]) (indices relative to the
+ * cloud), sort them by ascending index (which keeps the storage order, and
+ * hence the dimensional locality of Sec. III-A, for the next level) and write
+ *   d_out_xyz   the sampled points in that order (3 floats each),
+ *   d_out_frame d_in_frame[...] of those points in that order (the original
+ *               frame index; d_in_frame NULL means the identity),
+ *   d_sel_frame d_in_frame[sel] in the samples' own order (may be NULL).
+ * Outputs use the h_sel_off layout.  Clouds up to 65536 points.
+ */
+int afps_gather_levels(afps_ctx* ctx, int32_t B, const int64_t* h_in_pt_off,
+                       const float* d_in_xyz, const int32_t* d_in_frame,
+                       const int64_t* h_sel_off, const int32_t* d_sel,
+                       float* d_out_xyz, int32_t* d_out_frame, int32_t* d_sel_frame,
+                       void* stream);
+
+/*
+ * Wait for the stream and report device-side errors recorded since the last
+ * call (AFPS_ERR_TIMEOUT when a bounded wait gave up); clears them.
+ */
+int afps_sync(afps_ctx* ctx, void* stream);
+
+/* Message of the last error on this context (never NULL; "" if none). */
+const char* afps_last_error(const afps_ctx* ctx);
+
+/*
+ * Autotuner: time every kernel variant valid for the batch (same arguments
+ * as afps_sample_batched; d_out is written with the correct result) and
+ * remember the fastest per shape class.  Returns the number of classes
+ * tuned, or a negative error.
+ */
+int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_off,
+                          int32_t B, const int32_t* h_C, const int32_t* h_M,
+                          const int32_t* h_win, const int64_t* h_start,
+                          const int64_t* h_out_off, int32_t* d_out, void* stream);
+
+/* Write the tuning cache to path (NULL: the path given at create). */
+int afps_save_tuning(afps_ctx* ctx, const char* path);
+
+/*
+ * Describe the kernel variant the planner would use for n_items sectors of
+ * at most n_sector points and c_sector samples (for afps_sample, n_items is
+ * M): writes a short text (kind, points per thread, warps per CTA, cluster
+ * size) into buf.  Returns the text length or a negative error.
+ */
+int afps_describe_plan(afps_ctx* ctx, int64_t n_sector, int32_t c_sector,
+                       int32_t npdu_window, int32_t n_items, char* buf, int32_t buf_len);
+
+/* Number of kernel launches issued by this context since creation. */
+int64_t afps_launch_count(const afps_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFPS_H */

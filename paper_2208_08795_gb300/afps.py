@@ -1,0 +1,308 @@
+"""Thin ctypes binding of libafps.so (include/afps.h).
+
+The functions ``afps_*`` below have the C names and arguments (device and
+host buffers as integer addresses, the stream as a ``cudaStream_t`` address);
+they only marshal arguments.  :class:`Sampler` wraps them for torch tensors:
+torch provides device memory and the current stream, every step of the
+sampling runs in the library's CUDA kernels.  There is no CPU fallback: a
+missing or unloadable library raises :class:`AfpsLibraryError`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIBRARY = os.path.join(_PKG, "libafps.so")
+
+AFPS_OK = 0
+AFPS_ERR_INVALID_ARG = -1
+AFPS_ERR_SECTOR_TOO_SMALL = -2
+AFPS_ERR_NO_MEMORY = -3
+AFPS_ERR_TIMEOUT = -4
+AFPS_ERR_CUDA = -5
+AFPS_ERR_UNSUPPORTED = -6
+AFPS_MAX_SECTOR_POINTS = 131072
+AFPS_FLAG_GRAPH = 1
+AFPS_FLAG_AUTOTUNE = 2
+AFPS_FLAG_TEST_STALL_COPY = 0x100
+
+# every symbol include/afps.h declares
+EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
+           "afps_sample_batched_host", "afps_gather_levels", "afps_sync",
+           "afps_last_error", "afps_autotune_batched", "afps_save_tuning",
+           "afps_describe_plan", "afps_launch_count")
+
+
+class AfpsLibraryError(RuntimeError):
+    pass
+
+
+class AfpsError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"afps error {code}: {message}")
+        self.code = code
+        self.message = message
+
+
+class afps_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("timeout_ns", ctypes.c_int64), ("tune_cache", ctypes.c_char_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.afps_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(afps_config)]
+    L.afps_create.restype = ctypes.c_int
+    L.afps_destroy.argtypes = [vp]
+    L.afps_destroy.restype = None
+    L.afps_sample.argtypes = [vp, vp, i64, i32, i32, i32, i64, vp, vp]
+    L.afps_sample.restype = ctypes.c_int
+    batched = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
+    for name in ("afps_sample_batched", "afps_sample_batched_host", "afps_autotune_batched"):
+        getattr(L, name).argtypes = batched
+        getattr(L, name).restype = ctypes.c_int
+    L.afps_gather_levels.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.afps_gather_levels.restype = ctypes.c_int
+    L.afps_sync.argtypes = [vp, vp]
+    L.afps_sync.restype = ctypes.c_int
+    L.afps_last_error.argtypes = [vp]
+    L.afps_last_error.restype = ctypes.c_char_p
+    L.afps_save_tuning.argtypes = [vp, ctypes.c_char_p]
+    L.afps_save_tuning.restype = ctypes.c_int
+    L.afps_describe_plan.argtypes = [vp, i64, i32, i32, i32, ctypes.c_char_p, i32]
+    L.afps_describe_plan.restype = ctypes.c_int
+    L.afps_launch_count.argtypes = [vp]
+    L.afps_launch_count.restype = ctypes.c_int64
+    return L
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libafps.so (built by ``paper_2208_08795_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIBRARY
+            if not os.path.exists(p):
+                raise AfpsLibraryError(
+                    f"{p} is missing: build it with `python -m paper_2208_08795_gb300.build` "
+                    "(there is no CPU fallback)")
+            try:
+                _lib = _declare(ctypes.CDLL(p))
+            except OSError as e:
+                raise AfpsLibraryError(f"cannot load {p}: {e}") from e
+        return _lib
+
+
+# ------------------------------------------------------------- raw C calls
+def afps_create(device: int = 0, flags: int = 0, timeout_ns: int = 0,
+                tune_cache: str | None = None) -> int:
+    cfg = afps_config(device, flags, timeout_ns,
+                      tune_cache.encode() if tune_cache else None)
+    h = ctypes.c_void_p()
+    rc = load().afps_create(ctypes.byref(h), ctypes.byref(cfg))
+    if rc != AFPS_OK:
+        raise AfpsError(rc, "afps_create failed")
+    return h.value
+
+
+def afps_destroy(ctx: int) -> None:
+    load().afps_destroy(ctx)
+
+
+def afps_sample(ctx, d_xyz, N, C, M, npdu_window, start_idx, d_out, stream) -> int:
+    return load().afps_sample(ctx, d_xyz, N, C, M, npdu_window, start_idx, d_out, stream)
+
+
+def afps_sample_batched(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
+                        d_out, stream) -> int:
+    return load().afps_sample_batched(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start,
+                                      h_out_off, d_out, stream)
+
+
+def afps_sample_batched_host(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
+                             h_out, stream) -> int:
+    return load().afps_sample_batched_host(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win,
+                                           h_start, h_out_off, h_out, stream)
+
+
+def afps_autotune_batched(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
+                          d_out, stream) -> int:
+    return load().afps_autotune_batched(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start,
+                                        h_out_off, d_out, stream)
+
+
+def afps_gather_levels(ctx, B, h_in_pt_off, d_in_xyz, d_in_frame, h_sel_off, d_sel,
+                       d_out_xyz, d_out_frame, d_sel_frame, stream) -> int:
+    return load().afps_gather_levels(ctx, B, h_in_pt_off, d_in_xyz, d_in_frame, h_sel_off,
+                                     d_sel, d_out_xyz, d_out_frame, d_sel_frame, stream)
+
+
+def afps_sync(ctx, stream) -> int:
+    return load().afps_sync(ctx, stream)
+
+
+def afps_last_error(ctx) -> str:
+    return load().afps_last_error(ctx).decode()
+
+
+def afps_save_tuning(ctx, path: str | None) -> int:
+    return load().afps_save_tuning(ctx, path.encode() if path else None)
+
+
+def afps_describe_plan(ctx, n_sector: int, c_sector: int, npdu_window: int,
+                       n_items: int = 1) -> str:
+    buf = ctypes.create_string_buffer(128)
+    rc = load().afps_describe_plan(ctx, n_sector, c_sector, npdu_window, n_items, buf, 128)
+    if rc < 0:
+        raise AfpsError(rc, "afps_describe_plan failed")
+    return buf.value.decode()
+
+
+def afps_launch_count(ctx) -> int:
+    return load().afps_launch_count(ctx)
+
+
+# ---------------------------------------------------------------- helpers
+def _i64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class BatchArgs:
+    """Host arrays of a batched call, kept alive for the call's duration."""
+
+    def __init__(self, pt_off, C, M, k, start, out_off=None):
+        self.pt_off = _i64(pt_off)
+        B = self.pt_off.size - 1
+        self.B = B
+        self.C = _i32(np.broadcast_to(C, (B,)))
+        self.M = _i32(np.broadcast_to(M, (B,)))
+        self.k = _i32(np.broadcast_to(k, (B,)))
+        self.start = _i64(np.broadcast_to(start, (B,)))
+        if out_off is None:
+            out_off = np.zeros(B + 1, dtype=np.int64)
+            np.cumsum(self.C, out=out_off[1:])
+        self.out_off = _i64(out_off)
+
+    def args(self):
+        return (_ptr(self.pt_off), self.B, _ptr(self.C), _ptr(self.M), _ptr(self.k),
+                _ptr(self.start), _ptr(self.out_off))
+
+    @property
+    def total_out(self) -> int:
+        return int(self.out_off[-1])
+
+
+class Sampler:
+    """A libafps context on one CUDA device, driven with torch tensors."""
+
+    def __init__(self, device: int = 0, graph: bool = False, timeout_ns: int = 0,
+                 tune_cache: str | None = None, flags: int = 0):
+        flags |= AFPS_FLAG_GRAPH if graph else 0
+        self.device = device
+        self.ctx = afps_create(device, flags, timeout_ns, tune_cache)
+
+    def close(self):
+        if self.ctx:
+            afps_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != AFPS_OK:
+            raise AfpsError(rc, afps_last_error(self.ctx))
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return s.cuda_stream
+
+    @staticmethod
+    def _points(xyz):
+        import torch
+        if not (isinstance(xyz, torch.Tensor) and xyz.is_cuda and xyz.dtype == torch.float32
+                and xyz.dim() == 2 and xyz.shape[1] == 3 and xyz.is_contiguous()):
+            raise ValueError("xyz must be a contiguous float32 CUDA tensor of shape (N, 3)")
+        return xyz
+
+    def sample(self, xyz, C: int, M: int = 1, k: int = 0, start: int = 0, out=None,
+               stream=None):
+        """NPDU-AFPS of one cloud; returns C int32 indices (sector-major)."""
+        import torch
+        xyz = self._points(xyz)
+        if out is None:
+            out = torch.empty(C, dtype=torch.int32, device=xyz.device)
+        self._check(afps_sample(self.ctx, xyz.data_ptr(), xyz.shape[0], C, M, k, start,
+                                out.data_ptr(), self._stream(stream)))
+        return out
+
+    def sample_batched(self, xyz, pt_off, C, M, k, start=0, out_off=None, out=None,
+                       stream=None):
+        """Ragged batch: cloud b is xyz[pt_off[b]:pt_off[b+1]]."""
+        import torch
+        xyz = self._points(xyz)
+        ba = pt_off if isinstance(pt_off, BatchArgs) else BatchArgs(pt_off, C, M, k, start, out_off)
+        if out is None:
+            out = torch.empty(ba.total_out, dtype=torch.int32, device=xyz.device)
+        self._check(afps_sample_batched(self.ctx, xyz.data_ptr(), *ba.args(), out.data_ptr(),
+                                        self._stream(stream)))
+        return out
+
+    def sample_batched_host(self, h_xyz: np.ndarray, ba: "BatchArgs", h_out: np.ndarray,
+                            stream=None):
+        """Host buffers in and out; the copies run inside the call."""
+        assert h_xyz.dtype == np.float32 and h_xyz.flags.c_contiguous
+        assert h_out.dtype == np.int32 and h_out.flags.c_contiguous
+        self._check(load().afps_sample_batched_host(
+            self.ctx, h_xyz.ctypes.data, _ptr(ba.pt_off), ba.B, _ptr(ba.C), _ptr(ba.M),
+            _ptr(ba.k), _ptr(ba.start), _ptr(ba.out_off), h_out.ctypes.data,
+            self._stream(stream)))
+        return h_out
+
+    def autotune_batched(self, xyz, ba: "BatchArgs", out, stream=None) -> int:
+        rc = load().afps_autotune_batched(self.ctx, xyz.data_ptr(), _ptr(ba.pt_off), ba.B,
+                                          _ptr(ba.C), _ptr(ba.M), _ptr(ba.k), _ptr(ba.start),
+                                          _ptr(ba.out_off), out.data_ptr(), self._stream(stream))
+        if rc < 0:
+            raise AfpsError(rc, afps_last_error(self.ctx))
+        return rc
+
+    def gather_levels(self, in_pt_off, in_xyz, in_frame, sel_off, sel, out_xyz, out_frame,
+                      sel_frame=None, stream=None):
+        ipo, so = _i64(in_pt_off), _i64(sel_off)
+        self._check(afps_gather_levels(
+            self.ctx, ipo.size - 1, _ptr(ipo), in_xyz.data_ptr(),
+            in_frame.data_ptr() if in_frame is not None else None, _ptr(so), sel.data_ptr(),
+            out_xyz.data_ptr(), out_frame.data_ptr() if out_frame is not None else None,
+            sel_frame.data_ptr() if sel_frame is not None else None, self._stream(stream)))
+
+    def sync(self, stream=None):
+        self._check(afps_sync(self.ctx, self._stream(stream)))
+
+    def describe_plan(self, n_sector: int, c_sector: int, k: int, n_items: int = 1) -> str:
+        return afps_describe_plan(self.ctx, n_sector, c_sector, k, n_items)
+
+    @property
+    def launch_count(self) -> int:
+        return afps_launch_count(self.ctx)

@@ -1,0 +1,859 @@
+// afps_api.cu -- the C ABI of include/afps.h: argument checks, the sector
+// plan (Sec. III-B), kernel-variant choice, the batched work-item table,
+// CUDA-graph replay, the autotuner and device-error reporting.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/afps.h"
+#include "afps_internal.h"
+
+using afps::ItemDesc;
+using afps::LaunchArgs;
+using afps::SingleCloud;
+using afps::Variant;
+
+namespace {
+
+constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
+constexpr size_t kMaxGraphs = 32;
+
+// ---------------------------------------------------------------- buffers
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t want) {
+        if (want <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        size_t cap = std::max(want, (size_t)4096);
+        cudaError_t e = cudaMalloc(&p, cap);
+        if (e == cudaSuccess) bytes = cap;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+struct HostBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t want) {
+        if (want <= bytes) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+        size_t cap = std::max(want, (size_t)4096);
+        cudaError_t e = cudaMallocHost(&p, cap);
+        if (e == cudaSuccess) bytes = cap;
+        return e;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+// One launch class of a batched call: items that share a kernel variant.
+struct ClassPlan {
+    bool npdu = false;
+    int64_t n_max = 0;
+    int32_t c_max = 0;
+    Variant v{};
+    size_t first = 0;  // first item in the concatenated table
+    size_t count = 0;
+};
+
+struct BatchPlan {
+    std::vector<ItemDesc> items;  // class-major
+    std::vector<ClassPlan> classes;
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    DevBuf items;
+    DevBuf counters;
+    int64_t kernels = 0;
+    uint64_t last_use = 0;
+};
+
+}  // namespace
+
+struct afps_ctx {
+    int device = 0;
+    uint32_t flags = 0;
+    uint64_t timeout_ns = kDefaultTimeoutNs;
+    std::string tune_path;
+    int num_sms = 0;
+    int* d_status = nullptr;
+    std::string last_error;
+    cudaEvent_t ev_done = nullptr;    // last device work that used the shared workspace
+    cudaEvent_t ev_upload = nullptr;  // last host->device copy out of h_items
+    cudaStream_t capture = nullptr;   // private stream for graph capture
+    DevBuf items, counters, xyz_stage, out_stage;
+    HostBuf h_items;
+    std::unordered_map<std::string, GraphEntry> graphs;
+    std::map<std::string, Variant> tuned;
+    int64_t launches = 0;
+    uint64_t tick = 0;
+};
+
+namespace {
+
+int fail(afps_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+int cuda_fail(afps_ctx* ctx, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();  // clear a sticky launch error so the context stays usable
+    return fail(ctx, AFPS_ERR_CUDA, m);
+}
+
+#define AFPS_CUDA(ctx, call)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------- sectors
+// Sector s of a cloud (Sec. III-B): points [floor(sN/M), floor((s+1)N/M)),
+// output slots [floor(sC/M), floor((s+1)C/M)).
+inline int64_t sec_lo(int64_t N, int64_t M, int64_t s) { return s * N / M; }
+inline int64_t sec_off(int64_t C, int64_t M, int64_t s) { return s * C / M; }
+
+// A window of k >= 2n covers the whole sector wherever the sample lies, so
+// clamping k there changes no result and keeps p + k in int32 on the device.
+inline int32_t device_window(int32_t k) {
+    return (int32_t)std::min<int64_t>(k, 4LL * AFPS_MAX_SECTOR_POINTS);
+}
+
+struct CloudCheck {
+    int code = AFPS_OK;
+    std::string msg;
+    int64_t n_max = 0;
+    int32_t c_max = 0;
+    int32_t start_r = 0;
+};
+
+CloudCheck check_cloud(int64_t N, int32_t C, int32_t M, int32_t k, int64_t start) {
+    CloudCheck r;
+    std::ostringstream os;
+    if (N < 1 || N > INT32_MAX || C < 1 || (int64_t)C > N || M < 1 || M > C || k < 0 ||
+        start < 0 || start >= N) {
+        os << "invalid arguments: N=" << N << " C=" << C << " M=" << M << " k=" << k
+           << " start=" << start << " (need 1<=C<=N<2^31, 1<=M<=C, k>=0, 0<=start<N)";
+        r.code = AFPS_ERR_INVALID_ARG;
+        r.msg = os.str();
+        return r;
+    }
+    int64_t s0 = -1;
+    for (int64_t s = 0; s < M; ++s) {
+        const int64_t lo = sec_lo(N, M, s), hi = sec_lo(N, M, s + 1);
+        const int64_t c = sec_off(C, M, s + 1) - sec_off(C, M, s);
+        if (c > hi - lo) {
+            os << "sector " << s << " has " << (hi - lo) << " points but " << c
+               << " samples (N=" << N << " C=" << C << " M=" << M << ")";
+            r.code = AFPS_ERR_SECTOR_TOO_SMALL;
+            r.msg = os.str();
+            return r;
+        }
+        r.n_max = std::max(r.n_max, hi - lo);
+        r.c_max = std::max<int32_t>(r.c_max, (int32_t)c);
+        if (start >= lo && start < hi) s0 = s;
+    }
+    r.start_r = (int32_t)(start - sec_lo(N, M, s0));
+    if (r.n_max > AFPS_MAX_SECTOR_POINTS) {
+        os << "sector of " << r.n_max << " points exceeds AFPS_MAX_SECTOR_POINTS ("
+           << AFPS_MAX_SECTOR_POINTS << ")";
+        r.code = AFPS_ERR_UNSUPPORTED;
+        r.msg = os.str();
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------- variants
+const int kWarpP[] = {1, 2, 3, 4, 6, 8, 12, 16};
+const int kCtaP[] = {2, 4, 8};
+
+// Default variant for sectors of up to n_max points.
+Variant default_variant(int64_t n_max) {
+    Variant v{};
+    v.CS = 1;
+    v.occ = 0;
+    if (n_max <= 512) {
+        v.kind = afps::KIND_WARP;
+        for (int P : kWarpP)
+            if (32LL * P >= n_max) {
+                v.P = P;
+                break;
+            }
+        v.W = v.P <= 4 ? 8 : 4;
+        return v;
+    }
+    v.kind = afps::KIND_CTA;
+    if (n_max <= 4096) {
+        v.P = 4;
+        v.W = (int)((n_max + 127) / 128);
+        return v;
+    }
+    if (n_max <= 8192) {
+        v.P = 8;
+        v.W = (int)((n_max + 255) / 256);
+        return v;
+    }
+    v.P = 8;
+    v.W = 16;
+    v.CS = (int)((n_max + 4095) / 4096);
+    if (v.CS > 16) {
+        v.W = 32;
+        v.CS = (int)((n_max + 8191) / 8192);
+    }
+    return v;
+}
+
+// Every variant the autotuner tries for sectors of up to n_max points.
+std::vector<Variant> candidate_variants(int64_t n_max) {
+    std::vector<Variant> out;
+    if (n_max <= 512) {
+        for (int P : kWarpP) {
+            if (32LL * P < n_max) continue;
+            for (int W : {2, 4, 8}) out.push_back(Variant{afps::KIND_WARP, P, W, 1, 0});
+            break;  // the smallest P that fits: larger P only adds padding
+        }
+    }
+    for (int P : kCtaP) {
+        const int64_t W = (n_max + 32LL * P - 1) / (32LL * P);
+        if (W >= 2 && W <= 32) out.push_back(Variant{afps::KIND_CTA, P, (int)W, 1, 0});
+    }
+    if (n_max > 2048) {
+        for (int P : {4, 8})
+            for (int W : {8, 16, 32}) {
+                const int64_t CS = (n_max + 32LL * W * P - 1) / (32LL * W * P);
+                if (CS >= 2 && CS <= 16) out.push_back(Variant{afps::KIND_CTA, P, W, (int)CS, 0});
+            }
+    }
+    std::vector<Variant> ok;
+    for (const Variant& v : out)
+        if (afps::variant_supported(v) && afps::variant_capacity(v) >= n_max) ok.push_back(v);
+    return ok;
+}
+
+std::string class_key(bool npdu, int64_t n_max, int32_t c_max, size_t items) {
+    size_t b = 1;
+    while (b < items) b <<= 1;
+    std::ostringstream os;
+    os << (npdu ? "npdu" : "full") << ":n" << n_max << ":c" << c_max << ":i" << b;
+    return os.str();
+}
+
+Variant choose_variant(const afps_ctx* ctx, bool npdu, int64_t n_max, int32_t c_max,
+                       size_t items) {
+    auto it = ctx->tuned.find(class_key(npdu, n_max, c_max, items));
+    if (it != ctx->tuned.end() && afps::variant_capacity(it->second) >= n_max &&
+        afps::variant_supported(it->second))
+        return it->second;
+    return default_variant(n_max);
+}
+
+std::string describe(const Variant& v) {
+    std::ostringstream os;
+    if (v.kind == afps::KIND_WARP)
+        os << "warp P=" << v.P << " W=" << v.W;
+    else if (v.CS > 1)
+        os << "cluster P=" << v.P << " W=" << v.W << " CS=" << v.CS;
+    else
+        os << "cta P=" << v.P << " W=" << v.W;
+    return os.str();
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------- launching
+// Grid for `count` items of variant v: one CTA per W items (warp kind) or
+// one CTA / cluster per item, capped at what can be co-resident, in which
+// case the kernels stride over the remaining items (persistent launch).
+int grid_for(const Variant& v, size_t count) {
+    static std::map<std::tuple<int, int, int, int>, int> cache;
+    auto key = std::make_tuple(v.kind, v.P, v.W, v.CS);
+    auto it = cache.find(key);
+    int cap;
+    if (it == cache.end()) {
+        cap = afps::max_active_clusters(v);
+        cache[key] = cap;
+    } else {
+        cap = it->second;
+    }
+    size_t want = v.kind == afps::KIND_WARP ? (count + v.W - 1) / v.W : count;
+    if (cap > 0 && want > (size_t)cap) want = (size_t)cap;
+    return (int)std::max<size_t>(want, 1);
+}
+
+int launch_class(afps_ctx* ctx, const Variant& v, bool npdu, const ItemDesc* d_items,
+                 size_t count, unsigned int* d_counter, const float* xyz, int32_t* out,
+                 cudaStream_t stream) {
+    LaunchArgs a{};
+    a.xyz = xyz;
+    a.items = d_items;
+    a.n_items = (int32_t)count;
+    a.out = out;
+    // The dynamic queue is needed only when the grid is capped below one
+    // warp per item (persistent launch); otherwise items map to warps 1:1.
+    const int grid = grid_for(v, count);
+    const bool persistent =
+        v.kind == afps::KIND_WARP && (size_t)grid * (size_t)v.W < count && d_counter;
+    a.counter = persistent ? d_counter : nullptr;
+    a.status = ctx->d_status;
+    a.timeout_ns = ctx->timeout_ns;
+    a.stall_copy = (ctx->flags & AFPS_FLAG_TEST_STALL_COPY) ? 1u : 0u;
+    if (a.counter) AFPS_CUDA(ctx, cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), stream));
+    cudaError_t e = afps::launch_sector(v, npdu, a, grid, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sector kernel launch");
+    ctx->launches += 1;
+    return AFPS_OK;
+}
+
+// Size class of a sector: the warp capacities up to 512 points, then powers
+// of two.  Clouds of one class share a kernel variant in a batched call.
+int64_t size_bucket(int64_t n_max) {
+    if (n_max <= 512) {
+        for (int P : kWarpP)
+            if (32LL * P >= n_max) return 32LL * P;
+    }
+    int64_t b = 1024;
+    while (b < n_max) b <<= 1;
+    return b;
+}
+
+int build_plan(afps_ctx* ctx, const int64_t* pt_off, int32_t B, const int32_t* C,
+               const int32_t* M, const int32_t* K, const int64_t* start,
+               const int64_t* out_off, BatchPlan& plan) {
+    if (B < 1 || !pt_off || !C || !M || !K || !start || !out_off)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
+    if (pt_off[0] < 0 || out_off[0] < 0)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: negative first offset");
+    struct Member {
+        int32_t b;
+        CloudCheck chk;
+    };
+    std::map<std::pair<int, int64_t>, std::vector<Member>> groups;
+    for (int32_t b = 0; b < B; ++b) {
+        const int64_t N = pt_off[b + 1] - pt_off[b];
+        if (out_off[b + 1] - out_off[b] < (int64_t)C[b]) {
+            std::ostringstream os;
+            os << "cloud " << b << ": output range " << (out_off[b + 1] - out_off[b])
+               << " is smaller than C=" << C[b];
+            return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
+        }
+        CloudCheck chk = check_cloud(N, C[b], M[b], K[b], start[b]);
+        if (chk.code != AFPS_OK) {
+            std::ostringstream os;
+            os << "cloud " << b << ": " << chk.msg;
+            return fail(ctx, chk.code, os.str());
+        }
+        groups[{K[b] > 0 ? 1 : 0, size_bucket(chk.n_max)}].push_back(Member{b, chk});
+    }
+    plan.items.clear();
+    plan.classes.clear();
+    for (auto& g : groups) {
+        ClassPlan cp;
+        cp.npdu = g.first.first == 1;
+        cp.first = plan.items.size();
+        for (const Member& m : g.second) {
+            const int32_t b = m.b;
+            const int64_t N = pt_off[b + 1] - pt_off[b];
+            cp.n_max = std::max(cp.n_max, m.chk.n_max);
+            cp.c_max = std::max(cp.c_max, m.chk.c_max);
+            for (int64_t s = 0; s < M[b]; ++s) {
+                const int64_t lo = sec_lo(N, M[b], s), hi = sec_lo(N, M[b], s + 1);
+                const int64_t o0 = sec_off(C[b], M[b], s), o1 = sec_off(C[b], M[b], s + 1);
+                ItemDesc d{};
+                d.src = pt_off[b] + lo;
+                d.dst = out_off[b] + o0;
+                d.n = (int32_t)(hi - lo);
+                d.c = (int32_t)(o1 - o0);
+                d.first = std::min<int32_t>(m.chk.start_r, d.n - 1);
+                d.lo = (int32_t)lo;
+                d.k = device_window(K[b]);
+                plan.items.push_back(d);
+            }
+        }
+        cp.count = plan.items.size() - cp.first;
+        // largest work first (longest-processing-time order for the queue)
+        auto cost = [&](const ItemDesc& d) {
+            return cp.npdu ? (int64_t)d.c * (d.k + 1 + d.n / 32) : (int64_t)d.c * d.n;
+        };
+        std::stable_sort(plan.items.begin() + cp.first, plan.items.end(),
+                         [&](const ItemDesc& x, const ItemDesc& y) { return cost(x) > cost(y); });
+        cp.v = choose_variant(ctx, cp.npdu, cp.n_max, cp.c_max, cp.count);
+        plan.classes.push_back(cp);
+    }
+    return AFPS_OK;
+}
+
+// Run a plan out of the context's shared workspace (no graph).
+int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* d_out,
+             cudaStream_t stream) {
+    const size_t bytes = plan.items.size() * sizeof(ItemDesc);
+    // the pinned staging may still feed an earlier copy
+    AFPS_CUDA(ctx, cudaEventSynchronize(ctx->ev_upload));
+    AFPS_CUDA(ctx, ctx->h_items.reserve(bytes));
+    AFPS_CUDA(ctx, ctx->items.reserve(bytes));
+    AFPS_CUDA(ctx, ctx->counters.reserve(plan.classes.size() * sizeof(unsigned int)));
+    memcpy(ctx->h_items.p, plan.items.data(), bytes);
+    // earlier device work on the workspace, possibly on another stream
+    AFPS_CUDA(ctx, cudaStreamWaitEvent(stream, ctx->ev_done, 0));
+    AFPS_CUDA(ctx, cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, bytes, cudaMemcpyHostToDevice,
+                                   stream));
+    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_upload, stream));
+    const ItemDesc* d_items = static_cast<const ItemDesc*>(ctx->items.p);
+    unsigned int* counters = static_cast<unsigned int*>(ctx->counters.p);
+    for (size_t i = 0; i < plan.classes.size(); ++i) {
+        const ClassPlan& cp = plan.classes[i];
+        int rc = launch_class(ctx, cp.v, cp.npdu, d_items + cp.first, cp.count, counters + i,
+                              d_xyz, d_out, stream);
+        if (rc != AFPS_OK) return rc;
+    }
+    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, stream));
+    return AFPS_OK;
+}
+
+std::string graph_key(const float* d_xyz, int32_t* d_out, const int64_t* pt_off, int32_t B,
+                      const int32_t* C, const int32_t* M, const int32_t* K,
+                      const int64_t* start, const int64_t* out_off) {
+    std::string k;
+    k.reserve(64 + (size_t)B * 40);
+    auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+    put(&d_xyz, sizeof d_xyz);
+    put(&d_out, sizeof d_out);
+    put(&B, sizeof B);
+    put(pt_off, sizeof(int64_t) * (B + 1));
+    put(out_off, sizeof(int64_t) * (B + 1));
+    put(C, sizeof(int32_t) * B);
+    put(M, sizeof(int32_t) * B);
+    put(K, sizeof(int32_t) * B);
+    put(start, sizeof(int64_t) * B);
+    return k;
+}
+
+void drop_graph(GraphEntry& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.items.release();
+    g.counters.release();
+}
+
+void clear_graphs(afps_ctx* ctx) {
+    if (ctx->graphs.empty()) return;
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->graphs) drop_graph(kv.second);
+    ctx->graphs.clear();
+}
+
+// Capture the plan's launches (counter resets + one kernel per class) into a
+// graph that owns its own item table, so replays need no upload.
+int make_graph(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* d_out,
+               GraphEntry& g) {
+    const size_t bytes = plan.items.size() * sizeof(ItemDesc);
+    AFPS_CUDA(ctx, g.items.reserve(bytes));
+    AFPS_CUDA(ctx, g.counters.reserve(plan.classes.size() * sizeof(unsigned int)));
+    AFPS_CUDA(ctx, cudaMemcpy(g.items.p, plan.items.data(), bytes, cudaMemcpyHostToDevice));
+    const ItemDesc* d_items = static_cast<const ItemDesc*>(g.items.p);
+    unsigned int* counters = static_cast<unsigned int*>(g.counters.p);
+    AFPS_CUDA(ctx, cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = ctx->launches;
+    int rc = AFPS_OK;
+    for (size_t i = 0; i < plan.classes.size() && rc == AFPS_OK; ++i) {
+        const ClassPlan& cp = plan.classes[i];
+        rc = launch_class(ctx, cp.v, cp.npdu, d_items + cp.first, cp.count, counters + i, d_xyz,
+                          d_out, ctx->capture);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->capture, &graph);
+    g.kernels = ctx->launches - before;
+    ctx->launches = before;  // capture launched nothing yet
+    if (rc != AFPS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    return AFPS_OK;
+}
+
+int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int32_t B,
+                   const int32_t* C, const int32_t* M, const int32_t* K, const int64_t* start,
+                   const int64_t* out_off, int32_t* d_out, cudaStream_t stream) {
+    if (!d_xyz || !d_out) return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: NULL device pointer");
+    if (reinterpret_cast<uintptr_t>(d_xyz) % 4 || reinterpret_cast<uintptr_t>(d_out) % 4)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: xyz and out must be 4-byte aligned");
+    if (!(ctx->flags & AFPS_FLAG_GRAPH)) {
+        BatchPlan plan;
+        int rc = build_plan(ctx, pt_off, B, C, M, K, start, out_off, plan);
+        if (rc != AFPS_OK) return rc;
+        return run_plan(ctx, plan, d_xyz, d_out, stream);
+    }
+    if (B < 1 || !pt_off || !C || !M || !K || !start || !out_off)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
+    const std::string key = graph_key(d_xyz, d_out, pt_off, B, C, M, K, start, out_off);
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        BatchPlan plan;
+        int rc = build_plan(ctx, pt_off, B, C, M, K, start, out_off, plan);
+        if (rc != AFPS_OK) return rc;
+        if (ctx->graphs.size() >= kMaxGraphs) {  // evict the least recently used
+            auto victim = ctx->graphs.begin();
+            for (auto j = ctx->graphs.begin(); j != ctx->graphs.end(); ++j)
+                if (j->second.last_use < victim->second.last_use) victim = j;
+            cudaDeviceSynchronize();
+            drop_graph(victim->second);
+            ctx->graphs.erase(victim);
+        }
+        GraphEntry g;
+        rc = make_graph(ctx, plan, d_xyz, d_out, g);
+        if (rc != AFPS_OK) {
+            drop_graph(g);
+            return rc;
+        }
+        it = ctx->graphs.emplace(key, g).first;
+    }
+    it->second.last_use = ++ctx->tick;
+    AFPS_CUDA(ctx, cudaGraphLaunch(it->second.exec, stream));
+    ctx->launches += it->second.kernels;
+    return AFPS_OK;
+}
+
+int load_tuning(afps_ctx* ctx, const std::string& path) {
+    std::ifstream f(path);
+    if (!f) return 0;
+    std::string key;
+    Variant v{};
+    int n = 0;
+    while (f >> key >> v.kind >> v.P >> v.W >> v.CS >> v.occ) {
+        if (afps::variant_supported(v)) {
+            ctx->tuned[key] = v;
+            ++n;
+        }
+    }
+    return n;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+int afps_create(afps_ctx** out, const afps_config* cfg) {
+    if (!out) return AFPS_ERR_INVALID_ARG;
+    *out = nullptr;
+    afps_ctx* ctx = new (std::nothrow) afps_ctx();
+    if (!ctx) return AFPS_ERR_NO_MEMORY;
+    if (cfg) {
+        ctx->device = cfg->device;
+        ctx->flags = cfg->flags;
+        if (cfg->timeout_ns > 0) ctx->timeout_ns = (uint64_t)cfg->timeout_ns;
+        if (cfg->tune_cache) ctx->tune_path = cfg->tune_cache;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ctx->device < 0 || ctx->device >= ndev) {
+        cudaGetLastError();
+        delete ctx;
+        return AFPS_ERR_CUDA;
+    }
+    DeviceGuard guard(ctx->device);
+    cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount,
+                                           ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_upload, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_done, ctx->capture);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_upload, ctx->capture);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        afps_destroy(ctx);
+        return AFPS_ERR_CUDA;
+    }
+    if (!ctx->tune_path.empty()) load_tuning(ctx, ctx->tune_path);
+    *out = ctx;
+    return AFPS_OK;
+}
+
+void afps_destroy(afps_ctx* ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard guard(ctx->device);
+        cudaDeviceSynchronize();
+        for (auto& kv : ctx->graphs) drop_graph(kv.second);
+        ctx->graphs.clear();
+        ctx->items.release();
+        ctx->counters.release();
+        ctx->xyz_stage.release();
+        ctx->out_stage.release();
+        ctx->h_items.release();
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
+        if (ctx->ev_upload) cudaEventDestroy(ctx->ev_upload);
+        if (ctx->capture) cudaStreamDestroy(ctx->capture);
+        cudaGetLastError();
+    }
+    delete ctx;
+}
+
+int afps_sample(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int32_t M,
+                int32_t npdu_window, int64_t start_idx, int32_t* d_out, void* stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    if (!d_xyz || !d_out)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sample: NULL device pointer");
+    if (reinterpret_cast<uintptr_t>(d_xyz) % 4 || reinterpret_cast<uintptr_t>(d_out) % 4)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sample: xyz and out must be 4-byte aligned");
+    CloudCheck chk = check_cloud(N, C, M, npdu_window, start_idx);
+    if (chk.code != AFPS_OK) return fail(ctx, chk.code, "afps_sample: " + chk.msg);
+    DeviceGuard guard(ctx->device);
+    const bool npdu = npdu_window > 0;
+    const Variant v = choose_variant(ctx, npdu, chk.n_max, chk.c_max, (size_t)M);
+    LaunchArgs a{};
+    a.xyz = d_xyz;
+    a.items = nullptr;
+    a.single.pt_off = 0;
+    a.single.out_off = 0;
+    a.single.N = (int32_t)N;
+    a.single.C = C;
+    a.single.M = M;
+    a.single.k = device_window(npdu_window);
+    a.single.start_r = chk.start_r;
+    a.n_items = M;
+    a.out = d_out;
+    a.counter = nullptr;
+    a.status = ctx->d_status;
+    a.timeout_ns = ctx->timeout_ns;
+    a.stall_copy = (ctx->flags & AFPS_FLAG_TEST_STALL_COPY) ? 1u : 0u;
+    cudaError_t e = afps::launch_sector(v, npdu, a, grid_for(v, (size_t)M),
+                                        static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "afps_sample launch");
+    ctx->launches += 1;
+    return AFPS_OK;
+}
+
+int afps_sample_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_off, int32_t B,
+                        const int32_t* h_C, const int32_t* h_M, const int32_t* h_win,
+                        const int64_t* h_start, const int64_t* h_out_off, int32_t* d_out,
+                        void* stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    DeviceGuard guard(ctx->device);
+    return batched_device(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, d_out,
+                          static_cast<cudaStream_t>(stream));
+}
+
+int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off,
+                             int32_t B, const int32_t* h_C, const int32_t* h_M,
+                             const int32_t* h_win, const int64_t* h_start,
+                             const int64_t* h_out_off, int32_t* h_out, void* stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    if (!h_xyz || !h_out || !h_pt_off || !h_out_off || B < 1)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sample_batched_host: NULL argument or B < 1");
+    if (h_pt_off[0] != 0 || h_out_off[0] != 0)
+        return fail(ctx, AFPS_ERR_INVALID_ARG,
+                    "afps_sample_batched_host: h_pt_off[0] and h_out_off[0] must be 0");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t xyz_bytes = (size_t)h_pt_off[B] * 3 * sizeof(float);
+    const size_t out_bytes = (size_t)h_out_off[B] * sizeof(int32_t);
+    AFPS_CUDA(ctx, ctx->xyz_stage.reserve(xyz_bytes));
+    AFPS_CUDA(ctx, ctx->out_stage.reserve(out_bytes));
+    AFPS_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_done, 0));
+    AFPS_CUDA(ctx, cudaMemcpyAsync(ctx->xyz_stage.p, h_xyz, xyz_bytes, cudaMemcpyHostToDevice, st));
+    int rc = batched_device(ctx, static_cast<const float*>(ctx->xyz_stage.p), h_pt_off, B, h_C,
+                            h_M, h_win, h_start, h_out_off,
+                            static_cast<int32_t*>(ctx->out_stage.p), st);
+    if (rc != AFPS_OK) {
+        cudaStreamSynchronize(st);
+        return rc;
+    }
+    AFPS_CUDA(ctx, cudaMemcpyAsync(h_out, ctx->out_stage.p, out_bytes, cudaMemcpyDeviceToHost, st));
+    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, st));
+    AFPS_CUDA(ctx, cudaStreamSynchronize(st));
+    return AFPS_OK;
+}
+
+int afps_gather_levels(afps_ctx* ctx, int32_t B, const int64_t* h_in_pt_off,
+                       const float* d_in_xyz, const int32_t* d_in_frame,
+                       const int64_t* h_sel_off, const int32_t* d_sel, float* d_out_xyz,
+                       int32_t* d_out_frame, int32_t* d_sel_frame, void* stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    if (B < 1 || !h_in_pt_off || !h_sel_off || !d_in_xyz || !d_sel || !d_out_xyz)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_gather_levels: NULL argument or B < 1");
+    std::vector<afps::GatherDesc> descs((size_t)B);
+    int32_t max_n = 1;
+    for (int32_t b = 0; b < B; ++b) {
+        const int64_t n = h_in_pt_off[b + 1] - h_in_pt_off[b];
+        const int64_t c = h_sel_off[b + 1] - h_sel_off[b];
+        if (n < 1 || n > afps::kGatherMaxPoints || c < 0 || c >= 65536 || h_in_pt_off[b] < 0 ||
+            h_sel_off[b] < 0) {
+            std::ostringstream os;
+            os << "afps_gather_levels: cloud " << b << " has " << n << " points and " << c
+               << " samples (need 1 <= n <= " << afps::kGatherMaxPoints << ", 0 <= c < 65536)";
+            return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
+        }
+        descs[b] = afps::GatherDesc{h_in_pt_off[b], h_sel_off[b], (int32_t)n, (int32_t)c};
+        max_n = std::max<int32_t>(max_n, (int32_t)n);
+    }
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = descs.size() * sizeof(afps::GatherDesc);
+    AFPS_CUDA(ctx, cudaEventSynchronize(ctx->ev_upload));
+    AFPS_CUDA(ctx, ctx->h_items.reserve(bytes));
+    AFPS_CUDA(ctx, ctx->items.reserve(bytes));
+    memcpy(ctx->h_items.p, descs.data(), bytes);
+    AFPS_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_done, 0));
+    AFPS_CUDA(ctx, cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, bytes, cudaMemcpyHostToDevice, st));
+    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_upload, st));
+    cudaError_t e = afps::launch_gather(static_cast<const afps::GatherDesc*>(ctx->items.p), B,
+                                        max_n, d_in_xyz, d_in_frame, d_sel, d_out_xyz,
+                                        d_out_frame, d_sel_frame, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
+    ctx->launches += 1;
+    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, st));
+    return AFPS_OK;
+}
+
+int afps_sync(afps_ctx* ctx, void* stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    DeviceGuard guard(ctx->device);
+    AFPS_CUDA(ctx, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int status = 0;
+    AFPS_CUDA(ctx, cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) {
+        AFPS_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+        return fail(ctx, AFPS_ERR_TIMEOUT,
+                    status == afps::DEV_TIMEOUT_STAGE
+                        ? "a stage-in bulk copy did not complete within the timeout"
+                        : "a bulk copy was still in flight after the drain timeout");
+    }
+    return AFPS_OK;
+}
+
+const char* afps_last_error(const afps_ctx* ctx) {
+    return ctx ? ctx->last_error.c_str() : "NULL context";
+}
+
+int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_off, int32_t B,
+                          const int32_t* h_C, const int32_t* h_M, const int32_t* h_win,
+                          const int64_t* h_start, const int64_t* h_out_off, int32_t* d_out,
+                          void* stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    if (!d_xyz || !d_out) return fail(ctx, AFPS_ERR_INVALID_ARG, "autotune: NULL device pointer");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BatchPlan plan;
+    int rc = build_plan(ctx, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, plan);
+    if (rc != AFPS_OK) return rc;
+    // upload the table once, then time each candidate class by class
+    rc = run_plan(ctx, plan, d_xyz, d_out, st);
+    if (rc != AFPS_OK) return rc;
+    cudaEvent_t e0, e1;
+    AFPS_CUDA(ctx, cudaEventCreate(&e0));
+    AFPS_CUDA(ctx, cudaEventCreate(&e1));
+    const ItemDesc* d_items = static_cast<const ItemDesc*>(ctx->items.p);
+    unsigned int* counters = static_cast<unsigned int*>(ctx->counters.p);
+    int tuned = 0;
+    for (size_t i = 0; i < plan.classes.size() && rc == AFPS_OK; ++i) {
+        ClassPlan& cp = plan.classes[i];
+        float best_ms = 1e30f;
+        Variant best = cp.v;
+        for (const Variant& v : candidate_variants(cp.n_max)) {
+            if (grid_for(v, cp.count) < 1 || afps::max_active_clusters(v) < 1) continue;
+            float ms_sum = 0.f;
+            bool ok = true;
+            for (int rep = 0; rep < 4 && ok; ++rep) {  // one warm-up, three timed
+                if (cudaEventRecord(e0, st) != cudaSuccess) ok = false;
+                if (ok && launch_class(ctx, v, cp.npdu, d_items + cp.first, cp.count,
+                                       counters + i, d_xyz, d_out, st) != AFPS_OK)
+                    ok = false;
+                if (ok && cudaEventRecord(e1, st) != cudaSuccess) ok = false;
+                float ms = 0.f;
+                if (ok && (cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    ok = false;
+                if (rep > 0) ms_sum += ms;
+            }
+            if (!ok) {
+                cudaGetLastError();
+                continue;
+            }
+            if (ms_sum < best_ms) {
+                best_ms = ms_sum;
+                best = v;
+            }
+        }
+        ctx->tuned[class_key(cp.npdu, cp.n_max, cp.c_max, cp.count)] = best;
+        cp.v = best;
+        ++tuned;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    clear_graphs(ctx);  // graphs captured earlier may use other variants
+    ctx->last_error.clear();
+    rc = run_plan(ctx, plan, d_xyz, d_out, st);
+    return rc == AFPS_OK ? tuned : rc;
+}
+
+int afps_save_tuning(afps_ctx* ctx, const char* path) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    const std::string p = path ? std::string(path) : ctx->tune_path;
+    if (p.empty()) return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_save_tuning: no path");
+    std::ofstream f(p);
+    if (!f) return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_save_tuning: cannot open " + p);
+    for (const auto& kv : ctx->tuned)
+        f << kv.first << ' ' << kv.second.kind << ' ' << kv.second.P << ' ' << kv.second.W << ' '
+          << kv.second.CS << ' ' << kv.second.occ << '\n';
+    return AFPS_OK;
+}
+
+int afps_describe_plan(afps_ctx* ctx, int64_t n_sector, int32_t c_sector, int32_t npdu_window,
+                       int32_t n_items, char* buf, int32_t buf_len) {
+    if (!ctx || !buf || buf_len < 1 || n_sector < 1 || n_sector > AFPS_MAX_SECTOR_POINTS ||
+        n_items < 1)
+        return AFPS_ERR_INVALID_ARG;
+    const Variant v =
+        choose_variant(ctx, npdu_window > 0, n_sector, c_sector, (size_t)n_items);
+    const std::string s = describe(v);
+    snprintf(buf, (size_t)buf_len, "%s", s.c_str());
+    return (int)s.size();
+}
+
+int64_t afps_launch_count(const afps_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,305 @@
+// afps_cta.cu -- one CTA, or one thread-block cluster of CS CTAs, per sector.
+//
+// Used for sectors larger than a warp holds in registers, and for plain FPS
+// (M = 1) on whole clouds: the cross-core argmax that Sec. III-B calls the
+// scaling limit of parallel FPS.  The sector is split into CS contiguous
+// chunks, one per CTA; each CTA stages its chunk into shared memory by bulk
+// copy and thread t keeps chunk points t + T i (i < P) in registers.
+//
+// One iteration = one barrier:
+//   1. update + local argmax in registers (all points, or the NPDU window);
+//   2. warp argmax (two redux.sync steps), then lanes 0..CS-1 of every warp
+//      write the warp's record {distance bits, ~index, x, y, z} into slot
+//      (rank, warp) of CTA `lane` -- a distributed-shared-memory store
+//      (st.shared::cluster) when CS > 1, an ordinary one otherwise;
+//   3. barrier: barrier.cluster arrive.release / wait.acquire (CS > 1) or
+//      bar.sync (CS == 1);
+//   4. every warp reduces the CS * W records itself (a lane per record, then
+//      redux.sync), which yields the next sample and its coordinates without
+//      a second barrier.  Records are double-buffered by exchange parity, so
+//      a record is never overwritten before every reader passed the barrier
+//      that follows its read.
+#include "afps_device.cuh"
+
+namespace afps {
+
+struct __align__(16) Rec {
+    uint32_t bits;  // distance bits of the candidate (>= +0)
+    uint32_t jinv;  // 0xffffffff - sector index: larger = lower index
+    float x, y, z;
+    uint32_t pad[3];
+};
+static_assert(sizeof(Rec) == 32, "Rec layout");
+
+template <int P, bool NPDU, bool CLUSTER>
+__global__ void __launch_bounds__(1024) afps_cta_kernel(const LaunchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = blockDim.x;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int w = tid >> 5;
+    const int W = T >> 5;
+    const int CS = CLUSTER ? (int)dev::cluster_nctarank() : 1;
+    const int rank = CLUSTER ? (int)dev::cluster_ctarank() : 0;
+    const int E = CS * W;
+
+    uint64_t* barp = reinterpret_cast<uint64_t*>(smem);
+    Rec* recs = reinterpret_cast<Rec*>(smem + 16);
+    unsigned char* buf = smem + 16 + 2 * E * sizeof(Rec);
+    const uint32_t bar = dev::smem_u32(barp);
+    if (tid == 0) {
+        dev::mbar_init(bar, 1);
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    if (CLUSTER) dev::cluster_sync();  // every peer is running before any DSMEM store
+
+    uint32_t phase = 0;
+    uint32_t xchg = 0;  // exchange counter: record buffer parity
+    const int group = CLUSTER ? (int)dev::cluster_id_x() : (int)blockIdx.x;
+    const int ngroups = CLUSTER ? (int)dev::ncluster_x() : (int)gridDim.x;
+
+    for (int item = group; item < a.n_items; item += ngroups) {
+        const ItemDesc d = dev::load_item(a, item);
+        const int n = d.n;
+        const int chunk = CLUSTER ? (n + CS - 1) / CS : n;
+        const int c0 = rank * chunk;
+        const int cn = max(0, min(n - c0, chunk));
+
+        // ---- stage-in of this CTA's chunk
+        dev::fence_proxy_async_smem();
+        __syncthreads();
+        bool bulk = false;
+        const float* pts = reinterpret_cast<const float*>(buf);
+        if (cn > 0)
+            pts = dev::stage_points(a.xyz + 3 * (d.src + c0), cn, buf, bar, tid == 0, tid, T,
+                                    &bulk, a.stall_copy != 0);
+        if (bulk) {
+            if (!dev::mbar_wait_bounded(bar, phase, a.timeout_ns)) {
+                dev::record_status(a.status, DEV_TIMEOUT_STAGE);
+                if (!dev::mbar_wait_bounded(bar, phase, a.timeout_ns))
+                    dev::record_status(a.status, DEV_TIMEOUT_DRAIN);
+            }
+            phase ^= 1u;
+        }
+        __syncthreads();
+
+        float x[P], y[P], z[P], D[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const int jl = tid + T * i;
+            if (jl < cn) {
+                x[i] = pts[3 * jl];
+                y[i] = pts[3 * jl + 1];
+                z[i] = pts[3 * jl + 2];
+                D[i] = 1e10f;
+            } else {  // padding: distance +0 stays +0 and loses every tie
+                x[i] = 0.f;
+                y[i] = 0.f;
+                z[i] = 0.f;
+                D[i] = 0.f;
+            }
+        }
+
+        int p = d.first;  // sector offset of the current sample
+        const float* gq = a.xyz + 3 * (d.src + p);
+        float qx = __ldg(gq), qy = __ldg(gq + 1), qz = __ldg(gq + 2);
+        int32_t* out = a.out + d.dst;
+        const int c = d.c;
+        const int kl = d.k >> 1;
+        const int kr = d.k - kl;
+        const bool emitter = (rank == 0) && (w == 0);
+        int obuf = 0;
+
+        for (int t = 0; t < c; ++t) {
+            if (emitter) {
+                if (lane == (t & 31)) obuf = d.lo + p;
+                if ((t & 31) == 31 || t == c - 1) {
+                    if (lane <= (t & 31)) out[(t & ~31) + lane] = obuf;
+                }
+            }
+            if (t == c - 1) break;
+
+            // 1. update + local argmax (chunk-local offsets)
+            const int wlo = p - kl - c0, whi = p + kr - c0;
+            float best = -1.f;
+            int bi = 0;
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                if (T * i < cn || i == 0) {  // CTA-uniform row test
+                    if (NPDU) {
+                        if (T * i + T - 1 >= wlo && T * i <= whi) {
+                            const int jl = tid + T * i;
+                            if (jl >= wlo && jl <= whi && jl < cn)
+                                D[i] = fminf(D[i], dev::sqdist(x[i], y[i], z[i], qx, qy, qz));
+                        }
+                    } else {
+                        D[i] = fminf(D[i], dev::sqdist(x[i], y[i], z[i], qx, qy, qz));
+                    }
+                    if (D[i] > best) {
+                        best = D[i];
+                        bi = i;
+                    }
+                }
+            }
+
+            // 2. warp argmax and record
+            const unsigned bits = __float_as_uint(best);
+            const unsigned m = __reduce_max_sync(dev::kFull, bits);
+            const unsigned cand = bits == m ? (unsigned)(tid + T * bi) : 0xffffffffu;
+            const unsigned jw = __reduce_min_sync(dev::kFull, cand);  // chunk-local
+            Rec* R = recs + (xchg & 1u) * E;
+            if (lane < CS) {
+                const float wx = pts[3 * jw], wy = pts[3 * jw + 1], wz = pts[3 * jw + 2];
+                const uint32_t jinv = 0xffffffffu - (uint32_t)(c0 + (int)jw);
+                if (CLUSTER) {
+                    const uint32_t slot = dev::smem_u32(&R[rank * W + w]);
+                    const uint32_t remote = dev::mapa(slot, (uint32_t)lane);
+                    dev::st_cluster_v4(remote, m, jinv, __float_as_uint(wx), __float_as_uint(wy));
+                    dev::st_cluster_v4(remote + 16, __float_as_uint(wz), 0u, 0u, 0u);
+                } else {
+                    uint4* s = reinterpret_cast<uint4*>(&R[w]);
+                    s[0] = make_uint4(m, jinv, __float_as_uint(wx), __float_as_uint(wy));
+                    s[1] = make_uint4(__float_as_uint(wz), 0u, 0u, 0u);
+                }
+            }
+
+            // 3. one barrier
+            if (CLUSTER)
+                dev::cluster_sync();
+            else
+                __syncthreads();
+
+            // 4. every warp reduces the E records
+            unsigned long long bkey = 0ull;
+            int be = 0;
+            for (int e = lane; e < E; e += 32) {
+                const uint2 kv = *reinterpret_cast<const uint2*>(&R[e]);
+                const unsigned long long key = ((unsigned long long)kv.x << 32) | kv.y;
+                if (key > bkey) {
+                    bkey = key;
+                    be = e;
+                }
+            }
+            const unsigned hi = (unsigned)(bkey >> 32), lo = (unsigned)bkey;
+            const unsigned mm = __reduce_max_sync(dev::kFull, hi);
+            const unsigned lo2 = __reduce_max_sync(dev::kFull, hi == mm ? lo : 0u);
+            const unsigned ball = __ballot_sync(dev::kFull, hi == mm && lo == lo2);
+            const int e_star = __shfl_sync(dev::kFull, be, __ffs(ball) - 1);
+            p = (int)(0xffffffffu - lo2);
+            qx = R[e_star].x;
+            qy = R[e_star].y;
+            qz = R[e_star].z;
+            ++xchg;
+        }
+    }
+    if (CLUSTER) dev::cluster_sync();  // no CTA leaves while a peer may still store to it
+}
+
+using SectorKernel = void (*)(LaunchArgs);
+SectorKernel warp_kernel_for(int P, bool npdu);
+
+static SectorKernel cta_kernel_for(int P, bool npdu, bool cluster) {
+#define AFPS_CTA_CASE(PP)                                                             \
+    case PP:                                                                          \
+        if (cluster)                                                                  \
+            return npdu ? afps_cta_kernel<PP, true, true> : afps_cta_kernel<PP, false, true>; \
+        return npdu ? afps_cta_kernel<PP, true, false> : afps_cta_kernel<PP, false, false>;
+    switch (P) {
+        AFPS_CTA_CASE(2)
+        AFPS_CTA_CASE(4)
+        AFPS_CTA_CASE(8)
+        default:
+            return nullptr;
+    }
+#undef AFPS_CTA_CASE
+}
+
+size_t variant_smem(const Variant& v) {
+    if (v.kind == KIND_WARP)
+        return 16 * ((8 * (size_t)v.W + 15) / 16) + (size_t)v.W * (12 * 32 * (size_t)v.P + 16);
+    return 16 + 2 * (size_t)v.CS * v.W * sizeof(Rec) + 12 * 32 * (size_t)v.W * v.P + 16;
+}
+
+bool variant_supported(const Variant& v) {
+    if (v.kind == KIND_WARP)
+        return warp_kernel_for(v.P, false) != nullptr && v.W >= 1 && v.W <= 8 && v.CS == 1;
+    if (v.kind != KIND_CTA) return false;
+    if (!cta_kernel_for(v.P, false, false)) return false;
+    if (v.W < 1 || v.W > 32 || v.CS < 1 || v.CS > 16) return false;
+    return variant_smem(v) <= 227 * 1024;
+}
+
+static SectorKernel kernel_for(const Variant& v, bool npdu) {
+    if (v.kind == KIND_WARP) return warp_kernel_for(v.P, npdu);
+    return cta_kernel_for(v.P, npdu, v.CS > 1);
+}
+
+static cudaError_t prepare(SectorKernel fn, const Variant& v, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (v.kind == KIND_CTA && v.CS > 8)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+cudaError_t launch_sector(const Variant& v, bool npdu, const LaunchArgs& a, int grid,
+                          cudaStream_t stream) {
+    if (!variant_supported(v) || grid < 1) return cudaErrorInvalidValue;
+    SectorKernel fn = kernel_for(v, npdu);
+    const size_t smem = variant_smem(v);
+    cudaError_t e = prepare(fn, v, smem);
+    if (e != cudaSuccess) return e;
+    if (v.kind == KIND_CTA && v.CS > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(grid * v.CS), 1, 1);
+        cfg.blockDim = dim3((unsigned)(32 * v.W), 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)v.CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, fn, a);
+    }
+    fn<<<grid, 32 * v.W, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+int max_active_clusters(const Variant& v) {
+    if (!variant_supported(v)) return 0;
+    SectorKernel fn = kernel_for(v, false);
+    const size_t smem = variant_smem(v);
+    if (prepare(fn, v, smem) != cudaSuccess) return 0;
+    if (v.kind == KIND_CTA && v.CS > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)v.CS, 1, 1);
+        cfg.blockDim = dim3((unsigned)(32 * v.W), 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)v.CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) return 0;
+        return n;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * v.W, smem) !=
+        cudaSuccess)
+        return 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm * sms;
+}
+
+}  // namespace afps

@@ -1,0 +1,200 @@
+// afps_device.cuh -- inline-PTX helpers for sm_103a: mbarriers, 1-D bulk
+// copies (TMA engine), cluster shared memory and barriers, bounded waits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "afps_internal.h"
+
+namespace afps {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------- mbarrier
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Make barrier initialisation visible to the async proxy (bulk copies) and to
+// the other CTAs of a cluster.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Order this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier to complete, giving up after
+// timeout_ns.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  uint64_t timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > timeout_ns) return false;
+    }
+}
+
+// 1-D bulk copy global -> shared, completion signalled on `bar` as bytes.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// ---------------------------------------------------------------- clusters
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t ncluster_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Address of the same shared-memory offset in CTA `rank` of this cluster.
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint32_t a, uint32_t b,
+                                              uint32_t c, uint32_t d) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a),
+                 "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+// Full cluster barrier with release/acquire ordering of shared::cluster memory.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- misc
+__device__ __forceinline__ void record_status(int* status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+// Squared distance with every product and sum rounded on its own (the
+// intrinsics are never contracted into fused multiply-adds).
+__device__ __forceinline__ float sqdist(float x, float y, float z, float qx, float qy,
+                                        float qz) {
+    const float dx = __fsub_rn(x, qx);
+    const float dy = __fsub_rn(y, qy);
+    const float dz = __fsub_rn(z, qz);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Item `i` of a launch: from the device table, or computed from the single
+// cloud's parameters with the sector rule floor(s*N/M), floor(s*C/M).
+__device__ __forceinline__ ItemDesc load_item(const LaunchArgs& a, int i) {
+    if (a.items) return a.items[i];
+    const SingleCloud& s = a.single;
+    const int64_t lo = (int64_t)i * s.N / s.M;
+    const int64_t hi = (int64_t)(i + 1) * s.N / s.M;
+    const int64_t o0 = (int64_t)i * s.C / s.M;
+    const int64_t o1 = (int64_t)(i + 1) * s.C / s.M;
+    ItemDesc d;
+    d.src = s.pt_off + lo;
+    d.dst = s.out_off + o0;
+    d.n = (int32_t)(hi - lo);
+    d.c = (int32_t)(o1 - o0);
+    d.first = s.start_r < d.n - 1 ? s.start_r : d.n - 1;
+    d.lo = (int32_t)lo;
+    d.k = s.k;
+    d.pad = 0;
+    return d;
+}
+
+// Stage n points (3 floats each, starting at g, 4-byte aligned) into the
+// 16-byte aligned shared buffer `buf` (capacity >= 12 n + 16 bytes).  The
+// 16-byte aligned interior goes by one bulk copy issued by `issuer` and
+// completing on `bar`; the unaligned head and tail (at most 3 floats each)
+// are plain loads spread over threads tid = 0 .. nthr-1.  `stall` (fault
+// injection) arms the barrier without issuing the copy.  Returns the shared
+// address of point 0 and sets *bulk when a bulk copy was issued (the caller
+// then waits for the barrier's phase and synchronises its threads).
+__device__ __forceinline__ float* stage_points(const float* g, int n, unsigned char* buf,
+                                               uint32_t bar, bool issuer, int tid, int nthr,
+                                               bool* bulk, bool stall = false) {
+    const uintptr_t A = reinterpret_cast<uintptr_t>(g);
+    const uintptr_t E = A + 12ull * (uint64_t)n;
+    const uintptr_t a0 = A & ~uintptr_t(15);
+    const uintptr_t i0 = (A + 15) & ~uintptr_t(15);
+    const uintptr_t i1 = E & ~uintptr_t(15);
+    float* s = reinterpret_cast<float*>(buf + (A - a0));
+    const bool use_bulk = i1 > i0;
+    int nh, ts;
+    if (use_bulk) {
+        nh = (int)((i0 - A) >> 2);
+        ts = (int)((i1 - A) >> 2);
+        if (issuer) {
+            mbar_arrive_expect_tx(bar, (uint32_t)(i1 - i0));
+            if (!stall)
+                bulk_g2s(smem_u32(buf + (i0 - a0)), reinterpret_cast<const void*>(i0),
+                         (uint32_t)(i1 - i0), bar);
+        }
+    } else {
+        nh = 3 * n;
+        ts = 3 * n;
+    }
+    for (int f = tid; f < nh; f += nthr) s[f] = __ldg(g + f);
+    for (int f = ts + tid; f < 3 * n; f += nthr) s[f] = __ldg(g + f);
+    *bulk = use_bulk;
+    return s;
+}
+
+}  // namespace dev
+}  // namespace afps

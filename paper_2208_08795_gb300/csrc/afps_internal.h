@@ -1,0 +1,95 @@
+// afps_internal.h -- types shared by the host runtime (afps_api.cu) and the
+// kernels (afps_kernels.cu, afps_gather.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace afps {
+
+// One work item: one sector of one cloud (Sec. III-B).  Built on the host for
+// batched calls; computed on the fly for a single cloud.
+struct ItemDesc {
+    int64_t src;    // global point index (into xyz) of the sector's first point
+    int64_t dst;    // global output slot of the sector's first sample
+    int32_t n;      // points in the sector
+    int32_t c;      // samples taken from the sector
+    int32_t first;  // sector offset of the first sample
+    int32_t lo;     // sector's first point relative to its cloud (added to outputs)
+    int32_t k;      // NPDU window (0 = off)
+    int32_t pad;
+};
+static_assert(sizeof(ItemDesc) == 40, "ItemDesc layout");
+
+// A single cloud described by its parameters; items are its M sectors.
+struct SingleCloud {
+    int64_t pt_off;
+    int64_t out_off;
+    int32_t N, C, M, k;
+    int32_t start_r;  // offset of start_idx inside its own sector
+    int32_t pad;
+};
+
+enum Kind : int32_t { KIND_WARP = 0, KIND_CTA = 1 };
+
+// A kernel variant.  KIND_WARP: one warp per item, W items per CTA.
+// KIND_CTA: one CTA (CS == 1) or one cluster of CS CTAs per item, W warps
+// per CTA.  P = points held per thread, in registers.
+struct Variant {
+    int32_t kind;
+    int32_t P;
+    int32_t W;
+    int32_t CS;
+    int32_t occ;  // CTAs (or clusters) per SM for persistent grids; 0 = one per item
+};
+
+struct LaunchArgs {
+    const float* xyz;
+    const ItemDesc* items;  // device table, or nullptr: use `single`
+    SingleCloud single;
+    int32_t n_items;
+    int32_t* out;
+    unsigned int* counter;  // dynamic work queue head (warp kind), or nullptr
+    int* status;            // device error word (first error wins)
+    uint64_t timeout_ns;
+    uint32_t stall_copy;    // fault injection: arm the barrier, issue no copy
+    uint32_t pad;
+};
+
+// Device error codes written to *status.
+enum DeviceStatus : int { DEV_OK = 0, DEV_TIMEOUT_STAGE = 1, DEV_TIMEOUT_DRAIN = 2 };
+
+// Points a variant can hold per item.
+inline int64_t variant_capacity(const Variant& v) {
+    return v.kind == KIND_WARP ? 32LL * v.P : 32LL * v.W * v.P * v.CS;
+}
+
+// Dynamic shared memory of a variant (bytes).
+size_t variant_smem(const Variant& v);
+
+// Whether the variant is compiled (P values, warp counts, cluster sizes).
+bool variant_supported(const Variant& v);
+
+// Launch the sector kernel for `v` on `stream`.  grid_hint = number of
+// CTAs (warp kind) or clusters (CTA kind) to launch; the kernels stride over
+// items when the grid is smaller than the item count.
+cudaError_t launch_sector(const Variant& v, bool npdu, const LaunchArgs& a, int grid_hint,
+                          cudaStream_t stream);
+
+// Largest number of clusters of the variant that can be co-resident, or 0.
+int max_active_clusters(const Variant& v);
+
+// Chained-level gather (afps_gather_levels).
+struct GatherDesc {
+    int64_t in_off;   // first point of the cloud in the input arrays
+    int64_t sel_off;  // first sample in d_sel / first output slot
+    int32_t n;        // points in the cloud
+    int32_t c;        // samples
+};
+cudaError_t launch_gather(const GatherDesc* d_descs, int32_t B, int32_t max_n,
+                          const float* in_xyz, const int32_t* in_frame, const int32_t* sel,
+                          float* out_xyz, int32_t* out_frame, int32_t* sel_frame,
+                          cudaStream_t stream);
+constexpr int32_t kGatherMaxPoints = 65536;
+
+}  // namespace afps

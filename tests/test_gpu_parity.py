@@ -1,0 +1,317 @@
+"""CUDA path vs the FP32 oracle, element by element (int32 indices must be
+bit-identical), on seeded synthetic clouds shaped like the paper's workloads
+and on the method's edge cases.  Every call goes through the C ABI."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2208_08795_gb300 import afps as B
+from paper_2208_08795_gb300 import build as build_mod
+from paper_2208_08795_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def k_rule(M):
+    """NPDU window per sector count (Sec. IV-D: k = 8 for M <= 8, 16 for M >= 16)."""
+    return 8 if M <= 8 else 16
+
+
+@pytest.fixture(scope="module")
+def S():
+    build_mod.build()
+    s = B.Sampler(0)
+    yield s
+    s.close()
+
+
+def gpu_one(S, pts, C, M, k, start=0):
+    x = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
+    out = S.sample(x, C, M, k, start)
+    S.sync()
+    return out.cpu().numpy()
+
+
+def gpu_batch(S, clouds, C, M, k, start=0):
+    xyz, off = synth.pack(clouds)
+    x = torch.from_numpy(xyz).cuda()
+    ba = B.BatchArgs(off, C, M, k, start)
+    out = S.sample_batched(x, ba)
+    S.sync()
+    o = out.cpu().numpy()
+    return [o[ba.out_off[b]:ba.out_off[b + 1]] for b in range(ba.B)], ba
+
+
+def assert_same(got, ref, what=""):
+    got, ref = np.asarray(got), np.asarray(ref)
+    assert got.shape == ref.shape, (what, got.shape, ref.shape)
+    if not np.array_equal(got, ref):
+        i = int(np.nonzero(got != ref)[0][0])
+        raise AssertionError(f"{what}: first mismatch at {i}: gpu {got[i]} oracle {ref[i]}")
+
+
+# --------------------------------------------------------------- workloads
+@pytest.mark.parametrize("M,k", [(1, 0), (4, 0), (4, 8), (32, 16)])
+def test_sphere_torus_2048(S, M, k):
+    P = synth.sphere_torus_cloud(0)
+    assert_same(gpu_one(S, P, 512, M, k), oracle.afps(P, 512, M, k), f"M={M} k={k}")
+
+
+@pytest.fixture(scope="module")
+def objects():
+    return synth.object_batch(1, 32, 2048)
+
+
+@pytest.mark.parametrize("M", [1, 4, 16, 32])
+@pytest.mark.parametrize("npdu", [False, True])
+def test_object_batch_32x2048(S, objects, M, npdu):
+    k = k_rule(M) if npdu else 0
+    got, _ = gpu_batch(S, objects, 512, M, k)
+    for b, P in enumerate(objects):
+        assert_same(got[b], oracle.afps(P, 512, M, k), f"cloud {b} M={M} k={k}")
+
+
+@pytest.mark.parametrize("N", [8192, 16384, 32768])
+@pytest.mark.parametrize("M,npdu", [(1, False), (1, True), (8, True), (32, True), (64, True),
+                                    (128, True)])
+def test_slab_large(S, N, M, npdu):
+    P = synth.slab_cloud(2, N)
+    k = k_rule(M) if npdu else 0
+    assert_same(gpu_one(S, P, N // 4, M, k), oracle.afps(P, N // 4, M, k), f"N={N} M={M} k={k}")
+
+
+@pytest.mark.parametrize("npdu", [False, True])
+def test_ragged_batch_256(S, npdu):
+    clouds, Cs, Ms = synth.ragged_batch(3, 256)
+    ks = [k_rule(m) if npdu else 0 for m in Ms]
+    got, _ = gpu_batch(S, clouds, Cs, Ms, ks)
+    for b, P in enumerate(clouds):
+        assert_same(got[b], oracle.afps(P, Cs[b], Ms[b], ks[b]), f"cloud {b}")
+
+
+# --------------------------------------------------------------- edge cases
+EDGE = [
+    (1, 1, 1, 0, 0), (2, 2, 1, 0, 1), (2, 2, 2, 3, 1), (5, 3, 1, 1, 4), (31, 31, 1, 0, 30),
+    (33, 10, 3, 0, 32), (100, 100, 7, 0, 0), (100, 100, 7, 4, 99), (64, 64, 64, 0, 0),
+    (300, 40, 40, 2, 150), (513, 100, 1, 0, 0), (513, 100, 1, 5, 512), (1000, 250, 3, 1, 999),
+    (4097, 600, 1, 0, 17), (8193, 300, 1, 0, 8192), (5000, 1000, 4, 7, 2500),
+    (2048, 512, 16, 3000, 0), (777, 300, 13, 0, 5), (1030, 1030, 2, 0, 0),
+]
+
+
+@pytest.mark.parametrize("N,C,M,k,start", EDGE)
+def test_edge_cases(S, N, C, M, k, start):
+    P = synth.uniform_cloud(1000 + N + M + k, N)
+    assert_same(gpu_one(S, P, C, M, k, start), oracle.afps(P, C, M, k, start), str((N, C, M, k, start)))
+
+
+def test_max_sector(S):
+    N = B.AFPS_MAX_SECTOR_POINTS
+    P = synth.slab_cloud(9, N)
+    assert_same(gpu_one(S, P, 48, 1, 0, 12345), oracle.afps(P, 48, 1, 0, 12345), "max sector")
+
+
+def test_unsorted_and_duplicates(S):
+    P = synth.uniform_cloud(5, 700, axis=None)
+    assert_same(gpu_one(S, P, 200, 5, 6, 3), oracle.afps(P, 200, 5, 6, 3), "unsorted")
+    Q = np.repeat(synth.uniform_cloud(6, 40), 3, axis=0)  # every point three times
+    assert_same(gpu_one(S, Q, 120, 2, 0, 0), oracle.afps(Q, 120, 2, 0, 0), "duplicates")
+    Z = np.zeros((96, 3), dtype=np.float32)  # all distances zero
+    assert_same(gpu_one(S, Z, 96, 3, 0, 5), oracle.afps(Z, 96, 3, 0, 5), "all equal")
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3, 5])
+def test_unaligned_base(S, shift):
+    """Clouds starting at every 4-byte phase exercise the bulk copy's head and
+    tail handling."""
+    N = 3000
+    P = synth.uniform_cloud(77, N)
+    buf = torch.zeros(3 * N + 16, dtype=torch.float32, device="cuda")
+    view = buf[shift:shift + 3 * N].view(N, 3)
+    view.copy_(torch.from_numpy(P).cuda())
+    for (C, M, k) in ((300, 1, 0), (300, 10, 0), (600, 30, 16)):
+        out = S.sample(view, C, M, k, 7)
+        S.sync()
+        assert_same(out.cpu().numpy(), oracle.afps(P, C, M, k, 7), f"shift={shift} M={M}")
+
+
+def test_errors(S):
+    P = torch.from_numpy(synth.uniform_cloud(1, 64)).cuda()
+    bad = [(0, 1, 0, 0, B.AFPS_ERR_INVALID_ARG), (65, 1, 0, 0, B.AFPS_ERR_INVALID_ARG),
+           (8, 9, 0, 0, B.AFPS_ERR_INVALID_ARG), (8, 2, -1, 0, B.AFPS_ERR_INVALID_ARG),
+           (8, 2, 0, 64, B.AFPS_ERR_INVALID_ARG)]
+    for C, M, k, start, code in bad:
+        with pytest.raises(B.AfpsError) as ei:
+            S.sample(P, C, M, k, start, out=torch.empty(max(C, 1), dtype=torch.int32, device="cuda"))
+        assert ei.value.code == code
+    Q = torch.from_numpy(synth.uniform_cloud(2, 8)).cuda()
+    with pytest.raises(B.AfpsError) as ei:
+        S.sample(Q, 7, 5, 0, 0)
+    assert ei.value.code == B.AFPS_ERR_SECTOR_TOO_SMALL
+    big = torch.zeros((B.AFPS_MAX_SECTOR_POINTS + 1, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(B.AfpsError) as ei:
+        S.sample(big, 4, 1, 0, 0)
+    assert ei.value.code == B.AFPS_ERR_UNSUPPORTED
+    S.sync()
+
+
+# --------------------------------------------------------------- variants
+def pow2(n):
+    b = 1
+    while b < n:
+        b <<= 1
+    return b
+
+
+VARIANTS = [  # (N, C, M, k, kind, P, W, CS)
+    (1024, 256, 4, 0, 1, 2, 4, 1), (1024, 256, 4, 0, 1, 4, 2, 1), (1024, 256, 4, 0, 1, 8, 1, 1),
+    (1024, 256, 4, 0, 1, 2, 2, 2), (1024, 256, 4, 0, 1, 2, 1, 4), (1024, 256, 4, 8, 1, 2, 2, 2),
+    (4096, 512, 1, 0, 1, 4, 2, 16), (4096, 512, 1, 0, 1, 8, 4, 4), (4096, 512, 1, 16, 1, 8, 2, 8),
+    (10000, 700, 1, 0, 1, 8, 32, 2), (10000, 700, 1, 0, 1, 4, 8, 10), (10000, 700, 1, 5, 1, 8, 16, 3),
+    (3000, 300, 10, 0, 0, 12, 1, 1), (3000, 300, 10, 0, 0, 16, 8, 1), (3000, 300, 10, 9, 0, 12, 2, 1),
+    (640, 640, 20, 0, 0, 1, 8, 1), (640, 640, 20, 0, 0, 2, 4, 1), (640, 640, 20, 16, 0, 1, 8, 1),
+    (2000, 400, 100, 4, 0, 1, 4, 1), (2000, 500, 8, 0, 0, 8, 8, 1), (2000, 500, 8, 12, 0, 8, 4, 1),
+]
+
+
+@pytest.mark.parametrize("N,C,M,k,kind,Pp,W,CS", VARIANTS)
+def test_forced_variant(tmp_path, N, C, M, k, kind, Pp, W, CS):
+    """Pin one kernel variant through the tuning cache and compare."""
+    build_mod.build()
+    n_max = -(-N // M)
+    c_max = -(-C // M)
+    key = f"{'npdu' if k else 'full'}:n{n_max}:c{c_max}:i{pow2(M)}"
+    path = tmp_path / "tune.txt"
+    path.write_text(f"{key} {kind} {Pp} {W} {CS} 0\n")
+    s = B.Sampler(0, tune_cache=str(path))
+    try:
+        desc = s.describe_plan(n_max, c_max, k, M)
+        if kind == 0:
+            want = f"warp P={Pp} W={W}"
+        elif CS > 1:
+            want = f"cluster P={Pp} W={W} CS={CS}"
+        else:
+            want = f"cta P={Pp} W={W}"
+        P = synth.uniform_cloud(N + 31 * M + k, N)
+        x = torch.from_numpy(P).cuda()
+        out = s.sample(x, C, M, k, 1)
+        s.sync()
+        assert_same(out.cpu().numpy(), oracle.afps(P, C, M, k, 1), f"{key} -> {desc}")
+        assert desc == want, (desc, want)
+    finally:
+        s.close()
+
+
+# --------------------------------------------------------------- batching
+def test_graph_replay_and_launch_count(objects):
+    build_mod.build()
+    s = B.Sampler(0, graph=True)
+    try:
+        xyz, off = synth.pack(objects)
+        x = torch.from_numpy(xyz).cuda()
+        Ms = [32] * 16 + [4] * 8 + [1] * 8  # three launch classes in one graph
+        ks = [16] * 16 + [0] * 8 + [0] * 8
+        ba = B.BatchArgs(off, 512, Ms, ks, 0)
+        out = torch.full((ba.total_out,), -1, dtype=torch.int32, device="cuda")
+        s.sample_batched(x, ba, out=out)
+        n0 = s.launch_count
+        for _ in range(3):
+            out.fill_(-1)
+            s.sample_batched(x, ba, out=out)
+        s.sync()
+        assert s.launch_count - n0 == 3 * 3  # three classes, three replays
+        o = out.cpu().numpy()
+        for b, P in enumerate(objects):
+            assert_same(o[ba.out_off[b]:ba.out_off[b + 1]], oracle.afps(P, 512, Ms[b], ks[b]), f"cloud {b}")
+    finally:
+        s.close()
+
+
+def test_host_buffers_match_device(S, objects):
+    xyz, off = synth.pack(objects[:8])
+    ba = B.BatchArgs(off, 512, 16, 16, 0)
+    h_xyz = torch.from_numpy(xyz).pin_memory().numpy()
+    h_out = torch.full((ba.total_out,), -1, dtype=torch.int32).pin_memory().numpy()
+    S.sample_batched_host(h_xyz, ba, h_out)
+    for b, P in enumerate(objects[:8]):
+        assert_same(h_out[ba.out_off[b]:ba.out_off[b + 1]], oracle.afps(P, 512, 16, 16), f"cloud {b}")
+
+
+def test_same_alone_and_in_a_mix(S, objects):
+    """Each cloud's result is the same alone and inside a mixed batch."""
+    clouds = objects[:6] + [synth.slab_cloud(4, 9000), synth.uniform_cloud(8, 300)]
+    Cs = [512] * 6 + [2000, 100]
+    Ms = [1, 4, 16, 32, 2, 8, 1, 3]
+    ks = [0, 8, 16, 16, 0, 0, 0, 5]
+    mixed, _ = gpu_batch(S, clouds, Cs, Ms, ks, 0)
+    for b, P in enumerate(clouds):
+        alone = gpu_one(S, P, Cs[b], Ms[b], ks[b], 0)
+        assert_same(mixed[b], alone, f"cloud {b}")
+        assert_same(alone, oracle.afps(P, Cs[b], Ms[b], ks[b]), f"cloud {b}")
+
+
+def test_autotune(objects, tmp_path):
+    build_mod.build()
+    s = B.Sampler(0, tune_cache=str(tmp_path / "t.txt"))
+    try:
+        xyz, off = synth.pack(objects)
+        x = torch.from_numpy(xyz).cuda()
+        ba = B.BatchArgs(off, 512, 32, 16, 0)
+        out = torch.full((ba.total_out,), -1, dtype=torch.int32, device="cuda")
+        assert s.autotune_batched(x, ba, out) >= 1
+        s.sync()
+        assert B.afps_save_tuning(s.ctx, None) == 0
+        assert (tmp_path / "t.txt").read_text().strip()
+        o = out.cpu().numpy()
+        for b, P in enumerate(objects):
+            assert_same(o[ba.out_off[b]:ba.out_off[b + 1]], oracle.afps(P, 512, 32, 16), f"cloud {b}")
+    finally:
+        s.close()
+
+
+# --------------------------------------------------------------- failure detection
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """Fault injection on the host side of the barrier: the copy is never
+    issued, every bounded wait runs out after 1 ms, the kernel returns, the
+    status word says so, and the GPU and a fresh call still work."""
+    build_mod.build()
+    P = synth.uniform_cloud(3, 2048)
+    x = torch.from_numpy(P).cuda()
+    s = B.Sampler(0, timeout_ns=1_000_000, flags=B.AFPS_FLAG_TEST_STALL_COPY)
+    try:
+        for (M, k) in ((32, 16), (1, 0)):
+            s.sample(x, 64, M, k, 0)
+            with pytest.raises(B.AfpsError) as ei:
+                s.sync()
+            assert ei.value.code == B.AFPS_ERR_TIMEOUT
+            s.sync()  # cleared
+    finally:
+        s.close()
+    s2 = B.Sampler(0)
+    try:
+        assert_same(gpu_one(s2, P, 512, 4, 0), oracle.afps(P, 512, 4, 0), "after timeout")
+    finally:
+        s2.close()
+
+
+# --------------------------------------------------------------- chained levels
+def test_chained_levels_lidar(S):
+    frame = synth.lidar_frame(5)
+    levels = [16384, 4096, 1024, 256]
+    ref = oracle.chain(frame, levels, 32, 16)
+    cloud = torch.from_numpy(frame).cuda()
+    fidx = None
+    for L, C in enumerate(levels):
+        n = cloud.shape[0]
+        sel = S.sample(cloud, C, 32, 16, 0)
+        nxt = torch.empty((C, 3), dtype=torch.float32, device="cuda")
+        nfr = torch.empty(C, dtype=torch.int32, device="cuda")
+        sfr = torch.empty(C, dtype=torch.int32, device="cuda")
+        S.gather_levels([0, n], cloud, fidx, [0, C], sel, nxt, nfr, sfr)
+        S.sync()
+        assert_same(sfr.cpu().numpy(), ref[L], f"level {L}")
+        assert np.all(np.diff(nfr.cpu().numpy()) > 0)
+        cloud, fidx = nxt, nfr
