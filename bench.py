@@ -201,6 +201,12 @@ def time_e2e(sampler, h_xyz, ba, h_out, steps: int, warmup: int):
     return ts
 
 
+def _json_default(o):
+    if isinstance(o, np.generic):
+        return o.item()
+    raise TypeError(f"not JSON serializable: {type(o).__name__}")
+
+
 def pct(xs, q):
     return float(np.percentile(np.asarray(xs), q))
 
@@ -220,7 +226,7 @@ def npdu_work(out_idx, ba, k):
             compares += (o1 - o0 - 1) * n
             for p in idx[o0:o1 - 1] - lo:
                 if k > 0:
-                    evals += min(n - 1, p + (k - k // 2)) - max(0, p - k // 2) + 1
+                    evals += int(min(n - 1, p + (k - k // 2)) - max(0, p - k // 2) + 1)
                 else:
                     evals += n
     return evals, compares
@@ -239,7 +245,7 @@ def kernel_source_hash() -> str:
 # DRAM traffic of the headline kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum per launch), valid only for the kernel sources it was
 # taken on (their hash); otherwise reported as null.
-NCU_TRAFFIC = {"source_hash": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"source_hash": "ac0e0e7be1594cde", "bytes_per_launch": 841216}
 
 
 # ------------------------------------------------------------------ arms
@@ -270,7 +276,7 @@ def run_reference(args, rank: int, world: int) -> int:
                                    f"threads over clouds"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
+    print(json.dumps(line, default=_json_default))
     return 0
 
 
@@ -393,11 +399,20 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         same = sum(int(np.array_equal(head_out[ba.out_off[b]:ba.out_off[b + 1]], ref[b]))
                    for b in range(B_CLOUDS))
         line["parity"] = f"{same}/{B_CLOUDS} clouds bit-exact vs the FP32 oracle"
+        import oracle
+        agree, drel = [], []
+        for b, P in enumerate(clouds):
+            r64 = oracle.afps(P, C_SAMPLES, M_SECTORS, K_WINDOW, 0, precision="f64")
+            agree.append(float(np.mean(r64 == ref[b])))
+            R32, R64 = oracle.coverage_radius(P, ref[b]), oracle.coverage_radius(P, r64)
+            drel.append(abs(R32 - R64) / R64)
+        line["fp64_oracle"] = {"index_agreement": float(np.mean(agree)),
+                               "coverage_radius_rel_diff_max": float(max(drel))}
     else:
         line["cpu_baseline"] = None
     sampler.close()
     if rank == 0:
-        print(json.dumps(line))
+        print(json.dumps(line, default=_json_default))
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -257,9 +257,10 @@ class Sampler:
                                 out.data_ptr(), self._stream(stream)))
         return out
 
-    def sample_batched(self, xyz, pt_off, C, M, k, start=0, out_off=None, out=None,
-                       stream=None):
-        """Ragged batch: cloud b is xyz[pt_off[b]:pt_off[b+1]]."""
+    def sample_batched(self, xyz, pt_off, C=None, M=None, k=None, start=0, out_off=None,
+                       out=None, stream=None):
+        """Ragged batch: cloud b is xyz[pt_off[b]:pt_off[b+1]]; pt_off may be a
+        prepared :class:`BatchArgs` (then C, M, k, start, out_off are unused)."""
         import torch
         xyz = self._points(xyz)
         ba = pt_off if isinstance(pt_off, BatchArgs) else BatchArgs(pt_off, C, M, k, start, out_off)

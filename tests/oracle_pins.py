@@ -289,6 +289,19 @@ def pin_coverage_radius(L):
     assert abs(got - ref) <= 1e-12 * ref, (got, ref)
 
 
+def pin_chain_grid(L):
+    """Chained levels on the grid 0..64: FPS with 2^l + 1 samples takes the
+    multiples of 2^(6-l); sorted ascending they form the next, coarser grid,
+    whose FPS order is the closed form scaled by the spacing."""
+    P = synth.grid_1d(6)
+    levels = [33, 17, 9, 5]
+    got = oracle.chain(P, levels, 1, 0, library=L)
+    for j, C in enumerate(levels):
+        m = 5 - j  # the level-j cloud is a grid 0..2^(m+1) with spacing 2^j
+        expect = [(1 << j) * v for v in grid_closed_form(m + 1)][:C]
+        assert list(got[j]) == expect, (j, list(got[j]), expect)
+
+
 PINS = [pin_golden, pin_grid_closed_form, pin_npdu_stride_law, pin_brute_force,
         pin_brute_force_f64, pin_reductions, pin_invariants, pin_every_point, pin_metamorphic,
-        pin_errors, pin_coverage_radius]
+        pin_errors, pin_coverage_radius, pin_chain_grid]
