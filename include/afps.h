@@ -186,6 +186,39 @@ int afps_describe_plan(afps_ctx* ctx, int64_t n_sector, int32_t c_sector,
 /* Number of kernel launches issued by this context since creation. */
 int64_t afps_launch_count(const afps_ctx* ctx);
 
+/*
+ * afps_sample_batched for callers that cannot allocate.  The paper has no
+ * counterpart: this is a deployment variant of the batched call above.
+ *
+ * Who needs it: code that may not call cudaMalloc (a plugin inside a host
+ * framework that owns all device memory, a process under a fixed memory
+ * budget or pool, a real-time loop that must not take allocator locks or
+ * cause the implicit synchronisation an allocation can bring).  It takes no
+ * context and allocates nothing, on the device or on the host heap.
+ *
+ * Arguments, layouts and results are those of afps_sample_batched; the
+ * caller passes the input points and the output buffer.  The work-item table
+ * (40 bytes per sector) lives in a static device array of
+ * AFPS_NOALLOC_MAX_ITEMS items (about 320 KB) that every GPU loading the
+ * library holds until the process exits.  A batch with more sectors than
+ * that returns AFPS_ERR_SCRATCH_TOO_SMALL and launches nothing.
+ *
+ * It runs on the current device.  The first call on a device looks up the
+ * array's device address there (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's table: calls whose work overlaps on the GPU (different streams
+ * without ordering, or several host threads) race on it.  Calls on one
+ * stream are ordered and safe.  Device-side wait timeouts are recorded in the
+ * array's status word, which nothing reads back; use afps_sample_batched
+ * with afps_sync where such reports matter.
+ */
+#define AFPS_NOALLOC_MAX_ITEMS 8192
+#define AFPS_ERR_SCRATCH_TOO_SMALL (-7) /* batch exceeds AFPS_NOALLOC_MAX_ITEMS sectors */
+int afps_sample_batched_noalloc(const float* d_xyz, const int64_t* h_pt_off, int32_t B,
+                                const int32_t* h_C, const int32_t* h_M, const int32_t* h_win,
+                                const int64_t* h_start, const int64_t* h_out_off,
+                                int32_t* d_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

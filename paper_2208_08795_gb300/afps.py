@@ -25,6 +25,8 @@ AFPS_ERR_NO_MEMORY = -3
 AFPS_ERR_TIMEOUT = -4
 AFPS_ERR_CUDA = -5
 AFPS_ERR_UNSUPPORTED = -6
+AFPS_ERR_SCRATCH_TOO_SMALL = -7
+AFPS_NOALLOC_MAX_ITEMS = 8192
 AFPS_MAX_SECTOR_POINTS = 131072
 AFPS_FLAG_GRAPH = 1
 AFPS_FLAG_AUTOTUNE = 2
@@ -34,7 +36,7 @@ AFPS_FLAG_TEST_STALL_COPY = 0x100
 EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
            "afps_sample_batched_host", "afps_gather_levels", "afps_sync",
            "afps_last_error", "afps_autotune_batched", "afps_save_tuning",
-           "afps_describe_plan", "afps_launch_count")
+           "afps_describe_plan", "afps_launch_count", "afps_sample_batched_noalloc")
 
 
 class AfpsLibraryError(RuntimeError):
@@ -81,6 +83,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.afps_describe_plan.restype = ctypes.c_int
     L.afps_launch_count.argtypes = [vp]
     L.afps_launch_count.restype = ctypes.c_int64
+    L.afps_sample_batched_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.afps_sample_batched_noalloc.restype = ctypes.c_int
     return L
 
 
@@ -168,6 +172,13 @@ def afps_describe_plan(ctx, n_sector: int, c_sector: int, npdu_window: int,
 
 def afps_launch_count(ctx) -> int:
     return load().afps_launch_count(ctx)
+
+
+def afps_sample_batched_noalloc(d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
+                                d_out, stream) -> int:
+    """The batched call for callers that cannot allocate (no context)."""
+    return load().afps_sample_batched_noalloc(d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start,
+                                              h_out_off, d_out, stream)
 
 
 # ---------------------------------------------------------------- helpers
