@@ -201,7 +201,7 @@ CloudCheck check_cloud(int64_t N, int32_t C, int32_t M, int32_t k, int64_t start
 
 // ---------------------------------------------------------------- variants
 const int kWarpP[] = {1, 2, 3, 4, 6, 8, 12, 16};
-const int kCtaP[] = {2, 4, 8};
+const int kCtaP[] = {2, 4, 8, 16};
 
 // Default variant for sectors of up to n_max points.
 Variant default_variant(int64_t n_max) {
@@ -219,6 +219,7 @@ Variant default_variant(int64_t n_max) {
         return v;
     }
     v.kind = afps::KIND_CTA;
+    v.skip = 1;
     if (n_max <= 4096) {
         v.P = 4;
         v.W = (int)((n_max + 127) / 128);
@@ -239,30 +240,39 @@ Variant default_variant(int64_t n_max) {
     return v;
 }
 
-// Every variant the autotuner tries for sectors of up to n_max points.
-std::vector<Variant> candidate_variants(int64_t n_max) {
+// Every variant the autotuner tries for sectors of up to n_max points (with
+// and without the NPDU row skip when the class uses NPDU).
+std::vector<Variant> candidate_variants(int64_t n_max, bool npdu) {
     std::vector<Variant> out;
     if (n_max <= 512) {
         for (int P : kWarpP) {
             if (32LL * P < n_max) continue;
-            for (int W : {2, 4, 8}) out.push_back(Variant{afps::KIND_WARP, P, W, 1, 0});
+            for (int W : {2, 4, 8}) out.push_back(Variant{afps::KIND_WARP, P, W, 1, 0, 0});
             break;  // the smallest P that fits: larger P only adds padding
         }
     }
     for (int P : kCtaP) {
         const int64_t W = (n_max + 32LL * P - 1) / (32LL * P);
-        if (W >= 2 && W <= 32) out.push_back(Variant{afps::KIND_CTA, P, (int)W, 1, 0});
+        if (W >= 1 && W <= 32 && n_max > 64)
+            out.push_back(Variant{afps::KIND_CTA, P, (int)W, 1, 0, 0});
     }
     if (n_max > 2048) {
-        for (int P : {4, 8})
-            for (int W : {8, 16, 32}) {
+        for (int P : {4, 8, 16})
+            for (int W : {4, 8, 16, 32}) {
                 const int64_t CS = (n_max + 32LL * W * P - 1) / (32LL * W * P);
-                if (CS >= 2 && CS <= 16) out.push_back(Variant{afps::KIND_CTA, P, W, (int)CS, 0});
+                if (CS >= 2 && CS <= 16) out.push_back(Variant{afps::KIND_CTA, P, W, (int)CS, 0, 0});
             }
     }
     std::vector<Variant> ok;
-    for (const Variant& v : out)
-        if (afps::variant_supported(v) && afps::variant_capacity(v) >= n_max) ok.push_back(v);
+    for (const Variant& v : out) {
+        if (!afps::variant_supported(v) || afps::variant_capacity(v) < n_max) continue;
+        ok.push_back(v);
+        if (npdu) {
+            Variant s = v;
+            s.skip = 1;
+            ok.push_back(s);
+        }
+    }
     return ok;
 }
 
@@ -291,6 +301,7 @@ std::string describe(const Variant& v) {
         os << "cluster P=" << v.P << " W=" << v.W << " CS=" << v.CS;
     else
         os << "cta P=" << v.P << " W=" << v.W;
+    if (v.skip) os << " skip";
     return os.str();
 }
 
@@ -335,6 +346,7 @@ int launch_class(afps_ctx* ctx, const Variant& v, bool npdu, const ItemDesc* d_i
     a.status = ctx->d_status;
     a.timeout_ns = ctx->timeout_ns;
     a.stall_copy = (ctx->flags & AFPS_FLAG_TEST_STALL_COPY) ? 1u : 0u;
+    a.npdu_skip = v.skip ? 1u : 0u;
     if (a.counter) AFPS_CUDA(ctx, cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), stream));
     cudaError_t e = afps::launch_sector(v, npdu, a, grid, stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sector kernel launch");
@@ -554,13 +566,18 @@ int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int
     return AFPS_OK;
 }
 
+// Tuning cache: one line per class, "key kind P W CS occ [skip]".
 int load_tuning(afps_ctx* ctx, const std::string& path) {
     std::ifstream f(path);
     if (!f) return 0;
-    std::string key;
-    Variant v{};
+    std::string line;
     int n = 0;
-    while (f >> key >> v.kind >> v.P >> v.W >> v.CS >> v.occ) {
+    while (std::getline(f, line)) {
+        std::istringstream is(line);
+        std::string key;
+        Variant v{};
+        if (!(is >> key >> v.kind >> v.P >> v.W >> v.CS >> v.occ)) continue;
+        if (!(is >> v.skip)) v.skip = 0;
         if (afps::variant_supported(v)) {
             ctx->tuned[key] = v;
             ++n;
@@ -660,6 +677,7 @@ int afps_sample(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int32_t
     a.status = ctx->d_status;
     a.timeout_ns = ctx->timeout_ns;
     a.stall_copy = (ctx->flags & AFPS_FLAG_TEST_STALL_COPY) ? 1u : 0u;
+    a.npdu_skip = v.skip ? 1u : 0u;
     cudaError_t e = afps::launch_sector(v, npdu, a, grid_for(v, (size_t)M),
                                         static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "afps_sample launch");
@@ -793,7 +811,7 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
         ClassPlan& cp = plan.classes[i];
         float best_ms = 1e30f;
         Variant best = cp.v;
-        for (const Variant& v : candidate_variants(cp.n_max)) {
+        for (const Variant& v : candidate_variants(cp.n_max, cp.npdu)) {
             if (grid_for(v, cp.count) < 1 || afps::max_active_clusters(v) < 1) continue;
             float ms_sum = 0.f;
             bool ok = true;
@@ -838,7 +856,7 @@ int afps_save_tuning(afps_ctx* ctx, const char* path) {
     if (!f) return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_save_tuning: cannot open " + p);
     for (const auto& kv : ctx->tuned)
         f << kv.first << ' ' << kv.second.kind << ' ' << kv.second.P << ' ' << kv.second.W << ' '
-          << kv.second.CS << ' ' << kv.second.occ << '\n';
+          << kv.second.CS << ' ' << kv.second.occ << ' ' << kv.second.skip << '\n';
     return AFPS_OK;
 }
 

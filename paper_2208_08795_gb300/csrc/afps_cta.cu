@@ -8,17 +8,20 @@
 //
 // One iteration = one barrier:
 //   1. update + local argmax in registers (all points, or the NPDU window);
-//   2. warp argmax (two redux.sync steps), then lanes 0..CS-1 of every warp
-//      write the warp's record {distance bits, ~index, x, y, z} into slot
-//      (rank, warp) of CTA `lane` -- a distributed-shared-memory store
-//      (st.shared::cluster) when CS > 1, an ordinary one otherwise;
+//   2. warp argmax (two redux.sync steps), then the warp's record {distance
+//      bits, ~index} goes to slot (rank, warp): with CS > 1, lanes 0..CS-1
+//      store it with the point's x, y, z into CTA `lane` by a distributed-
+//      shared-memory store (st.shared::cluster); with CS == 1 lane 0 stores
+//      the 8-byte key;
 //   3. barrier: barrier.cluster arrive.release / wait.acquire (CS > 1) or
 //      bar.sync (CS == 1);
 //   4. every warp reduces the CS * W records itself (a lane per record, then
-//      redux.sync), which yields the next sample and its coordinates without
-//      a second barrier.  Records are double-buffered by exchange parity, so
-//      a record is never overwritten before every reader passed the barrier
-//      that follows its read.
+//      redux.sync), which yields the next sample without a second barrier;
+//      its coordinates come from this CTA's shared memory (CS == 1) or from
+//      the owner warp's record, whose slot follows from the index (CS > 1).
+//      Records are double-buffered by exchange parity, so a record is never
+//      overwritten before every reader passed the barrier that follows its
+//      read.
 #include "afps_device.cuh"
 
 namespace afps {
@@ -32,7 +35,7 @@ struct __align__(16) Rec {
 static_assert(sizeof(Rec) == 32, "Rec layout");
 
 template <int P, bool NPDU, bool CLUSTER>
-__global__ void __launch_bounds__(1024) afps_cta_kernel(const LaunchArgs a) {
+__global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = blockDim.x;
     const int tid = threadIdx.x;
@@ -84,21 +87,32 @@ __global__ void __launch_bounds__(1024) afps_cta_kernel(const LaunchArgs a) {
         }
         __syncthreads();
 
-        float x[P], y[P], z[P], D[P];
+        // rows i = 2h, 2h+1 share packed registers (f32x2 arithmetic)
+        constexpr int PP = (P + 1) / 2;
+        unsigned long long X2[PP], Y2[PP], Z2[PP];
+        float D[2 * PP];
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-            const int jl = tid + T * i;
-            if (jl < cn) {
-                x[i] = pts[3 * jl];
-                y[i] = pts[3 * jl + 1];
-                z[i] = pts[3 * jl + 2];
-                D[i] = 1e10f;
-            } else {  // padding: distance +0 stays +0 and loses every tie
-                x[i] = 0.f;
-                y[i] = 0.f;
-                z[i] = 0.f;
-                D[i] = 0.f;
+        for (int h = 0; h < PP; ++h) {
+            float xs[2], ys[2], zs[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = 2 * h + u;
+                const int jl = tid + T * i;
+                if (i < P && jl < cn) {
+                    xs[u] = pts[3 * jl];
+                    ys[u] = pts[3 * jl + 1];
+                    zs[u] = pts[3 * jl + 2];
+                    D[i] = 1e10f;
+                } else {  // padding: distance +0 stays +0 and loses every tie
+                    xs[u] = 0.f;
+                    ys[u] = 0.f;
+                    zs[u] = 0.f;
+                    D[i] = 0.f;
+                }
             }
+            X2[h] = dev::pack2(xs[0], xs[1]);
+            Y2[h] = dev::pack2(ys[0], ys[1]);
+            Z2[h] = dev::pack2(zs[0], zs[1]);
         }
 
         int p = d.first;  // sector offset of the current sample
@@ -109,36 +123,46 @@ __global__ void __launch_bounds__(1024) afps_cta_kernel(const LaunchArgs a) {
         const int kl = d.k >> 1;
         const int kr = d.k - kl;
         const bool emitter = (rank == 0) && (w == 0);
-        int obuf = 0;
+        int obuf = lane == 0 ? d.lo + p : 0;
 
-        for (int t = 0; t < c; ++t) {
-            if (emitter) {
-                if (lane == (t & 31)) obuf = d.lo + p;
-                if ((t & 31) == 31 || t == c - 1) {
-                    if (lane <= (t & 31)) out[(t & ~31) + lane] = obuf;
-                }
-            }
-            if (t == c - 1) break;
-
+        for (int t = 1; t < c; ++t) {
             // 1. update + local argmax (chunk-local offsets)
             const int wlo = p - kl - c0, whi = p + kr - c0;
+            const unsigned long long qx2 = dev::pack2(qx, qx), qy2 = dev::pack2(qy, qy),
+                                     qz2 = dev::pack2(qz, qz);
             float best = -1.f;
             int bi = 0;
 #pragma unroll
-            for (int i = 0; i < P; ++i) {
-                if (T * i < cn || i == 0) {  // CTA-uniform row test
-                    if (NPDU) {
-                        if (T * i + T - 1 >= wlo && T * i <= whi) {
-                            const int jl = tid + T * i;
-                            if (jl >= wlo && jl <= whi && jl < cn)
-                                D[i] = fminf(D[i], dev::sqdist(x[i], y[i], z[i], qx, qy, qz));
+            for (int h = 0; h < PP; ++h) {
+                const int i0 = 2 * h;
+                if (T * i0 < cn || h == 0) {  // CTA-uniform: the row pair holds real points
+                    // NPDU: row pairs the window misses are skipped by a CTA-
+                    // uniform test (npdu_skip) or computed and masked; inside a
+                    // row the window is always a mask, not a branch.
+                    const bool hit =
+                        !NPDU || !a.npdu_skip || (T * i0 + 2 * T - 1 >= wlo && T * i0 <= whi);
+                    if (hit) {
+                        float d0, d1;
+                        dev::sqdist2(X2[h], Y2[h], Z2[h], qx2, qy2, qz2, d0, d1);
+                        d0 = fminf(D[i0], d0);
+                        d1 = fminf(D[i0 + 1], d1);
+                        if (NPDU) {
+                            const int j0 = tid + T * i0, j1 = j0 + T;
+                            const unsigned span = (unsigned)(whi - wlo);
+                            D[i0] = ((unsigned)(j0 - wlo) <= span && j0 < cn) ? d0 : D[i0];
+                            D[i0 + 1] = ((unsigned)(j1 - wlo) <= span && j1 < cn) ? d1 : D[i0 + 1];
+                        } else {
+                            D[i0] = d0;
+                            D[i0 + 1] = d1;
                         }
-                    } else {
-                        D[i] = fminf(D[i], dev::sqdist(x[i], y[i], z[i], qx, qy, qz));
                     }
-                    if (D[i] > best) {
-                        best = D[i];
-                        bi = i;
+                    bool gt = D[i0] > best;
+                    best = gt ? D[i0] : best;
+                    bi = gt ? i0 : bi;
+                    if (i0 + 1 < P) {
+                        gt = D[i0 + 1] > best;
+                        best = gt ? D[i0 + 1] : best;
+                        bi = gt ? i0 + 1 : bi;
                     }
                 }
             }
@@ -148,20 +172,18 @@ __global__ void __launch_bounds__(1024) afps_cta_kernel(const LaunchArgs a) {
             const unsigned m = __reduce_max_sync(dev::kFull, bits);
             const unsigned cand = bits == m ? (unsigned)(tid + T * bi) : 0xffffffffu;
             const unsigned jw = __reduce_min_sync(dev::kFull, cand);  // chunk-local
+            const uint32_t jinv = 0xffffffffu - (uint32_t)(c0 + (int)jw);
             Rec* R = recs + (xchg & 1u) * E;
-            if (lane < CS) {
-                const float wx = pts[3 * jw], wy = pts[3 * jw + 1], wz = pts[3 * jw + 2];
-                const uint32_t jinv = 0xffffffffu - (uint32_t)(c0 + (int)jw);
-                if (CLUSTER) {
+            if (CLUSTER) {
+                if (lane < CS) {
+                    const float wx = pts[3 * jw], wy = pts[3 * jw + 1], wz = pts[3 * jw + 2];
                     const uint32_t slot = dev::smem_u32(&R[rank * W + w]);
                     const uint32_t remote = dev::mapa(slot, (uint32_t)lane);
                     dev::st_cluster_v4(remote, m, jinv, __float_as_uint(wx), __float_as_uint(wy));
                     dev::st_cluster_v4(remote + 16, __float_as_uint(wz), 0u, 0u, 0u);
-                } else {
-                    uint4* s = reinterpret_cast<uint4*>(&R[w]);
-                    s[0] = make_uint4(m, jinv, __float_as_uint(wx), __float_as_uint(wy));
-                    s[1] = make_uint4(__float_as_uint(wz), 0u, 0u, 0u);
                 }
+            } else if (lane == 0) {
+                *reinterpret_cast<uint2*>(&R[w]) = make_uint2(m, jinv);
             }
 
             // 3. one barrier
@@ -170,28 +192,37 @@ __global__ void __launch_bounds__(1024) afps_cta_kernel(const LaunchArgs a) {
             else
                 __syncthreads();
 
-            // 4. every warp reduces the E records
+            // 4. every warp reduces the E records: max distance bits, then
+            //    the largest ~index (= lowest index) among them
             unsigned long long bkey = 0ull;
-            int be = 0;
             for (int e = lane; e < E; e += 32) {
                 const uint2 kv = *reinterpret_cast<const uint2*>(&R[e]);
                 const unsigned long long key = ((unsigned long long)kv.x << 32) | kv.y;
-                if (key > bkey) {
-                    bkey = key;
-                    be = e;
-                }
+                bkey = key > bkey ? key : bkey;
             }
             const unsigned hi = (unsigned)(bkey >> 32), lo = (unsigned)bkey;
             const unsigned mm = __reduce_max_sync(dev::kFull, hi);
             const unsigned lo2 = __reduce_max_sync(dev::kFull, hi == mm ? lo : 0u);
-            const unsigned ball = __ballot_sync(dev::kFull, hi == mm && lo == lo2);
-            const int e_star = __shfl_sync(dev::kFull, be, __ffs(ball) - 1);
             p = (int)(0xffffffffu - lo2);
-            qx = R[e_star].x;
-            qy = R[e_star].y;
-            qz = R[e_star].z;
+            if (CLUSTER) {
+                // the winner's record sits at (owner rank, owner warp)
+                const int r = p / chunk;
+                const int e_star = r * W + (((p - r * chunk) % T) >> 5);
+                qx = R[e_star].x;
+                qy = R[e_star].y;
+                qz = R[e_star].z;
+            } else {
+                qx = pts[3 * p];
+                qy = pts[3 * p + 1];
+                qz = pts[3 * p + 2];
+            }
             ++xchg;
+            if (emitter) {
+                obuf = lane == (t & 31) ? d.lo + p : obuf;
+                if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
+            }
         }
+        if (emitter && lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
     }
     if (CLUSTER) dev::cluster_sync();  // no CTA leaves while a peer may still store to it
 }
@@ -209,6 +240,7 @@ static SectorKernel cta_kernel_for(int P, bool npdu, bool cluster) {
         AFPS_CTA_CASE(2)
         AFPS_CTA_CASE(4)
         AFPS_CTA_CASE(8)
+        AFPS_CTA_CASE(16)
         default:
             return nullptr;
     }
@@ -226,7 +258,7 @@ bool variant_supported(const Variant& v) {
         return warp_kernel_for(v.P, false) != nullptr && v.W >= 1 && v.W <= 8 && v.CS == 1;
     if (v.kind != KIND_CTA) return false;
     if (!cta_kernel_for(v.P, false, false)) return false;
-    if (v.W < 1 || v.W > 32 || v.CS < 1 || v.CS > 16) return false;
+    if (v.W < 1 || v.W > (v.P >= 16 ? 8 : 32) || v.CS < 1 || v.CS > 16) return false;
     return variant_smem(v) <= 227 * 1024;
 }
 

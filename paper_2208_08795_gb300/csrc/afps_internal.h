@@ -41,6 +41,7 @@ struct Variant {
     int32_t W;
     int32_t CS;
     int32_t occ;  // CTAs (or clusters) per SM for persistent grids; 0 = one per item
+    int32_t skip; // NPDU: skip rows the window misses (uniform branch) instead of masking
 };
 
 struct LaunchArgs {
@@ -53,7 +54,7 @@ struct LaunchArgs {
     int* status;            // device error word (first error wins)
     uint64_t timeout_ns;
     uint32_t stall_copy;    // fault injection: arm the barrier, issue no copy
-    uint32_t pad;
+    uint32_t npdu_skip;     // Variant::skip
 };
 
 // Device error codes written to *status.

@@ -66,6 +66,7 @@ afps::Variant na_variant(int64_t n_max) {
     }
     v.kind = afps::KIND_CTA;
     v.P = 8;
+    v.skip = 1;
     if (n_max <= 8192) {
         v.W = (int)((n_max + 255) / 256);
         return v;
@@ -76,7 +77,7 @@ afps::Variant na_variant(int64_t n_max) {
 }
 
 bool same_variant(const afps::Variant& a, const afps::Variant& b) {
-    return a.kind == b.kind && a.P == b.P && a.W == b.W && a.CS == b.CS;
+    return a.kind == b.kind && a.P == b.P && a.W == b.W && a.CS == b.CS && a.skip == b.skip;
 }
 
 // Sector rule of Sec. III-B: points [floor(sN/M), floor((s+1)N/M)), samples
@@ -216,6 +217,7 @@ extern "C" int afps_sample_batched_noalloc(const float* d_xyz, const int64_t* h_
         a.status = reinterpret_cast<int*>(base);
         a.timeout_ns = 2000000000ull;
         a.stall_copy = 0;
+        a.npdu_skip = cls[c].v.skip ? 1u : 0u;
         const int grid = cls[c].v.kind == afps::KIND_WARP
                              ? (cls[c].count + cls[c].v.W - 1) / cls[c].v.W
                              : cls[c].count;

@@ -71,21 +71,32 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         }
         __syncwarp();
 
-        float x[P], y[P], z[P], D[P];
+        // rows i = 2h, 2h+1 share packed registers (f32x2 arithmetic)
+        constexpr int PP = (P + 1) / 2;
+        unsigned long long X2[PP], Y2[PP], Z2[PP];
+        float D[2 * PP];
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-            const int j = lane + 32 * i;
-            if (j < n) {
-                x[i] = pts[3 * j];
-                y[i] = pts[3 * j + 1];
-                z[i] = pts[3 * j + 2];
-                D[i] = 1e10f;
-            } else {  // padding: distance +0 stays +0 and loses every tie
-                x[i] = 0.f;
-                y[i] = 0.f;
-                z[i] = 0.f;
-                D[i] = 0.f;
+        for (int h = 0; h < PP; ++h) {
+            float xs[2], ys[2], zs[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = 2 * h + u;
+                const int j = lane + 32 * i;
+                if (i < P && j < n) {
+                    xs[u] = pts[3 * j];
+                    ys[u] = pts[3 * j + 1];
+                    zs[u] = pts[3 * j + 2];
+                    D[i] = 1e10f;
+                } else {  // padding: distance +0 stays +0 and loses every tie
+                    xs[u] = 0.f;
+                    ys[u] = 0.f;
+                    zs[u] = 0.f;
+                    D[i] = 0.f;
+                }
             }
+            X2[h] = dev::pack2(xs[0], xs[1]);
+            Y2[h] = dev::pack2(ys[0], ys[1]);
+            Z2[h] = dev::pack2(zs[0], zs[1]);
         }
 
         int32_t* out = a.out + d.dst;
@@ -93,33 +104,47 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         const int kl = d.k >> 1;
         const int kr = d.k - kl;
         int p = d.first;
-        int obuf = 0;
-        for (int t = 0; t < c; ++t) {
-            if (lane == (t & 31)) obuf = d.lo + p;
-            if ((t & 31) == 31 || t == c - 1) {
-                if (lane <= (t & 31)) out[(t & ~31) + lane] = obuf;
-            }
-            if (t == c - 1) break;
-
+        // sample t's index is kept by lane t % 32 and stored once per 32 samples
+        int obuf = lane == 0 ? d.lo + p : 0;
+        for (int t = 1; t < c; ++t) {
             const float qx = pts[3 * p], qy = pts[3 * p + 1], qz = pts[3 * p + 2];
-            const int wlo = p - kl, whi = p + kr;
+            const unsigned long long qx2 = dev::pack2(qx, qx), qy2 = dev::pack2(qy, qy),
+                                     qz2 = dev::pack2(qz, qz);
+            // window [p - kl, p + kr] as one unsigned range test
+            const unsigned wlo = (unsigned)(p - kl);
+            const unsigned wspan = (unsigned)(kl + kr);
             float best = -1.f;
             int bi = 0;
 #pragma unroll
-            for (int i = 0; i < P; ++i) {
-                if (32 * i < n) {  // warp-uniform: the row holds real points
-                    if (NPDU) {
-                        if (32 * i + 31 >= wlo && 32 * i <= whi) {  // row meets the window
-                            const int j = lane + 32 * i;
-                            if (j >= wlo && j <= whi && j < n)
-                                D[i] = fminf(D[i], dev::sqdist(x[i], y[i], z[i], qx, qy, qz));
+            for (int h = 0; h < PP; ++h) {
+                const int i0 = 2 * h;
+                if (32 * i0 < n) {  // warp-uniform: the row pair holds real points
+                    // NPDU: every row pair is computed and the window applied as
+                    // a mask, or (npdu_skip) pairs the window misses are skipped
+                    // by a warp-uniform test; never a divergent branch.
+                    const bool hit = !NPDU || !a.npdu_skip ||
+                                     (32 * i0 + 63 >= p - kl && 32 * i0 <= p + kr);
+                    if (hit) {
+                        float d0, d1;
+                        dev::sqdist2(X2[h], Y2[h], Z2[h], qx2, qy2, qz2, d0, d1);
+                        d0 = fminf(D[i0], d0);
+                        d1 = fminf(D[i0 + 1], d1);
+                        if (NPDU) {
+                            const int j0 = lane + 32 * i0, j1 = j0 + 32;
+                            D[i0] = (((unsigned)j0 - wlo) <= wspan && j0 < n) ? d0 : D[i0];
+                            D[i0 + 1] = (((unsigned)j1 - wlo) <= wspan && j1 < n) ? d1 : D[i0 + 1];
+                        } else {
+                            D[i0] = d0;
+                            D[i0 + 1] = d1;
                         }
-                    } else {
-                        D[i] = fminf(D[i], dev::sqdist(x[i], y[i], z[i], qx, qy, qz));
                     }
-                    if (D[i] > best) {  // strict: lowest row wins ties
-                        best = D[i];
-                        bi = i;
+                    bool gt = D[i0] > best;  // strict: lowest row wins ties
+                    best = gt ? D[i0] : best;
+                    bi = gt ? i0 : bi;
+                    if (i0 + 1 < P) {
+                        gt = D[i0 + 1] > best;
+                        best = gt ? D[i0 + 1] : best;
+                        bi = gt ? i0 + 1 : bi;
                     }
                 }
             }
@@ -127,7 +152,10 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
             const unsigned m = __reduce_max_sync(dev::kFull, bits);
             const unsigned cand = bits == m ? (unsigned)(lane + 32 * bi) : 0xffffffffu;
             p = (int)__reduce_min_sync(dev::kFull, cand);
+            obuf = lane == (t & 31) ? d.lo + p : obuf;
+            if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
         }
+        if (lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
 
         if (a.counter) {
             unsigned v = 0;
