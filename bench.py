@@ -248,6 +248,35 @@ def kernel_source_hash() -> str:
 NCU_TRAFFIC = {"source_hash": None, "bytes_per_launch": None}
 
 
+# ------------------------------------------------------------------ serving
+SERVING_LEVELS = [16384, 4096, 1024, 256]
+SERVING_RATES = [500.0, 2000.0, 8000.0, 32000.0]
+
+
+def serving_sweep(sampler, seconds_per_rate: float = 0.25):
+    """Poisson streams of LiDAR-like frames (16-32K points, 32 rings, range
+    U[2, 60] m, 2% dropout, emitted column by column), each a chained request
+    16384 -> 4096 -> 1024 -> 256 with NPDU-AFPS M = 32, k = 16, at rising
+    arrival rates; latency is arrival to result on the host."""
+    from paper_2208_08795_gb300 import afps as A, serving, synth
+    frames = [synth.lidar_frame(100 + i) for i in range(8)]
+    srv = A.Server(sampler, SERVING_LEVELS, 32, 16, hbm_budget_bytes=2 << 30,
+                   max_inflight=256)
+    try:
+        serving.poisson_run(srv, frames, 1000.0, 20, seed=99)  # warm-up
+        rows = []
+        for i, rate in enumerate(SERVING_RATES):
+            n = int(min(2000, max(100, rate * seconds_per_rate)))
+            r = serving.poisson_run(srv, frames, rate, n, seed=i)
+            rows.append({k: round(v, 3) if isinstance(v, float) else v for k, v in r.items()})
+    finally:
+        srv.close()
+    return {"workload": "LiDAR-like frames, 16-32K points, chained 16384->4096->1024->256, "
+                        "NPDU-AFPS M=32 k=16, Poisson arrivals",
+            "hbm_budget_bytes": 2 << 30, "rates": rows,
+            "saturation_frames_per_s": max(r["achieved_frames_per_s"] for r in rows)}
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args, rank: int, world: int) -> int:
     """The oracle, as it stands, on the host cores: the reference arm."""
@@ -351,6 +380,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     ts = time_e2e(sampler, h_xyz, ba, h_out, args.steps, args.warmup)
     barrier()
     e2e_ms = max_over_ranks(float(np.mean(ts)), world, dev)
+    serving_stats = serving_sweep(sampler) if args.serving else None
     clk = clocks.stop()
     e2e_ok = bool(np.array_equal(h_out, head_out))
 
@@ -393,6 +423,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         "e2e": {"value": B_CLOUDS * world / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h_xyz.nbytes), "d2h_bytes_per_step": int(h_out.nbytes),
                 "matches_device_path": e2e_ok},
+        "serving": serving_stats,
         "gpu_launches": launches,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
@@ -434,6 +465,8 @@ def main(argv=None) -> int:
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-seconds", type=float, default=5.0)
+    ap.add_argument("--no-serving", dest="serving", action="store_false",
+                    help="skip the serving sweep")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -219,6 +219,80 @@ int afps_sample_batched_noalloc(const float* d_xyz, const int64_t* h_pt_off, int
                                 const int64_t* h_start, const int64_t* h_out_off,
                                 int32_t* d_out, void* stream);
 
+/* ----------------------------------------------------------------------------
+ * Serving runtime: continuous batching of chained sampling requests.
+ *
+ * A request is one sensor frame (N points) and a chain of sampling levels,
+ * the PointNet++ set-abstraction hierarchy the paper accelerates (Sec. I-II):
+ * level 0 samples levels[0] points from the frame with NPDU-AFPS (M sectors,
+ * window k), level l+1 samples levels[l+1] points from level l's samples
+ * taken in ascending frame index (storage order kept, Sec. III-A).  The
+ * result lists, per level, the frame indices of that level's samples in
+ * emission (sector-major) order.
+ *
+ * Each afps_server_step admits queued requests while the device arena (the
+ * HBM budget) and the slot count allow, then launches one batched sampling
+ * call over the current level of every admitted request, one gather that
+ * builds every next-level cloud on the device, and device-to-host copies of
+ * finished results.  Requests at different levels share each launch; a
+ * request admitted while others are on the GPU joins the next step.  Frames
+ * and level clouds stay resident in the arena until their request finishes.
+ * The host runs at most max_steps_ahead steps ahead of the GPU.
+ * -------------------------------------------------------------------------- */
+#define AFPS_SERVER_MAX_LEVELS 8
+#define AFPS_ERR_BUSY (-8) /* afps_server_submit: the host queue is full */
+
+typedef struct afps_server afps_server;
+
+typedef struct afps_server_config {
+    int64_t hbm_budget_bytes;  /* device arena for admitted requests (bytes) */
+    int64_t max_queued;        /* frames waiting for admission; <= 0: 4096 */
+    int32_t max_inflight;      /* admitted requests at once; <= 0: 256 */
+    int32_t n_levels;          /* 1 .. AFPS_SERVER_MAX_LEVELS */
+    int32_t levels[AFPS_SERVER_MAX_LEVELS]; /* samples per level */
+    int32_t M;                 /* sectors per level (capped at the level's size) */
+    int32_t npdu_window;       /* k >= 0 (0 = no NPDU) */
+    int32_t max_steps_ahead;   /* <= 0: 2 */
+} afps_server_config;
+
+typedef struct afps_server_result {
+    uint64_t tag;              /* the caller's tag from afps_server_submit */
+    int32_t status;            /* AFPS_OK or an error code */
+    int32_t n_levels;
+    int32_t count[AFPS_SERVER_MAX_LEVELS];
+    const int32_t* indices;    /* sum(count) frame indices, level after level; owned by
+                                  the server, valid until the next afps_server_poll */
+    double submit_ms, admit_ms, done_ms; /* server clock (afps_server_clock_ms) */
+} afps_server_result;
+
+/* Create a server on ctx's device, issuing its work on `stream` (NULL: a
+ * stream of its own).  Allocates the arena and pinned result buffers. */
+int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_config* cfg,
+                       void* stream);
+
+/* Queue one frame (N points, host memory, copied before return).  Needs
+ * levels[0] <= N <= 65536 and the request to fit the arena on its own.
+ * Returns AFPS_ERR_BUSY when max_queued frames are waiting. */
+int afps_server_submit(afps_server* srv, const float* h_xyz, int64_t N, uint64_t tag);
+
+/* One continuous-batching step (see above).  Returns the number of requests
+ * it advanced by one level (0 when idle), or a negative error. */
+int afps_server_step(afps_server* srv);
+
+/* Move up to max_results finished requests into out; returns how many. */
+int afps_server_poll(afps_server* srv, afps_server_result* out, int32_t max_results);
+
+/* Counts of queued, in-flight (admitted, unfinished) requests and arena
+ * bytes in use; any pointer may be NULL. */
+int afps_server_stats(afps_server* srv, int64_t* queued, int64_t* inflight,
+                      int64_t* arena_used);
+
+/* Milliseconds since the server was created (the clock of the results). */
+double afps_server_clock_ms(const afps_server* srv);
+
+/* Wait for the server's device work and free everything it owns. */
+void afps_server_destroy(afps_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

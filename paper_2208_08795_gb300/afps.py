@@ -36,7 +36,9 @@ AFPS_FLAG_TEST_STALL_COPY = 0x100
 EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
            "afps_sample_batched_host", "afps_gather_levels", "afps_sync",
            "afps_last_error", "afps_autotune_batched", "afps_save_tuning",
-           "afps_describe_plan", "afps_launch_count", "afps_sample_batched_noalloc")
+           "afps_describe_plan", "afps_launch_count", "afps_sample_batched_noalloc",
+           "afps_server_create", "afps_server_submit", "afps_server_step", "afps_server_poll",
+           "afps_server_stats", "afps_server_clock_ms", "afps_server_destroy")
 
 
 class AfpsLibraryError(RuntimeError):
@@ -48,6 +50,24 @@ class AfpsError(RuntimeError):
         super().__init__(f"afps error {code}: {message}")
         self.code = code
         self.message = message
+
+
+AFPS_ERR_BUSY = -8
+AFPS_SERVER_MAX_LEVELS = 8
+
+
+class afps_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_queued", ctypes.c_int64),
+                ("max_inflight", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("levels", ctypes.c_int32 * AFPS_SERVER_MAX_LEVELS), ("M", ctypes.c_int32),
+                ("npdu_window", ctypes.c_int32), ("max_steps_ahead", ctypes.c_int32)]
+
+
+class afps_server_result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("count", ctypes.c_int32 * AFPS_SERVER_MAX_LEVELS),
+                ("indices", ctypes.POINTER(ctypes.c_int32)), ("submit_ms", ctypes.c_double),
+                ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
 
 
 class afps_config(ctypes.Structure):
@@ -85,6 +105,20 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.afps_launch_count.restype = ctypes.c_int64
     L.afps_sample_batched_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
     L.afps_sample_batched_noalloc.restype = ctypes.c_int
+    L.afps_server_create.argtypes = [ctypes.POINTER(vp), vp, ctypes.POINTER(afps_server_config), vp]
+    L.afps_server_create.restype = ctypes.c_int
+    L.afps_server_submit.argtypes = [vp, vp, i64, ctypes.c_uint64]
+    L.afps_server_submit.restype = ctypes.c_int
+    L.afps_server_step.argtypes = [vp]
+    L.afps_server_step.restype = ctypes.c_int
+    L.afps_server_poll.argtypes = [vp, ctypes.POINTER(afps_server_result), i32]
+    L.afps_server_poll.restype = ctypes.c_int
+    L.afps_server_stats.argtypes = [vp, vp, vp, vp]
+    L.afps_server_stats.restype = ctypes.c_int
+    L.afps_server_clock_ms.argtypes = [vp]
+    L.afps_server_clock_ms.restype = ctypes.c_double
+    L.afps_server_destroy.argtypes = [vp]
+    L.afps_server_destroy.restype = None
     return L
 
 
@@ -318,3 +352,102 @@ class Sampler:
     @property
     def launch_count(self) -> int:
         return afps_launch_count(self.ctx)
+
+
+# ------------------------------------------------------------------ serving
+def afps_server_create(ctx, cfg: afps_server_config, stream=None) -> int:
+    h = ctypes.c_void_p()
+    rc = load().afps_server_create(ctypes.byref(h), ctx, ctypes.byref(cfg), stream)
+    if rc != AFPS_OK:
+        raise AfpsError(rc, "afps_server_create failed")
+    return h.value
+
+
+def afps_server_submit(srv, h_xyz, N, tag) -> int:
+    return load().afps_server_submit(srv, h_xyz, N, tag)
+
+
+def afps_server_step(srv) -> int:
+    return load().afps_server_step(srv)
+
+
+def afps_server_poll(srv, out, max_results) -> int:
+    return load().afps_server_poll(srv, out, max_results)
+
+
+def afps_server_stats(srv, queued, inflight, arena_used) -> int:
+    return load().afps_server_stats(srv, queued, inflight, arena_used)
+
+
+def afps_server_clock_ms(srv) -> float:
+    return load().afps_server_clock_ms(srv)
+
+
+def afps_server_destroy(srv) -> None:
+    load().afps_server_destroy(srv)
+
+
+class ServerResult:
+    """One finished request: per-level frame indices (copied) and times."""
+
+    def __init__(self, r: afps_server_result):
+        self.tag = int(r.tag)
+        self.status = int(r.status)
+        counts = [int(r.count[l]) for l in range(r.n_levels)]
+        flat = np.ctypeslib.as_array(r.indices, shape=(sum(counts),)).copy()
+        self.levels = np.split(flat, np.cumsum(counts)[:-1])
+        self.submit_ms, self.admit_ms, self.done_ms = r.submit_ms, r.admit_ms, r.done_ms
+
+
+class Server:
+    """Continuous-batching server for chained sampling requests (afps_server_*)."""
+
+    def __init__(self, sampler: "Sampler", levels, M: int, k: int, hbm_budget_bytes: int,
+                 max_inflight: int = 256, max_queued: int = 4096, max_steps_ahead: int = 2,
+                 stream=None):
+        cfg = afps_server_config()
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.max_queued = int(max_queued)
+        cfg.max_inflight = int(max_inflight)
+        cfg.n_levels = len(levels)
+        for i, c in enumerate(levels):
+            cfg.levels[i] = int(c)
+        cfg.M, cfg.npdu_window, cfg.max_steps_ahead = int(M), int(k), int(max_steps_ahead)
+        self.sampler = sampler
+        self.srv = afps_server_create(sampler.ctx, cfg, stream)
+        self._buf = (afps_server_result * 256)()
+
+    def close(self):
+        if self.srv:
+            afps_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, xyz: np.ndarray, tag: int) -> int:
+        a = np.ascontiguousarray(xyz, dtype=np.float32)
+        return afps_server_submit(self.srv, a.ctypes.data, a.shape[0], tag)
+
+    def step(self) -> int:
+        rc = afps_server_step(self.srv)
+        if rc < 0:
+            raise AfpsError(rc, afps_last_error(self.sampler.ctx))
+        return rc
+
+    def poll(self):
+        n = afps_server_poll(self.srv, self._buf, len(self._buf))
+        if n < 0:
+            raise AfpsError(n, "afps_server_poll failed")
+        return [ServerResult(self._buf[i]) for i in range(n)]
+
+    def stats(self):
+        q, f, u = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        afps_server_stats(self.srv, ctypes.byref(q), ctypes.byref(f), ctypes.byref(u))
+        return q.value, f.value, u.value
+
+    def clock_ms(self) -> float:
+        return afps_server_clock_ms(self.srv)

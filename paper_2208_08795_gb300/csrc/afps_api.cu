@@ -26,6 +26,7 @@ namespace {
 
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
 constexpr size_t kMaxGraphs = 32;
+constexpr int kStageSlots = 4;  // pinned upload buffers in flight
 
 // ---------------------------------------------------------------- buffers
 struct DevBuf {
@@ -102,10 +103,11 @@ struct afps_ctx {
     int* d_status = nullptr;
     std::string last_error;
     cudaEvent_t ev_done = nullptr;    // last device work that used the shared workspace
-    cudaEvent_t ev_upload = nullptr;  // last host->device copy out of h_items
     cudaStream_t capture = nullptr;   // private stream for graph capture
     DevBuf items, counters, xyz_stage, out_stage;
-    HostBuf h_items;
+    HostBuf stage[kStageSlots];         // pinned upload ring
+    cudaEvent_t stage_ev[kStageSlots] = {};  // last copy out of each slot
+    int stage_next = 0;
     std::unordered_map<std::string, GraphEntry> graphs;
     std::map<std::string, Variant> tuned;
     int64_t launches = 0;
@@ -366,24 +368,28 @@ int64_t size_bucket(int64_t n_max) {
     return b;
 }
 
-int build_plan(afps_ctx* ctx, const int64_t* pt_off, int32_t B, const int32_t* C,
-               const int32_t* M, const int32_t* K, const int64_t* start,
-               const int64_t* out_off, BatchPlan& plan) {
-    if (B < 1 || !pt_off || !C || !M || !K || !start || !out_off)
+// Cloud b: n_pts[b] points from point pt_begin[b] of the xyz base, C[b]
+// indices written from out_begin[b] of the output base (out_cap[b] slots).
+int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t* n_pts,
+               const int64_t* out_begin, const int64_t* out_cap, const int32_t* C,
+               const int32_t* M, const int32_t* K, const int64_t* start, BatchPlan& plan) {
+    if (B < 1 || !pt_begin || !n_pts || !out_begin || !out_cap || !C || !M || !K || !start)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
-    if (pt_off[0] < 0 || out_off[0] < 0)
-        return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: negative first offset");
     struct Member {
         int32_t b;
         CloudCheck chk;
     };
     std::map<std::pair<int, int64_t>, std::vector<Member>> groups;
     for (int32_t b = 0; b < B; ++b) {
-        const int64_t N = pt_off[b + 1] - pt_off[b];
-        if (out_off[b + 1] - out_off[b] < (int64_t)C[b]) {
+        const int64_t N = n_pts[b];
+        if (pt_begin[b] < 0 || out_begin[b] < 0) {
             std::ostringstream os;
-            os << "cloud " << b << ": output range " << (out_off[b + 1] - out_off[b])
-               << " is smaller than C=" << C[b];
+            os << "cloud " << b << ": negative point or output offset";
+            return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
+        }
+        if (out_cap[b] < (int64_t)C[b]) {
+            std::ostringstream os;
+            os << "cloud " << b << ": output range " << out_cap[b] << " is smaller than C=" << C[b];
             return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
         }
         CloudCheck chk = check_cloud(N, C[b], M[b], K[b], start[b]);
@@ -402,15 +408,15 @@ int build_plan(afps_ctx* ctx, const int64_t* pt_off, int32_t B, const int32_t* C
         cp.first = plan.items.size();
         for (const Member& m : g.second) {
             const int32_t b = m.b;
-            const int64_t N = pt_off[b + 1] - pt_off[b];
+            const int64_t N = n_pts[b];
             cp.n_max = std::max(cp.n_max, m.chk.n_max);
             cp.c_max = std::max(cp.c_max, m.chk.c_max);
             for (int64_t s = 0; s < M[b]; ++s) {
                 const int64_t lo = sec_lo(N, M[b], s), hi = sec_lo(N, M[b], s + 1);
                 const int64_t o0 = sec_off(C[b], M[b], s), o1 = sec_off(C[b], M[b], s + 1);
                 ItemDesc d{};
-                d.src = pt_off[b] + lo;
-                d.dst = out_off[b] + o0;
+                d.src = pt_begin[b] + lo;
+                d.dst = out_begin[b] + o0;
                 d.n = (int32_t)(hi - lo);
                 d.c = (int32_t)(o1 - o0);
                 d.first = std::min<int32_t>(m.chk.start_r, d.n - 1);
@@ -432,21 +438,47 @@ int build_plan(afps_ctx* ctx, const int64_t* pt_off, int32_t B, const int32_t* C
     return AFPS_OK;
 }
 
+// Copy `bytes` of host data into the device buffer `dst` on `stream`, through
+// the next slot of the pinned upload ring (waiting only for that slot's
+// previous copy, kStageSlots uploads ago).  Device work that used the
+// workspace earlier, possibly on another stream, is ordered before the copy.
+int upload(afps_ctx* ctx, DevBuf& dst, const void* src, size_t bytes, cudaStream_t stream) {
+    const int s = ctx->stage_next;
+    ctx->stage_next = (s + 1) % kStageSlots;
+    AFPS_CUDA(ctx, cudaEventSynchronize(ctx->stage_ev[s]));
+    AFPS_CUDA(ctx, ctx->stage[s].reserve(bytes));
+    AFPS_CUDA(ctx, dst.reserve(bytes));
+    memcpy(ctx->stage[s].p, src, bytes);
+    AFPS_CUDA(ctx, cudaStreamWaitEvent(stream, ctx->ev_done, 0));
+    AFPS_CUDA(ctx, cudaMemcpyAsync(dst.p, ctx->stage[s].p, bytes, cudaMemcpyHostToDevice, stream));
+    AFPS_CUDA(ctx, cudaEventRecord(ctx->stage_ev[s], stream));
+    return AFPS_OK;
+}
+
+// The public batched layout: cloud b is points [pt_off[b], pt_off[b+1]),
+// outputs [out_off[b], out_off[b+1]).
+int build_plan_consecutive(afps_ctx* ctx, const int64_t* pt_off, int32_t B, const int32_t* C,
+                           const int32_t* M, const int32_t* K, const int64_t* start,
+                           const int64_t* out_off, BatchPlan& plan) {
+    if (B < 1 || !pt_off || !out_off)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
+    std::vector<int64_t> pb((size_t)B), np((size_t)B), ob((size_t)B), oc((size_t)B);
+    for (int32_t b = 0; b < B; ++b) {
+        pb[b] = pt_off[b];
+        np[b] = pt_off[b + 1] - pt_off[b];
+        ob[b] = out_off[b];
+        oc[b] = out_off[b + 1] - out_off[b];
+    }
+    return build_plan(ctx, B, pb.data(), np.data(), ob.data(), oc.data(), C, M, K, start, plan);
+}
+
 // Run a plan out of the context's shared workspace (no graph).
 int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* d_out,
              cudaStream_t stream) {
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);
-    // the pinned staging may still feed an earlier copy
-    AFPS_CUDA(ctx, cudaEventSynchronize(ctx->ev_upload));
-    AFPS_CUDA(ctx, ctx->h_items.reserve(bytes));
-    AFPS_CUDA(ctx, ctx->items.reserve(bytes));
     AFPS_CUDA(ctx, ctx->counters.reserve(plan.classes.size() * sizeof(unsigned int)));
-    memcpy(ctx->h_items.p, plan.items.data(), bytes);
-    // earlier device work on the workspace, possibly on another stream
-    AFPS_CUDA(ctx, cudaStreamWaitEvent(stream, ctx->ev_done, 0));
-    AFPS_CUDA(ctx, cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, bytes, cudaMemcpyHostToDevice,
-                                   stream));
-    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_upload, stream));
+    int urc = upload(ctx, ctx->items, plan.items.data(), bytes, stream);
+    if (urc != AFPS_OK) return urc;
     const ItemDesc* d_items = static_cast<const ItemDesc*>(ctx->items.p);
     unsigned int* counters = static_cast<unsigned int*>(ctx->counters.p);
     for (size_t i = 0; i < plan.classes.size(); ++i) {
@@ -532,7 +564,7 @@ int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: xyz and out must be 4-byte aligned");
     if (!(ctx->flags & AFPS_FLAG_GRAPH)) {
         BatchPlan plan;
-        int rc = build_plan(ctx, pt_off, B, C, M, K, start, out_off, plan);
+        int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan);
         if (rc != AFPS_OK) return rc;
         return run_plan(ctx, plan, d_xyz, d_out, stream);
     }
@@ -542,7 +574,7 @@ int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
         BatchPlan plan;
-        int rc = build_plan(ctx, pt_off, B, C, M, K, start, out_off, plan);
+        int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan);
         if (rc != AFPS_OK) return rc;
         if (ctx->graphs.size() >= kMaxGraphs) {  // evict the least recently used
             auto victim = ctx->graphs.begin();
@@ -588,6 +620,52 @@ int load_tuning(afps_ctx* ctx, const std::string& path) {
 
 }  // namespace
 
+// ============================================================ internal API
+namespace afps {
+
+int gather_run(afps_ctx* ctx, const GatherDesc* descs, int32_t B, const float* in_xyz,
+               const int32_t* in_frame, const int32_t* sel, float* out_xyz, int32_t* out_frame,
+               int32_t* sel_frame, cudaStream_t stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    int32_t max_n = 1;
+    for (int32_t b = 0; b < B; ++b) {
+        const GatherDesc& g = descs[b];
+        if (g.n < 1 || g.n > kGatherMaxPoints || g.c < 0 || g.c >= 65536 || g.in_xyz < 0 ||
+            g.sel < 0 || g.out_xyz < 0 || (g.in_frame >= 0 && !in_frame) ||
+            (g.out_frame >= 0 && !out_frame) || (g.sel_frame >= 0 && !sel_frame)) {
+            std::ostringstream os;
+            os << "gather: cloud " << b << " has " << g.n << " points and " << g.c
+               << " samples (need 1 <= n <= " << kGatherMaxPoints
+               << ", 0 <= c < 65536) or a frame offset without its array";
+            return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
+        }
+        max_n = std::max(max_n, g.n);
+    }
+    int rc = upload(ctx, ctx->items, descs, (size_t)B * sizeof(GatherDesc), stream);
+    if (rc != AFPS_OK) return rc;
+    cudaError_t e = launch_gather(static_cast<const GatherDesc*>(ctx->items.p), B, max_n, in_xyz,
+                                  in_frame, sel, out_xyz, out_frame, sel_frame, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
+    ctx->launches += 1;
+    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, stream));
+    return AFPS_OK;
+}
+
+int sample_scattered(afps_ctx* ctx, const float* xyz, int32_t B, const int64_t* pt_begin,
+                     const int64_t* n_pts, const int32_t* C, const int32_t* M, const int32_t* K,
+                     const int64_t* start, int32_t* out, const int64_t* out_begin,
+                     cudaStream_t stream) {
+    if (!ctx || !xyz || !out) return AFPS_ERR_INVALID_ARG;
+    std::vector<int64_t> cap((size_t)std::max(B, 1));
+    for (int32_t b = 0; b < B; ++b) cap[b] = C[b];
+    BatchPlan plan;
+    int rc = build_plan(ctx, B, pt_begin, n_pts, out_begin, cap.data(), C, M, K, start, plan);
+    if (rc != AFPS_OK) return rc;
+    return run_plan(ctx, plan, xyz, out, stream);
+}
+
+}  // namespace afps
+
 // ====================================================================== ABI
 extern "C" {
 
@@ -614,10 +692,12 @@ int afps_create(afps_ctx** out, const afps_config* cfg) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_upload, cudaEventDisableTiming);
+    for (int i = 0; i < kStageSlots && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&ctx->stage_ev[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_done, ctx->capture);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_upload, ctx->capture);
+    for (int i = 0; i < kStageSlots && e == cudaSuccess; ++i)
+        e = cudaEventRecord(ctx->stage_ev[i], ctx->capture);
     if (e != cudaSuccess) {
         cudaGetLastError();
         afps_destroy(ctx);
@@ -639,10 +719,12 @@ void afps_destroy(afps_ctx* ctx) {
         ctx->counters.release();
         ctx->xyz_stage.release();
         ctx->out_stage.release();
-        ctx->h_items.release();
+        for (int i = 0; i < kStageSlots; ++i) {
+            ctx->stage[i].release();
+            if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
+        }
         if (ctx->d_status) cudaFree(ctx->d_status);
         if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
-        if (ctx->ev_upload) cudaEventDestroy(ctx->ev_upload);
         if (ctx->capture) cudaStreamDestroy(ctx->capture);
         cudaGetLastError();
     }
@@ -734,37 +816,23 @@ int afps_gather_levels(afps_ctx* ctx, int32_t B, const int64_t* h_in_pt_off,
     if (B < 1 || !h_in_pt_off || !h_sel_off || !d_in_xyz || !d_sel || !d_out_xyz)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_gather_levels: NULL argument or B < 1");
     std::vector<afps::GatherDesc> descs((size_t)B);
-    int32_t max_n = 1;
     for (int32_t b = 0; b < B; ++b) {
         const int64_t n = h_in_pt_off[b + 1] - h_in_pt_off[b];
         const int64_t c = h_sel_off[b + 1] - h_sel_off[b];
-        if (n < 1 || n > afps::kGatherMaxPoints || c < 0 || c >= 65536 || h_in_pt_off[b] < 0 ||
-            h_sel_off[b] < 0) {
-            std::ostringstream os;
-            os << "afps_gather_levels: cloud " << b << " has " << n << " points and " << c
-               << " samples (need 1 <= n <= " << afps::kGatherMaxPoints << ", 0 <= c < 65536)";
-            return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
-        }
-        descs[b] = afps::GatherDesc{h_in_pt_off[b], h_sel_off[b], (int32_t)n, (int32_t)c};
-        max_n = std::max<int32_t>(max_n, (int32_t)n);
+        afps::GatherDesc& g = descs[b];
+        g.in_xyz = h_in_pt_off[b];
+        g.in_frame = d_in_frame ? h_in_pt_off[b] : -1;
+        g.sel = h_sel_off[b];
+        g.out_xyz = h_sel_off[b];
+        g.out_frame = d_out_frame ? h_sel_off[b] : -1;
+        g.sel_frame = d_sel_frame ? h_sel_off[b] : -1;
+        g.n = (int32_t)std::min<int64_t>(n, INT32_MAX);
+        g.c = (int32_t)std::min<int64_t>(c, INT32_MAX);
+        if (n < 1 || c < 0) g.n = -1;  // rejected below
     }
     DeviceGuard guard(ctx->device);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t bytes = descs.size() * sizeof(afps::GatherDesc);
-    AFPS_CUDA(ctx, cudaEventSynchronize(ctx->ev_upload));
-    AFPS_CUDA(ctx, ctx->h_items.reserve(bytes));
-    AFPS_CUDA(ctx, ctx->items.reserve(bytes));
-    memcpy(ctx->h_items.p, descs.data(), bytes);
-    AFPS_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_done, 0));
-    AFPS_CUDA(ctx, cudaMemcpyAsync(ctx->items.p, ctx->h_items.p, bytes, cudaMemcpyHostToDevice, st));
-    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_upload, st));
-    cudaError_t e = afps::launch_gather(static_cast<const afps::GatherDesc*>(ctx->items.p), B,
-                                        max_n, d_in_xyz, d_in_frame, d_sel, d_out_xyz,
-                                        d_out_frame, d_sel_frame, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
-    ctx->launches += 1;
-    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, st));
-    return AFPS_OK;
+    return afps::gather_run(ctx, descs.data(), B, d_in_xyz, d_in_frame, d_sel, d_out_xyz,
+                            d_out_frame, d_sel_frame, static_cast<cudaStream_t>(stream));
 }
 
 int afps_sync(afps_ctx* ctx, void* stream) {
@@ -796,7 +864,7 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
     DeviceGuard guard(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     BatchPlan plan;
-    int rc = build_plan(ctx, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, plan);
+    int rc = build_plan_consecutive(ctx, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, plan);
     if (rc != AFPS_OK) return rc;
     // upload the table once, then time each candidate class by class
     rc = run_plan(ctx, plan, d_xyz, d_out, st);

@@ -28,10 +28,10 @@ __global__ void __launch_bounds__(1024) afps_gather_kernel(
     for (int i = tid; i < words; i += T) cnt[i] = 0u;
     __syncthreads();
     for (int s = tid; s < c; s += T) {
-        const int j = sel[d.sel_off + s];
+        const int j = sel[d.sel + s];
         if (j >= 0 && j < n) {
             atomicAdd(&cnt[j >> 1], 1u << (16 * (j & 1)));
-            if (sel_frame) sel_frame[d.sel_off + s] = in_frame ? in_frame[d.in_off + j] : j;
+            if (d.sel_frame >= 0) sel_frame[d.sel_frame + s] = d.in_frame >= 0 ? in_frame[d.in_frame + j] : j;
         }
     }
     __syncthreads();
@@ -65,15 +65,15 @@ __global__ void __launch_bounds__(1024) afps_gather_kernel(
     for (int j = j0; j < j1; ++j) {
         uint32_t k = (cnt[j >> 1] >> (16 * (j & 1))) & 0xffffu;
         if (!k) continue;
-        const float* src = in_xyz + 3 * (d.in_off + j);
+        const float* src = in_xyz + 3 * (d.in_xyz + j);
         const float px = src[0], py = src[1], pz = src[2];
-        const int32_t fr = in_frame ? in_frame[d.in_off + j] : j;
+        const int32_t fr = d.in_frame >= 0 ? in_frame[d.in_frame + j] : j;
         for (; k; --k, ++pos) {
-            float* dst = out_xyz + 3 * (d.sel_off + pos);
+            float* dst = out_xyz + 3 * (d.out_xyz + pos);
             dst[0] = px;
             dst[1] = py;
             dst[2] = pz;
-            if (out_frame) out_frame[d.sel_off + pos] = fr;
+            if (d.out_frame >= 0) out_frame[d.out_frame + pos] = fr;
         }
     }
 }

@@ -80,17 +80,38 @@ cudaError_t launch_sector(const Variant& v, bool npdu, const LaunchArgs& a, int 
 // Largest number of clusters of the variant that can be co-resident, or 0.
 int max_active_clusters(const Variant& v);
 
-// Chained-level gather (afps_gather_levels).
+// Chained-level gather (afps_gather_levels and the serving runtime).  All
+// offsets are in elements of their arrays (points for xyz); -1 means "none"
+// (identity frame indices on input, no output).
 struct GatherDesc {
-    int64_t in_off;   // first point of the cloud in the input arrays
-    int64_t sel_off;  // first sample in d_sel / first output slot
-    int32_t n;        // points in the cloud
-    int32_t c;        // samples
+    int64_t in_xyz;     // first point of the cloud in in_xyz
+    int64_t in_frame;   // first frame index of the cloud in in_frame, or -1
+    int64_t sel;        // first sample in sel (indices relative to the cloud)
+    int64_t out_xyz;    // first output point in out_xyz
+    int64_t out_frame;  // first output entry in out_frame, or -1
+    int64_t sel_frame;  // first output entry in sel_frame, or -1
+    int32_t n;          // points in the cloud
+    int32_t c;          // samples
 };
 cudaError_t launch_gather(const GatherDesc* d_descs, int32_t B, int32_t max_n,
                           const float* in_xyz, const int32_t* in_frame, const int32_t* sel,
                           float* out_xyz, int32_t* out_frame, int32_t* sel_frame,
                           cudaStream_t stream);
 constexpr int32_t kGatherMaxPoints = 65536;
+
+}  // namespace afps
+
+// ---- runtime functions over scattered clouds (afps_api.cu), for the server
+struct afps_ctx;
+namespace afps {
+// Batched sampling of B clouds at arbitrary offsets of one xyz / output base.
+int sample_scattered(afps_ctx* ctx, const float* xyz, int32_t B, const int64_t* pt_begin,
+                     const int64_t* n_pts, const int32_t* C, const int32_t* M, const int32_t* K,
+                     const int64_t* start, int32_t* out, const int64_t* out_begin,
+                     cudaStream_t stream);
+// Gather of B clouds described by host descriptors.
+int gather_run(afps_ctx* ctx, const GatherDesc* descs, int32_t B, const float* in_xyz,
+               const int32_t* in_frame, const int32_t* sel, float* out_xyz, int32_t* out_frame,
+               int32_t* sel_frame, cudaStream_t stream);
 
 }  // namespace afps

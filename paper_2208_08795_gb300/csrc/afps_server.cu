@@ -1,0 +1,429 @@
+// afps_server.cu -- serving runtime: continuous batching of chained NPDU-AFPS
+// requests over one device arena (see the afps_server_* block of afps.h).
+//
+// Each request owns one arena block laid out as
+//   xyz (points, 12 B each):  frame N | cloud 1: C0 | ... | cloud L: C_{L-1}
+//   int32:                    out_0: C0 | ... | out_{L-1} | frame index of
+//                             clouds 1..L-1 | results: C0 + ... + C_{L-1}
+// where cloud l+1 is level l's samples in ascending frame index (built by the
+// gather kernel) and out_l the level's sample indices relative to cloud l.
+// Blocks start on 48-byte boundaries so that every xyz part starts on a point
+// boundary of the arena (point offsets = byte offsets / 12) and every int32
+// part on a 4-byte one.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "../../include/afps.h"
+#include "afps_internal.h"
+
+namespace {
+
+constexpr int64_t kBlockAlign = 48;
+
+struct Block {
+    int64_t off = -1;  // bytes from the arena base
+    int64_t bytes = 0;
+};
+
+// First-fit allocator over the arena with coalescing frees.
+class Arena {
+   public:
+    explicit Arena(int64_t size) { free_[0] = size; }
+    Block alloc(int64_t bytes) {
+        bytes = (bytes + kBlockAlign - 1) / kBlockAlign * kBlockAlign;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                Block b{it->first, bytes};
+                const int64_t rest = it->second - bytes;
+                const int64_t at = it->first + bytes;
+                free_.erase(it);
+                if (rest > 0) free_[at] = rest;
+                used_ += bytes;
+                return b;
+            }
+        }
+        return Block{};
+    }
+    void release(const Block& b) {
+        if (b.off < 0) return;
+        used_ -= b.bytes;
+        auto it = free_.emplace(b.off, b.bytes).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    int64_t used() const { return used_; }
+
+   private:
+    std::map<int64_t, int64_t> free_;
+    int64_t used_ = 0;
+};
+
+enum State { QUEUED, ACTIVE, COMPLETING, DONE };
+
+struct Request {
+    uint64_t tag = 0;
+    int64_t N = 0;
+    std::vector<float> frame;  // host copy until admission
+    State state = QUEUED;
+    int level = 0;             // next level to sample
+    Block block;
+    int slot = -1;             // pinned result slot
+    int64_t xyz_pt[AFPS_SERVER_MAX_LEVELS + 1];  // cloud l, in points from the arena base
+    int64_t out_el[AFPS_SERVER_MAX_LEVELS];      // out_l, in int32 elements
+    int64_t fidx_el[AFPS_SERVER_MAX_LEVELS + 1]; // frame index of cloud l (l >= 1)
+    int64_t res_el = 0;                          // results, all levels
+    cudaEvent_t done_ev = nullptr;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct afps_server {
+    afps_ctx* ctx = nullptr;
+    afps_server_config cfg{};
+    int levels[AFPS_SERVER_MAX_LEVELS] = {};
+    int64_t total_samples = 0;  // sum of levels
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    unsigned char* arena_base = nullptr;
+    std::unique_ptr<Arena> arena;
+    int32_t* pinned = nullptr;  // max_inflight result slots
+    std::vector<int> free_slots;
+    std::deque<std::unique_ptr<Request>> queue;
+    std::vector<std::unique_ptr<Request>> active;  // ACTIVE or COMPLETING
+    std::vector<std::unique_ptr<Request>> done;    // DONE, not yet polled
+    std::vector<std::unique_ptr<Request>> handed;  // returned by the last poll
+    std::deque<cudaEvent_t> step_events;           // steps in flight
+    std::vector<cudaEvent_t> event_pool;
+    std::chrono::steady_clock::time_point t0;
+    double now() const {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+            .count();
+    }
+};
+
+namespace {
+
+int64_t footprint(const afps_server* s, int64_t N) {
+    int64_t pts = N, ints = 0;
+    for (int l = 0; l < s->cfg.n_levels; ++l) {
+        pts += s->levels[l];   // cloud l+1
+        ints += s->levels[l];  // out_l
+        ints += s->levels[l];  // results of level l
+        if (l + 1 < s->cfg.n_levels) ints += s->levels[l];  // frame index of cloud l+1
+    }
+    return 12 * pts + 4 * ints + kBlockAlign;
+}
+
+cudaEvent_t take_event(afps_server* s) {
+    if (!s->event_pool.empty()) {
+        cudaEvent_t e = s->event_pool.back();
+        s->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void give_event(afps_server* s, cudaEvent_t e) {
+    if (e) s->event_pool.push_back(e);
+}
+
+// Finished requests: the device work of their last step has completed.
+void reap(afps_server* s) {
+    for (auto& r : s->active) {
+        if (r && r->state == COMPLETING && cudaEventQuery(r->done_ev) == cudaSuccess) {
+            r->state = DONE;
+            r->t_done = s->now();
+            s->arena->release(r->block);
+            r->block = Block{};
+            give_event(s, r->done_ev);
+            r->done_ev = nullptr;
+            s->done.push_back(std::move(r));
+        }
+    }
+    s->active.erase(std::remove(s->active.begin(), s->active.end(), nullptr), s->active.end());
+    cudaGetLastError();  // cudaEventQuery's cudaErrorNotReady is not an error here
+}
+
+bool admit_one(afps_server* s, Request& r) {
+    if (s->free_slots.empty()) return false;
+    Block b = s->arena->alloc(footprint(s, r.N));
+    if (b.off < 0) return false;
+    r.block = b;
+    r.slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    const int L = s->cfg.n_levels;
+    int64_t pt = b.off / 12;  // b.off is a multiple of 48
+    r.xyz_pt[0] = pt;
+    pt += r.N;
+    for (int l = 0; l < L; ++l) {
+        r.xyz_pt[l + 1] = pt;
+        pt += s->levels[l];
+    }
+    int64_t el = pt * 3;  // int32 elements after the xyz part
+    for (int l = 0; l < L; ++l) {
+        r.out_el[l] = el;
+        el += s->levels[l];
+    }
+    r.fidx_el[0] = -1;
+    for (int l = 1; l < L; ++l) {
+        r.fidx_el[l] = el;
+        el += s->levels[l - 1];
+    }
+    r.res_el = el;
+    r.state = ACTIVE;
+    r.level = 0;
+    r.t_admit = s->now();
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_config* cfg,
+                       void* stream) {
+    if (!out || !ctx || !cfg) return AFPS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cfg->n_levels < 1 || cfg->n_levels > AFPS_SERVER_MAX_LEVELS || cfg->M < 1 ||
+        cfg->npdu_window < 0 || cfg->hbm_budget_bytes <= 0)
+        return AFPS_ERR_INVALID_ARG;
+    for (int l = 0; l < cfg->n_levels; ++l) {
+        if (cfg->levels[l] < 1 || cfg->levels[l] >= 65536) return AFPS_ERR_INVALID_ARG;
+        if (l > 0 && cfg->levels[l] > cfg->levels[l - 1]) return AFPS_ERR_INVALID_ARG;
+    }
+    std::unique_ptr<afps_server> s(new (std::nothrow) afps_server());
+    if (!s) return AFPS_ERR_NO_MEMORY;
+    s->ctx = ctx;
+    s->cfg = *cfg;
+    if (s->cfg.max_inflight <= 0) s->cfg.max_inflight = 256;
+    if (s->cfg.max_queued <= 0) s->cfg.max_queued = 4096;
+    if (s->cfg.max_steps_ahead <= 0) s->cfg.max_steps_ahead = 2;
+    for (int l = 0; l < cfg->n_levels; ++l) {
+        s->levels[l] = cfg->levels[l];
+        s->total_samples += cfg->levels[l];
+    }
+    s->t0 = std::chrono::steady_clock::now();
+    if (cudaGetDevice(&s->device) != cudaSuccess) return AFPS_ERR_CUDA;
+    if (stream) {
+        s->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return AFPS_ERR_CUDA;
+        s->own_stream = true;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)cfg->hbm_budget_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        return AFPS_ERR_NO_MEMORY;
+    }
+    s->arena_base = static_cast<unsigned char*>(p);
+    s->arena.reset(new Arena(cfg->hbm_budget_bytes / kBlockAlign * kBlockAlign));
+    void* h = nullptr;
+    if (cudaMallocHost(&h, (size_t)s->cfg.max_inflight * s->total_samples * sizeof(int32_t)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        return AFPS_ERR_NO_MEMORY;
+    }
+    s->pinned = static_cast<int32_t*>(h);
+    for (int i = s->cfg.max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
+    *out = s.release();
+    return AFPS_OK;
+}
+
+int afps_server_submit(afps_server* s, const float* h_xyz, int64_t N, uint64_t tag) {
+    if (!s || !h_xyz || N < s->levels[0] || N > 65536) return AFPS_ERR_INVALID_ARG;
+    if (footprint(s, N) > s->cfg.hbm_budget_bytes) return AFPS_ERR_INVALID_ARG;
+    if ((int64_t)s->queue.size() >= s->cfg.max_queued) return AFPS_ERR_BUSY;
+    std::unique_ptr<Request> r(new (std::nothrow) Request());
+    if (!r) return AFPS_ERR_NO_MEMORY;
+    r->tag = tag;
+    r->N = N;
+    r->frame.assign(h_xyz, h_xyz + 3 * N);
+    r->t_submit = s->now();
+    s->queue.push_back(std::move(r));
+    return AFPS_OK;
+}
+
+int afps_server_step(afps_server* s) {
+    if (!s) return AFPS_ERR_INVALID_ARG;
+    // stay at most max_steps_ahead steps ahead of the GPU
+    while ((int)s->step_events.size() >= s->cfg.max_steps_ahead) {
+        cudaEvent_t e = s->step_events.front();
+        s->step_events.pop_front();
+        cudaError_t err = cudaEventSynchronize(e);
+        give_event(s, e);
+        if (err != cudaSuccess) return AFPS_ERR_CUDA;
+    }
+    while (!s->step_events.empty() && cudaEventQuery(s->step_events.front()) == cudaSuccess) {
+        give_event(s, s->step_events.front());
+        s->step_events.pop_front();
+    }
+    cudaGetLastError();
+    reap(s);
+
+    // admission, first come first served, by arena footprint and slots
+    float* xyz = reinterpret_cast<float*>(s->arena_base);
+    int32_t* ints = reinterpret_cast<int32_t*>(s->arena_base);
+    while (!s->queue.empty() && (int)s->active.size() < s->cfg.max_inflight) {
+        Request& r = *s->queue.front();
+        if (!admit_one(s, r)) break;
+        if (cudaMemcpyAsync(xyz + 3 * r.xyz_pt[0], r.frame.data(), r.frame.size() * sizeof(float),
+                            cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return AFPS_ERR_CUDA;
+        }
+        std::vector<float>().swap(r.frame);
+        s->active.push_back(std::move(s->queue.front()));
+        s->queue.pop_front();
+    }
+
+    // one batched sampling launch over every active request's current level
+    std::vector<Request*> run;
+    for (auto& r : s->active)
+        if (r->state == ACTIVE) run.push_back(r.get());
+    if (run.empty()) return 0;
+    const int32_t B = (int32_t)run.size();
+    std::vector<int64_t> pt_begin(B), n_pts(B), start(B, 0), out_begin(B);
+    std::vector<int32_t> C(B), M(B), K(B, s->cfg.npdu_window);
+    std::vector<afps::GatherDesc> g(B);
+    for (int32_t b = 0; b < B; ++b) {
+        Request& r = *run[b];
+        const int l = r.level;
+        const int64_t n = l == 0 ? r.N : s->levels[l - 1];
+        pt_begin[b] = r.xyz_pt[l];
+        n_pts[b] = n;
+        C[b] = s->levels[l];
+        M[b] = std::min(s->cfg.M, C[b]);
+        out_begin[b] = r.out_el[l];
+        afps::GatherDesc& d = g[b];
+        d.in_xyz = r.xyz_pt[l];
+        d.in_frame = r.fidx_el[l];  // -1 at level 0: the frame itself
+        d.sel = r.out_el[l];
+        d.out_xyz = r.xyz_pt[l + 1];
+        d.out_frame = l + 1 < s->cfg.n_levels ? r.fidx_el[l + 1] : -1;
+        int64_t res = r.res_el;
+        for (int q = 0; q < l; ++q) res += s->levels[q];
+        d.sel_frame = res;
+        d.n = (int32_t)n;
+        d.c = C[b];
+    }
+    int rc = afps::sample_scattered(s->ctx, xyz, B, pt_begin.data(), n_pts.data(), C.data(),
+                                    M.data(), K.data(), start.data(), ints, out_begin.data(),
+                                    s->stream);
+    if (rc != AFPS_OK) return rc;
+    rc = afps::gather_run(s->ctx, g.data(), B, xyz, ints, ints, xyz, ints, ints, s->stream);
+    if (rc != AFPS_OK) return rc;
+
+    // finished chains: copy their results to pinned memory
+    cudaEvent_t fin = nullptr;
+    for (Request* r : run) {
+        if (++r->level < s->cfg.n_levels) continue;
+        if (cudaMemcpyAsync(s->pinned + (int64_t)r->slot * s->total_samples, ints + r->res_el,
+                            (size_t)s->total_samples * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            s->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return AFPS_ERR_CUDA;
+        }
+        r->state = COMPLETING;
+        if (!fin) fin = take_event(s);
+    }
+    if (fin) {
+        if (cudaEventRecord(fin, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
+        // each finishing request keeps its own handle on the step's completion
+        bool first = true;
+        for (Request* r : run) {
+            if (r->state != COMPLETING || r->done_ev) continue;
+            if (first) {
+                r->done_ev = fin;
+                first = false;
+            } else {
+                cudaEvent_t e = take_event(s);
+                if (!e || cudaEventRecord(e, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
+                r->done_ev = e;
+            }
+        }
+    }
+    cudaEvent_t se = take_event(s);
+    if (!se || cudaEventRecord(se, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
+    s->step_events.push_back(se);
+    return B;
+}
+
+int afps_server_poll(afps_server* s, afps_server_result* out, int32_t max_results) {
+    if (!s || (!out && max_results > 0)) return AFPS_ERR_INVALID_ARG;
+    // results handed out by the previous poll give their slots back now
+    for (auto& r : s->handed) s->free_slots.push_back(r->slot);
+    s->handed.clear();
+    reap(s);
+    int n = 0;
+    while (n < max_results && !s->done.empty()) {
+        std::unique_ptr<Request> r = std::move(s->done.front());
+        s->done.erase(s->done.begin());
+        afps_server_result& o = out[n++];
+        memset(&o, 0, sizeof(o));
+        o.tag = r->tag;
+        o.status = AFPS_OK;
+        o.n_levels = s->cfg.n_levels;
+        for (int l = 0; l < s->cfg.n_levels; ++l) o.count[l] = s->levels[l];
+        o.indices = s->pinned + (int64_t)r->slot * s->total_samples;
+        o.submit_ms = r->t_submit;
+        o.admit_ms = r->t_admit;
+        o.done_ms = r->t_done;
+        s->handed.push_back(std::move(r));
+    }
+    return n;
+}
+
+int afps_server_stats(afps_server* s, int64_t* queued, int64_t* inflight, int64_t* arena_used) {
+    if (!s) return AFPS_ERR_INVALID_ARG;
+    if (queued) *queued = (int64_t)s->queue.size();
+    if (inflight) *inflight = (int64_t)s->active.size();
+    if (arena_used) *arena_used = s->arena->used();
+    return AFPS_OK;
+}
+
+double afps_server_clock_ms(const afps_server* s) { return s ? s->now() : 0.0; }
+
+void afps_server_destroy(afps_server* s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    for (auto& r : s->active)
+        if (r && r->done_ev) cudaEventDestroy(r->done_ev);
+    for (cudaEvent_t e : s->step_events) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+    if (s->arena_base) cudaFree(s->arena_base);
+    if (s->pinned) cudaFreeHost(s->pinned);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    cudaGetLastError();
+    delete s;
+}
+
+}  // extern "C"

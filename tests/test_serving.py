@@ -1,0 +1,91 @@
+"""Serving runtime: continuous batching of chained requests
+16384 -> 4096 -> 1024 -> 256 (NPDU-AFPS, M = 32, k = 16) on LiDAR-like
+frames.  Every result must equal the oracle's chained sampling and the same
+frame served alone, whatever else shares the GPU steps."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_08795_gb300 import afps as B
+from paper_2208_08795_gb300 import build as build_mod
+from paper_2208_08795_gb300 import serving, synth
+
+pytestmark = pytest.mark.gpu
+
+LEVELS = [16384, 4096, 1024, 256]
+
+
+@pytest.fixture(scope="module")
+def sampler():
+    build_mod.build()
+    s = B.Sampler(0)
+    yield s
+    s.close()
+
+
+def drain(server, n):
+    done = {}
+    while len(done) < n:
+        server.step()
+        for r in server.poll():
+            done[r.tag] = r
+    return done
+
+
+def test_mixed_stream_matches_oracle_and_alone(sampler):
+    frames = [synth.lidar_frame(s) for s in range(10)]
+    # a budget for about three requests at once: the rest waits for admission
+    srv = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=3_000_000)
+    try:
+        for t, f in enumerate(frames):
+            assert srv.submit(f, t) == 0
+        q, inflight, used = srv.stats()
+        assert q == len(frames)
+        srv.step()
+        q, inflight, used = srv.stats()
+        assert 1 <= inflight < len(frames) and q == len(frames) - inflight and used <= 3_000_000
+        mixed = drain(srv, len(frames))
+    finally:
+        srv.close()
+    for t, f in enumerate(frames):
+        ref = oracle.chain(f, LEVELS, 32, 16)
+        for l in range(len(LEVELS)):
+            assert np.array_equal(mixed[t].levels[l], ref[l]), (t, l)
+        assert mixed[t].submit_ms <= mixed[t].admit_ms <= mixed[t].done_ms
+    alone = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=3_000_000)
+    try:
+        for t in (0, 7):
+            assert alone.submit(frames[t], 100 + t) == 0
+            r = drain(alone, 1)[100 + t]
+            for l in range(len(LEVELS)):
+                assert np.array_equal(r.levels[l], mixed[t].levels[l]), (t, l)
+    finally:
+        alone.close()
+
+
+def test_poisson_stream_completes(sampler):
+    frames = [synth.lidar_frame(s) for s in range(4)]
+    srv = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=64 << 20)
+    try:
+        res = serving.poisson_run(srv, frames, rate_hz=2000.0, n_requests=60, seed=1,
+                                  keep_results=True)
+    finally:
+        srv.close()
+    assert res["requests"] == 60 and res["p99_ms"] >= res["p50_ms"] > 0
+    ref0 = oracle.chain(frames[0], LEVELS, 32, 16)
+    for t in (0, 4, 8):
+        for l in range(len(LEVELS)):
+            assert np.array_equal(res["results"][t].levels[l], ref0[l])
+
+
+def test_submit_rejects_bad_frames(sampler):
+    srv = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=3_000_000, max_queued=1)
+    try:
+        small = synth.uniform_cloud(1, 1000)
+        assert srv.submit(small, 0) == B.AFPS_ERR_INVALID_ARG  # fewer points than level 0
+        f = synth.lidar_frame(3)
+        assert srv.submit(f, 1) == 0
+        assert srv.submit(f, 2) == B.AFPS_ERR_BUSY  # queue of one is full
+        drain(srv, 1)
+    finally:
+        srv.close()
