@@ -248,6 +248,60 @@ def kernel_source_hash() -> str:
 NCU_TRAFFIC = {"source_hash": None, "bytes_per_launch": None}
 
 
+# ------------------------------------------------------------------ other configs
+def time_batch(sampler, x, ba, out, steps, warmup, flush):
+    """Autotune (untimed), then per-step device time; returns (mean ms, p99 ms)."""
+    sampler.autotune_batched(x, ba, out)
+    sampler.sync()
+    ms, _ = time_device(sampler, x, ba, out, steps, warmup, flush)
+    return float(np.mean(ms)), float(pct(ms, 99))
+
+
+def large_clouds(sampler, flush, dev, steps: int):
+    """Single large clouds N in {8192, 16384, 32768} (1 x 1 x 0.2 slab with 5%
+    Gaussian bumps, sorted by x), C = N/4: plain FPS (M = 1, one thread-block
+    cluster) and NPDU-AFPS with M in {8, 32, 64, 128}."""
+    import torch
+    from paper_2208_08795_gb300 import afps as A, synth
+    rows = []
+    for N in (8192, 16384, 32768):
+        P = synth.slab_cloud(2, N)
+        x = torch.from_numpy(P).to(dev)
+        for M, k in ((1, 0), (8, 8), (32, 16), (64, 16), (128, 16)):
+            ba = A.BatchArgs([0, N], N // 4, M, k, 0)
+            out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
+            ms, p99 = time_batch(sampler, x, ba, out, steps, 3, flush)
+            plan = sampler.describe_plan(-(-N // M), -(-(N // 4) // M), k, M)
+            rows.append({"N": N, "C": N // 4, "M": M, "k": k, "ms": round(ms, 4),
+                         "p99_ms": round(p99, 4), "variant": plan})
+    for r in rows:  # speedup over plain FPS at equal N and C
+        base = next(b for b in rows if b["N"] == r["N"] and b["M"] == 1)
+        r["speedup_vs_fps"] = round(base["ms"] / r["ms"], 2)
+    return {"workload": "slab clouds 8K/16K/32K, C=N/4", "runs": rows}
+
+
+def ragged_batch(sampler, flush, dev, steps: int):
+    """256 object-scale clouds, N ~ U[2048, 32768], C = N/4, M = round(N/256)
+    (sectors of about 256 points), NPDU k = 16: all (cloud, sector) items in
+    one persistent launch, replayed from a CUDA graph, variant autotuned."""
+    import torch
+    from paper_2208_08795_gb300 import afps as A, synth
+    clouds, Cs, Ms = synth.ragged_batch(3, 256)
+    xyz, off = synth.pack(clouds)
+    x = torch.from_numpy(xyz).to(dev)
+    res = {}
+    for k in (0, 16):
+        ba = A.BatchArgs(off, Cs, Ms, k, 0)
+        out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
+        ms, p99 = time_batch(sampler, x, ba, out, steps, 3, flush)
+        res["npdu" if k else "full"] = {"ms": round(ms, 4), "p99_ms": round(p99, 4),
+                                        "clouds_per_s": round(256 / (ms / 1e3), 1),
+                                        "hbm_gbs": round((12 * int(off[-1]) + 4 * ba.total_out)
+                                                         / (ms / 1e3) / 1e9, 1)}
+    return {"workload": f"ragged batch of 256 clouds, {int(off[-1])} points, "
+                        f"{sum(Ms)} sectors, C=N/4", **res}
+
+
 # ------------------------------------------------------------------ serving
 SERVING_LEVELS = [16384, 4096, 1024, 256]
 SERVING_RATES = [500.0, 2000.0, 8000.0, 32000.0]
@@ -381,6 +435,9 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     barrier()
     e2e_ms = max_over_ranks(float(np.mean(ts)), world, dev)
     serving_stats = serving_sweep(sampler) if args.serving else None
+    extra_steps = max(5, min(args.steps, 20))
+    large = large_clouds(sampler, flush, dev, extra_steps) if args.configs else None
+    ragged = ragged_batch(sampler, flush, dev, extra_steps) if args.configs else None
     clk = clocks.stop()
     e2e_ok = bool(np.array_equal(h_out, head_out))
 
@@ -424,6 +481,8 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
                 "h2d_bytes_per_step": int(h_xyz.nbytes), "d2h_bytes_per_step": int(h_out.nbytes),
                 "matches_device_path": e2e_ok},
         "serving": serving_stats,
+        "large_clouds": large,
+        "ragged_batch": ragged,
         "gpu_launches": launches,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
@@ -467,6 +526,8 @@ def main(argv=None) -> int:
     ap.add_argument("--cpu-seconds", type=float, default=5.0)
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the serving sweep")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the large-cloud and ragged-batch sections")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
