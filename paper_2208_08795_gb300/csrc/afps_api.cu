@@ -202,7 +202,7 @@ CloudCheck check_cloud(int64_t N, int32_t C, int32_t M, int32_t k, int64_t start
 }
 
 // ---------------------------------------------------------------- variants
-const int kWarpP[] = {1, 2, 3, 4, 6, 8, 12, 16};
+const int kWarpP[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
 const int kCtaP[] = {2, 4, 8, 16};
 
 // Default variant for sectors of up to n_max points.
@@ -246,7 +246,7 @@ Variant default_variant(int64_t n_max) {
 // and without the NPDU row skip when the class uses NPDU).
 std::vector<Variant> candidate_variants(int64_t n_max, bool npdu) {
     std::vector<Variant> out;
-    if (n_max <= 512) {
+    if (n_max <= 1024) {
         for (int P : kWarpP) {
             if (32LL * P < n_max) continue;
             for (int W : {2, 4, 8}) out.push_back(Variant{afps::KIND_WARP, P, W, 1, 0, 0});
@@ -846,6 +846,8 @@ int afps_sync(afps_ctx* ctx, void* stream) {
         return fail(ctx, AFPS_ERR_TIMEOUT,
                     status == afps::DEV_TIMEOUT_STAGE
                         ? "a stage-in bulk copy did not complete within the timeout"
+                    : status == afps::DEV_TIMEOUT_EXCHANGE
+                        ? "a cluster record exchange did not complete within the timeout"
                         : "a bulk copy was still in flight after the drain timeout");
     }
     return AFPS_OK;

@@ -116,6 +116,16 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint32_t a, uint32_
                  "r"(b), "r"(c), "r"(d)
                  : "memory");
 }
+// Asynchronous 16-byte store into another CTA's shared memory whose
+// completion is counted (as bytes) on that CTA's mbarrier `remote_bar`.
+__device__ __forceinline__ void st_async_v4(uint32_t remote_addr, uint32_t remote_bar, uint32_t a,
+                                            uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%2, %3, %4, %5}, "
+        "[%1];" ::"r"(remote_addr),
+        "r"(remote_bar), "r"(a), "r"(b), "r"(c), "r"(d)
+        : "memory");
+}
 // Full cluster barrier with release/acquire ordering of shared::cluster memory.
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");

@@ -58,7 +58,12 @@ struct LaunchArgs {
 };
 
 // Device error codes written to *status.
-enum DeviceStatus : int { DEV_OK = 0, DEV_TIMEOUT_STAGE = 1, DEV_TIMEOUT_DRAIN = 2 };
+enum DeviceStatus : int {
+    DEV_OK = 0,
+    DEV_TIMEOUT_STAGE = 1,     // a stage-in bulk copy did not complete in time
+    DEV_TIMEOUT_DRAIN = 2,     // ... nor within the second, draining wait
+    DEV_TIMEOUT_EXCHANGE = 3,  // a cluster record exchange did not complete in time
+};
 
 // Points a variant can hold per item.
 inline int64_t variant_capacity(const Variant& v) {

@@ -182,6 +182,8 @@ SectorKernel warp_kernel_for(int P, bool npdu) {
         AFPS_WARP_CASE(8)
         AFPS_WARP_CASE(12)
         AFPS_WARP_CASE(16)
+        AFPS_WARP_CASE(24)
+        AFPS_WARP_CASE(32)
         default:
             return nullptr;
     }

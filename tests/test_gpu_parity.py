@@ -174,18 +174,23 @@ VARIANTS = [  # (N, C, M, k, kind, P, W, CS)
     (3000, 300, 10, 0, 0, 12, 1, 1), (3000, 300, 10, 0, 0, 16, 8, 1), (3000, 300, 10, 9, 0, 12, 2, 1),
     (640, 640, 20, 0, 0, 1, 8, 1), (640, 640, 20, 0, 0, 2, 4, 1), (640, 640, 20, 16, 0, 1, 8, 1),
     (2000, 400, 100, 4, 0, 1, 4, 1), (2000, 500, 8, 0, 0, 8, 8, 1), (2000, 500, 8, 12, 0, 8, 4, 1),
+    (5000, 1000, 6, 0, 0, 32, 2, 1), (5000, 1000, 6, 16, 0, 32, 4, 1, 1),
+    (4000, 800, 6, 16, 0, 24, 4, 1), (4000, 800, 6, 9, 0, 24, 2, 1, 1),
+    (3000, 600, 4, 16, 1, 4, 8, 1, 1), (20000, 2000, 2, 8, 1, 8, 8, 5, 1),
 ]
 
 
-@pytest.mark.parametrize("N,C,M,k,kind,Pp,W,CS", VARIANTS)
-def test_forced_variant(tmp_path, N, C, M, k, kind, Pp, W, CS):
+@pytest.mark.parametrize("row", VARIANTS, ids=[str(r) for r in VARIANTS])
+def test_forced_variant(tmp_path, row):
     """Pin one kernel variant through the tuning cache and compare."""
+    N, C, M, k, kind, Pp, W, CS = row[:8]
+    skip = row[8] if len(row) > 8 else 0
     build_mod.build()
     n_max = -(-N // M)
     c_max = -(-C // M)
     key = f"{'npdu' if k else 'full'}:n{n_max}:c{c_max}:i{pow2(M)}"
     path = tmp_path / "tune.txt"
-    path.write_text(f"{key} {kind} {Pp} {W} {CS} 0\n")
+    path.write_text(f"{key} {kind} {Pp} {W} {CS} 0 {skip}\n")
     s = B.Sampler(0, tune_cache=str(path))
     try:
         desc = s.describe_plan(n_max, c_max, k, M)
@@ -195,6 +200,8 @@ def test_forced_variant(tmp_path, N, C, M, k, kind, Pp, W, CS):
             want = f"cluster P={Pp} W={W} CS={CS}"
         else:
             want = f"cta P={Pp} W={W}"
+        if skip:
+            want += " skip"
         P = synth.uniform_cloud(N + 31 * M + k, N)
         x = torch.from_numpy(P).cuda()
         out = s.sample(x, C, M, k, 1)
