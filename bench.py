@@ -232,11 +232,15 @@ def npdu_work(out_idx, ba, k):
     return evals, compares
 
 
+HEADLINE_KERNEL_SOURCES = ("afps_warp.cu", "afps_device.cuh", "afps_internal.h")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources the headline kernel (afps_warp_kernel) is built from."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2208_08795_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in HEADLINE_KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -245,7 +249,7 @@ def kernel_source_hash() -> str:
 # DRAM traffic of the headline kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum per launch), valid only for the kernel sources it was
 # taken on (their hash); otherwise reported as null.
-NCU_TRAFFIC = {"source_hash": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"source_hash": "53903cfcbf0212d1", "bytes_per_launch": 844032}
 
 
 # ------------------------------------------------------------------ other configs

@@ -1,0 +1,75 @@
+"""Single sampling workloads, run a few times, for profiling with ncu.
+
+    python -m paper_2208_08795_gb300.profile_cases <case> [--reps R]
+
+Cases (inputs from `synth`, kernel variants from the default planner):
+  headline     32 object clouds x 2048 points, C = 512, NPDU-AFPS M = 32, k = 16 (batched)
+  fps2048      the same batch, plain FPS (M = 1)
+  cluster32k   one 32768-point slab cloud, C = 8192, plain FPS (one thread-block cluster)
+  npdu32k      the same cloud, NPDU-AFPS M = 32, k = 16
+  ragged       256 clouds of 2K-32K points, C = N/4, sectors of ~256 points, k = 16 (persistent)
+  chain        one LiDAR-like frame, levels 16384 -> 4096 -> 1024 -> 256, M = 32, k = 16
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+import torch
+
+from . import afps, build, synth
+
+CASES = ("headline", "fps2048", "cluster32k", "npdu32k", "ragged", "chain")
+
+
+def run(case: str, reps: int) -> None:
+    build.build()
+    s = afps.Sampler(0)
+    dev = torch.device("cuda", 0)
+    if case in ("headline", "fps2048", "ragged"):
+        if case == "ragged":
+            clouds, C, M = synth.ragged_batch(3, 256)
+            k = 16
+        else:
+            clouds, C = synth.object_batch(1, 32, 2048), 512
+            M, k = (32, 16) if case == "headline" else (1, 0)
+        xyz, off = synth.pack(clouds)
+        x = torch.from_numpy(xyz).to(dev)
+        ba = afps.BatchArgs(off, C, M, k, 0)
+        out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
+        for _ in range(reps):
+            s.sample_batched(x, ba, out=out)
+    elif case in ("cluster32k", "npdu32k"):
+        x = torch.from_numpy(synth.slab_cloud(2, 32768)).to(dev)
+        M, k = (1, 0) if case == "cluster32k" else (32, 16)
+        for _ in range(reps):
+            s.sample(x, 8192, M, k, 0)
+    elif case == "chain":
+        frame = torch.from_numpy(synth.lidar_frame(5)).to(dev)
+        for _ in range(reps):
+            cloud, fidx = frame, None
+            for C in (16384, 4096, 1024, 256):
+                n = cloud.shape[0]
+                sel = s.sample(cloud, C, 32, 16, 0)
+                nxt = torch.empty((C, 3), dtype=torch.float32, device=dev)
+                nfr = torch.empty(C, dtype=torch.int32, device=dev)
+                s.gather_levels([0, n], cloud, fidx, [0, C], sel, nxt, nfr)
+                cloud, fidx = nxt, nfr
+    else:
+        raise SystemExit(f"unknown case {case!r}; one of {', '.join(CASES)}")
+    s.sync()
+    s.close()
+    print(f"{case}: {reps} runs ok")
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("case", choices=CASES)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args(argv)
+    run(a.case, a.reps)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
