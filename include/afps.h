@@ -143,7 +143,8 @@ int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h
  *   d_out_frame d_in_frame[...] of those points in that order (the original
  *               frame index; d_in_frame NULL means the identity),
  *   d_sel_frame d_in_frame[sel] in the samples' own order (may be NULL).
- * Outputs use the h_sel_off layout.  Clouds up to 65536 points.
+ * Outputs use the h_sel_off layout and must not overlap the inputs.  Clouds
+ * up to 65536 points.
  */
 int afps_gather_levels(afps_ctx* ctx, int32_t B, const int64_t* h_in_pt_off,
                        const float* d_in_xyz, const int32_t* d_in_frame,

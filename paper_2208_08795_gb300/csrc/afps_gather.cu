@@ -5,10 +5,13 @@
 // previous samples taken in ascending storage index, which preserves the
 // storage order and so the dimensional locality that AFPS and NPDU rely on
 // (Sec. III-A).  One CTA per cloud: a counting sort over the cloud's n points
-// (16-bit counters in shared memory, two per word), a block-wide exclusive
-// scan, then a scatter of points and original frame indices in ascending
-// order.  Counting (not flags) keeps repeated indices, should a degenerate
-// cloud produce any.
+// (16-bit counters in shared memory, two per word) and a block-wide exclusive
+// scan give every sample its destination; each thread writes the source index
+// of the samples in its range of points to their destinations, then all
+// threads copy points and original frame indices for consecutive
+// destinations in parallel.  Counting (not flags) keeps repeated indices,
+// should a degenerate cloud produce any.  The output xyz must not overlap the
+// input.
 #include "afps_device.cuh"
 
 namespace afps {
@@ -18,30 +21,36 @@ __global__ void __launch_bounds__(1024) afps_gather_kernel(
     const int32_t* __restrict__ in_frame, const int32_t* __restrict__ sel,
     float* __restrict__ out_xyz, int32_t* __restrict__ out_frame,
     int32_t* __restrict__ sel_frame) {
-    extern __shared__ __align__(16) uint32_t cnt[];  // (n + 1) / 2 words + 32 warp sums
+    extern __shared__ __align__(16) uint32_t cnt[];  // (n + 1) / 2 words of two 16-bit counters
     __shared__ uint32_t warp_sum[32];
+    __shared__ uint32_t total;
     const GatherDesc d = descs[blockIdx.x];
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int n = d.n, c = d.c;
     const int words = (n + 1) >> 1;
 
+    // 1. count the samples of every point
     for (int i = tid; i < words; i += T) cnt[i] = 0u;
     __syncthreads();
-    for (int s = tid; s < c; s += T) {
-        const int j = sel[d.sel + s];
-        if (j >= 0 && j < n) {
-            atomicAdd(&cnt[j >> 1], 1u << (16 * (j & 1)));
-            if (d.sel_frame >= 0) sel_frame[d.sel_frame + s] = d.in_frame >= 0 ? in_frame[d.in_frame + j] : j;
+    constexpr int kBatch = 8;  // loads in flight per thread
+    for (int s0 = 0; s0 < c; s0 += kBatch * T) {
+        int jv[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int s = s0 + u * T + tid;
+            jv[u] = s < c ? sel[d.sel + s] : -1;
         }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (jv[u] >= 0 && jv[u] < n) atomicAdd(&cnt[jv[u] >> 1], 1u << (16 * (jv[u] & 1)));
     }
     __syncthreads();
 
-    // each thread owns points [j0, j1)
+    // 2. exclusive scan over points; thread t owns points [j0, j1)
     const int per = (n + T - 1) / T;
     const int j0 = min(n, tid * per), j1 = min(n, j0 + per);
     uint32_t local = 0;
     for (int j = j0; j < j1; ++j) local += (cnt[j >> 1] >> (16 * (j & 1))) & 0xffffu;
-    // block exclusive scan of `local`
     uint32_t incl = local;
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t v = __shfl_up_sync(dev::kFull, incl, o);
@@ -51,29 +60,74 @@ __global__ void __launch_bounds__(1024) afps_gather_kernel(
     __syncthreads();
     if (w == 0) {
         const int nw = T >> 5;
-        uint32_t v = lane < nw ? warp_sum[lane] : 0u;
+        const uint32_t v = lane < nw ? warp_sum[lane] : 0u;
         uint32_t inc = v;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t u = __shfl_up_sync(dev::kFull, inc, o);
             if (lane >= o) inc += u;
         }
         if (lane < nw) warp_sum[lane] = inc - v;  // exclusive prefix of warps
+        if (lane == nw - 1) total = inc;
     }
     __syncthreads();
-    uint32_t pos = warp_sum[w] + incl - local;
 
+    // 3. destination of every sample: its point index goes into the first
+    //    word of the destination's xyz slot (overwritten in step 4)
+    int32_t* slot = reinterpret_cast<int32_t*>(out_xyz) + 3 * d.out_xyz;
+    uint32_t pos = warp_sum[w] + incl - local;
     for (int j = j0; j < j1; ++j) {
-        uint32_t k = (cnt[j >> 1] >> (16 * (j & 1))) & 0xffffu;
-        if (!k) continue;
-        const float* src = in_xyz + 3 * (d.in_xyz + j);
-        const float px = src[0], py = src[1], pz = src[2];
-        const int32_t fr = d.in_frame >= 0 ? in_frame[d.in_frame + j] : j;
-        for (; k; --k, ++pos) {
-            float* dst = out_xyz + 3 * (d.out_xyz + pos);
-            dst[0] = px;
-            dst[1] = py;
-            dst[2] = pz;
-            if (d.out_frame >= 0) out_frame[d.out_frame + pos] = fr;
+        for (uint32_t k = (cnt[j >> 1] >> (16 * (j & 1))) & 0xffffu; k; --k, ++pos)
+            slot[3 * pos] = j;
+    }
+    __syncthreads();
+
+    // 4. all threads copy consecutive destinations, kBatch loads in flight
+    const int m = (int)total;
+    for (int i0 = 0; i0 < m; i0 += kBatch * T) {
+        int jv[kBatch];
+        float px[kBatch], py[kBatch], pz[kBatch];
+        int32_t fr[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int i = i0 + u * T + tid;
+            jv[u] = i < m ? slot[3 * i] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const float* src = in_xyz + 3 * (d.in_xyz + jv[u]);
+            px[u] = src[0];
+            py[u] = src[1];
+            pz[u] = src[2];
+            fr[u] = d.in_frame >= 0 ? in_frame[d.in_frame + jv[u]] : jv[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int i = i0 + u * T + tid;
+            if (i < m) {
+                float* dst = out_xyz + 3 * (d.out_xyz + i);
+                dst[0] = px[u];
+                dst[1] = py[u];
+                dst[2] = pz[u];
+                if (d.out_frame >= 0) out_frame[d.out_frame + i] = fr[u];
+            }
+        }
+    }
+
+    // 5. frame index of every sample in its own (emission) order
+    if (d.sel_frame >= 0) {
+        for (int s0 = 0; s0 < c; s0 += kBatch * T) {
+            int jv[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int s = s0 + u * T + tid;
+                jv[u] = s < c ? sel[d.sel + s] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int s = s0 + u * T + tid;
+                if (s < c && jv[u] >= 0 && jv[u] < n)
+                    sel_frame[d.sel_frame + s] = d.in_frame >= 0 ? in_frame[d.in_frame + jv[u]] : jv[u];
+            }
         }
     }
 }
