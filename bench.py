@@ -190,13 +190,21 @@ def time_device(sampler, x, ba, out, steps: int, warmup: int, flush):
 
 
 def time_e2e(sampler, h_xyz, ba, h_out, steps: int, warmup: int):
-    """Host buffers in, host indices out, copies inside each timed call."""
+    """The C-ABI call afps_sample_batched_host on pinned host buffers: the
+    host-to-device copy of the points, the sampling and the device-to-host copy
+    of the indices are inside each timed call (which returns after the copy)."""
+    import torch
+    from paper_2208_08795_gb300 import afps as A
+    fn = A.load().afps_sample_batched_host
+    args = (sampler.ctx, h_xyz.ctypes.data, *ba.args(), h_out.ctypes.data,
+            torch.cuda.current_stream().cuda_stream)
     for _ in range(warmup):
-        sampler.sample_batched_host(h_xyz, ba, h_out)
+        if fn(*args) != 0:
+            raise A.AfpsError(-1, A.afps_last_error(sampler.ctx))
     ts = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        sampler.sample_batched_host(h_xyz, ba, h_out)
+        fn(*args)
         ts.append((time.perf_counter() - t0) * 1e3)
     return ts
 

@@ -123,10 +123,15 @@ int afps_sample_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_o
                         const int64_t* h_out_off, int32_t* d_out, void* stream);
 
 /*
- * afps_sample_batched on HOST buffers: copies h_xyz (h_pt_off[B] points) to
- * context-owned device memory, samples, copies the h_out_off[B] indices back
- * to h_out and waits for the stream.  Pinned host memory makes the copies
- * asynchronous DMA; pageable memory works but is slower.  Synchronous.
+ * afps_sample_batched on HOST buffers (h_pt_off[0] = h_out_off[0] = 0):
+ * samples the h_pt_off[B] points of h_xyz, writes the h_out_off[B] indices to
+ * h_out and waits for the stream before returning.  Pageable memory: copies
+ * through context-owned device memory.  Page-locked memory with
+ * AFPS_FLAG_GRAPH: one cached CUDA graph per argument set (pointers
+ * included); when the buffers are mapped into the device's address space the
+ * kernels read the points and write the indices in host memory directly (on
+ * Grace-Blackwell over the coherent C2C link), otherwise the graph holds the
+ * two copies around device staging.  Synchronous.
  */
 int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off,
                              int32_t B, const int32_t* h_C, const int32_t* h_M,

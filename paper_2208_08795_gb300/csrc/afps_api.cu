@@ -88,6 +88,7 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     DevBuf items;
     DevBuf counters;
+    DevBuf xyz, out;  // device staging of a host-buffer graph
     int64_t kernels = 0;
     uint64_t last_use = 0;
 };
@@ -333,7 +334,7 @@ int grid_for(const Variant& v, size_t count) {
 
 int launch_class(afps_ctx* ctx, const Variant& v, bool npdu, const ItemDesc* d_items,
                  size_t count, unsigned int* d_counter, const float* xyz, int32_t* out,
-                 cudaStream_t stream) {
+                 cudaStream_t stream, bool host_resident = false) {
     LaunchArgs a{};
     a.xyz = xyz;
     a.items = d_items;
@@ -349,6 +350,7 @@ int launch_class(afps_ctx* ctx, const Variant& v, bool npdu, const ItemDesc* d_i
     a.timeout_ns = ctx->timeout_ns;
     a.stall_copy = (ctx->flags & AFPS_FLAG_TEST_STALL_COPY) ? 1u : 0u;
     a.npdu_skip = v.skip ? 1u : 0u;
+    a.host_resident = host_resident ? 1u : 0u;
     if (a.counter) AFPS_CUDA(ctx, cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), stream));
     cudaError_t e = afps::launch_sector(v, npdu, a, grid, stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sector kernel launch");
@@ -514,6 +516,8 @@ void drop_graph(GraphEntry& g) {
     g.exec = nullptr;
     g.items.release();
     g.counters.release();
+    g.xyz.release();
+    g.out.release();
 }
 
 void clear_graphs(afps_ctx* ctx) {
@@ -526,7 +530,8 @@ void clear_graphs(afps_ctx* ctx) {
 // Capture the plan's launches (counter resets + one kernel per class) into a
 // graph that owns its own item table, so replays need no upload.
 int make_graph(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* d_out,
-               GraphEntry& g) {
+               GraphEntry& g, const float* h_xyz = nullptr, size_t xyz_bytes = 0,
+               int32_t* h_out = nullptr, size_t out_bytes = 0, bool host_resident = false) {
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);
     AFPS_CUDA(ctx, g.items.reserve(bytes));
     AFPS_CUDA(ctx, g.counters.reserve(plan.classes.size() * sizeof(unsigned int)));
@@ -536,11 +541,18 @@ int make_graph(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t
     AFPS_CUDA(ctx, cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
     const int64_t before = ctx->launches;
     int rc = AFPS_OK;
+    if (h_xyz && cudaMemcpyAsync(const_cast<float*>(d_xyz), h_xyz, xyz_bytes,
+                                 cudaMemcpyHostToDevice, ctx->capture) != cudaSuccess)
+        rc = AFPS_ERR_CUDA;
     for (size_t i = 0; i < plan.classes.size() && rc == AFPS_OK; ++i) {
         const ClassPlan& cp = plan.classes[i];
         rc = launch_class(ctx, cp.v, cp.npdu, d_items + cp.first, cp.count, counters + i, d_xyz,
-                          d_out, ctx->capture);
+                          d_out, ctx->capture, host_resident);
     }
+    if (rc == AFPS_OK && h_out &&
+        cudaMemcpyAsync(h_out, d_out, out_bytes, cudaMemcpyDeviceToHost, ctx->capture) !=
+            cudaSuccess)
+        rc = AFPS_ERR_CUDA;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->capture, &graph);
     g.kernels = ctx->launches - before;
@@ -599,6 +611,73 @@ int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int
 }
 
 // Tuning cache: one line per class, "key kind P W CS occ [skip]".
+bool is_pinned(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+// afps_sample_batched_host with pinned buffers and AFPS_FLAG_GRAPH: one graph
+// per argument set.  When both buffers are mapped into the device's address
+// space (page-locked host memory; on Grace-Blackwell the GPU reaches it over
+// the coherent C2C link) the kernels read the points and write the indices
+// in host memory directly, with plain loads and stores; otherwise the graph
+// holds the host->device copy, the sampling launches and the device->host
+// copy around its own device staging.  A call is one replay and a wait.
+int host_graph_call(afps_ctx* ctx, const float* h_xyz, const int64_t* pt_off, int32_t B,
+                    const int32_t* C, const int32_t* M, const int32_t* K, const int64_t* start,
+                    const int64_t* out_off, int32_t* h_out, size_t xyz_bytes, size_t out_bytes,
+                    cudaStream_t stream) {
+    std::string key = "H" + graph_key(h_xyz, h_out, pt_off, B, C, M, K, start, out_off);
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        BatchPlan plan;
+        int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan);
+        if (rc != AFPS_OK) return rc;
+        if (ctx->graphs.size() >= kMaxGraphs) {
+            auto victim = ctx->graphs.begin();
+            for (auto j = ctx->graphs.begin(); j != ctx->graphs.end(); ++j)
+                if (j->second.last_use < victim->second.last_use) victim = j;
+            cudaDeviceSynchronize();
+            drop_graph(victim->second);
+            ctx->graphs.erase(victim);
+        }
+        GraphEntry g;
+        void* dx = nullptr;
+        void* dout = nullptr;
+        const bool mapped =
+            cudaHostGetDevicePointer(&dx, const_cast<float*>(h_xyz), 0) == cudaSuccess &&
+            cudaHostGetDevicePointer(&dout, h_out, 0) == cudaSuccess && dx && dout &&
+            reinterpret_cast<uintptr_t>(dx) % 4 == 0 && reinterpret_cast<uintptr_t>(dout) % 4 == 0;
+        cudaGetLastError();
+        if (mapped) {
+            rc = make_graph(ctx, plan, static_cast<const float*>(dx), static_cast<int32_t*>(dout),
+                            g, nullptr, 0, nullptr, 0, true);
+        } else {
+            if (g.xyz.reserve(xyz_bytes) != cudaSuccess || g.out.reserve(out_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                drop_graph(g);
+                return fail(ctx, AFPS_ERR_NO_MEMORY, "afps_sample_batched_host: device staging");
+            }
+            rc = make_graph(ctx, plan, static_cast<const float*>(g.xyz.p),
+                            static_cast<int32_t*>(g.out.p), g, h_xyz, xyz_bytes, h_out, out_bytes);
+        }
+        if (rc != AFPS_OK) {
+            drop_graph(g);
+            return rc;
+        }
+        it = ctx->graphs.emplace(key, g).first;
+    }
+    it->second.last_use = ++ctx->tick;
+    AFPS_CUDA(ctx, cudaGraphLaunch(it->second.exec, stream));
+    ctx->launches += it->second.kernels;
+    AFPS_CUDA(ctx, cudaStreamSynchronize(stream));
+    return AFPS_OK;
+}
+
 int load_tuning(afps_ctx* ctx, const std::string& path) {
     std::ifstream f(path);
     if (!f) return 0;
@@ -791,6 +870,9 @@ int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t xyz_bytes = (size_t)h_pt_off[B] * 3 * sizeof(float);
     const size_t out_bytes = (size_t)h_out_off[B] * sizeof(int32_t);
+    if ((ctx->flags & AFPS_FLAG_GRAPH) && is_pinned(h_xyz) && is_pinned(h_out))
+        return host_graph_call(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
+                               h_out, xyz_bytes, out_bytes, st);
     AFPS_CUDA(ctx, ctx->xyz_stage.reserve(xyz_bytes));
     AFPS_CUDA(ctx, ctx->out_stage.reserve(out_bytes));
     AFPS_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_done, 0));

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
         const float* pts = reinterpret_cast<const float*>(buf);
         if (cn > 0)
             pts = dev::stage_points(a.xyz + 3 * (d.src + c0), cn, buf, bar, tid == 0, tid, T,
-                                    &bulk, a.stall_copy != 0);
+                                    &bulk, a.stall_copy != 0, a.host_resident != 0);
         if (bulk) {
             if (!dev::mbar_wait_bounded(bar, phase, a.timeout_ns)) {
                 dev::record_status(a.status, DEV_TIMEOUT_STAGE);
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
 
         int p = d.first;  // sector offset of the current sample
         const float* gq = a.xyz + 3 * (d.src + p);
-        float qx = __ldg(gq), qy = __ldg(gq + 1), qz = __ldg(gq + 2);
+        float qx = gq[0], qy = gq[1], qz = gq[2];
         int32_t* out = a.out + d.dst;
         const int c = d.c;
         const int kl = d.k >> 1;

@@ -207,19 +207,22 @@ __device__ __forceinline__ ItemDesc load_item(const LaunchArgs& a, int i) {
 // 16-byte aligned interior goes by one bulk copy issued by `issuer` and
 // completing on `bar`; the unaligned head and tail (at most 3 floats each)
 // are plain loads spread over threads tid = 0 .. nthr-1.  `stall` (fault
-// injection) arms the barrier without issuing the copy.  Returns the shared
+// injection) arms the barrier without issuing the copy.  `no_bulk` stages
+// everything with plain loads (points in host memory reached over the C2C
+// link, which the bulk-copy engine is not used for).  Returns the shared
 // address of point 0 and sets *bulk when a bulk copy was issued (the caller
 // then waits for the barrier's phase and synchronises its threads).
 __device__ __forceinline__ float* stage_points(const float* g, int n, unsigned char* buf,
                                                uint32_t bar, bool issuer, int tid, int nthr,
-                                               bool* bulk, bool stall = false) {
+                                               bool* bulk, bool stall = false,
+                                               bool no_bulk = false) {
     const uintptr_t A = reinterpret_cast<uintptr_t>(g);
     const uintptr_t E = A + 12ull * (uint64_t)n;
     const uintptr_t a0 = A & ~uintptr_t(15);
     const uintptr_t i0 = (A + 15) & ~uintptr_t(15);
     const uintptr_t i1 = E & ~uintptr_t(15);
     float* s = reinterpret_cast<float*>(buf + (A - a0));
-    const bool use_bulk = i1 > i0;
+    const bool use_bulk = i1 > i0 && !no_bulk;
     int nh, ts;
     if (use_bulk) {
         nh = (int)((i0 - A) >> 2);
@@ -234,8 +237,8 @@ __device__ __forceinline__ float* stage_points(const float* g, int n, unsigned c
         nh = 3 * n;
         ts = 3 * n;
     }
-    for (int f = tid; f < nh; f += nthr) s[f] = __ldg(g + f);
-    for (int f = ts + tid; f < 3 * n; f += nthr) s[f] = __ldg(g + f);
+    for (int f = tid; f < nh; f += nthr) s[f] = g[f];
+    for (int f = ts + tid; f < 3 * n; f += nthr) s[f] = g[f];
     *bulk = use_bulk;
     return s;
 }

@@ -55,6 +55,8 @@ struct LaunchArgs {
     uint64_t timeout_ns;
     uint32_t stall_copy;    // fault injection: arm the barrier, issue no copy
     uint32_t npdu_skip;     // Variant::skip
+    uint32_t host_resident; // points live in (mapped) host memory: plain loads only
+    uint32_t pad;
 };
 
 // Device error codes written to *status.

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         bool bulk;
         const float* pts =
             dev::stage_points(a.xyz + 3 * d.src, n, buf, bar, lane == 0, lane, 32, &bulk,
-                              a.stall_copy != 0);
+                              a.stall_copy != 0, a.host_resident != 0);
         if (bulk) {
             if (!dev::mbar_wait_bounded(bar, phase, a.timeout_ns)) {
                 dev::record_status(a.status, DEV_TIMEOUT_STAGE);

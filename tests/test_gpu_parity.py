@@ -247,6 +247,27 @@ def test_host_buffers_match_device(S, objects):
         assert_same(h_out[ba.out_off[b]:ba.out_off[b + 1]], oracle.afps(P, 512, 16, 16), f"cloud {b}")
 
 
+def test_host_buffers_graph_replay(objects):
+    """Pinned host buffers with graphs: copies and launches replay as one graph."""
+    build_mod.build()
+    s = B.Sampler(0, graph=True)
+    try:
+        xyz, off = synth.pack(objects[8:16])
+        ba = B.BatchArgs(off, 512, [32, 16, 4, 1, 32, 32, 8, 2], [16, 16, 8, 0, 0, 3, 0, 0], 0)
+        h_xyz = torch.from_numpy(xyz).pin_memory().numpy()
+        h_out = torch.full((ba.total_out,), -1, dtype=torch.int32).pin_memory().numpy()
+        n0 = s.launch_count
+        for rep in range(3):
+            h_out[:] = -1
+            s.sample_batched_host(h_xyz, ba, h_out)
+            for b, P in enumerate(objects[8:16]):
+                ref = oracle.afps(P, 512, int(ba.M[b]), int(ba.k[b]))
+                assert_same(h_out[ba.out_off[b]:ba.out_off[b + 1]], ref, f"rep {rep} cloud {b}")
+        assert s.launch_count > n0
+    finally:
+        s.close()
+
+
 def test_same_alone_and_in_a_mix(S, objects):
     """Each cloud's result is the same alone and inside a mixed batch."""
     clouds = objects[:6] + [synth.slab_cloud(4, 9000), synth.uniform_cloud(8, 300)]
