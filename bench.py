@@ -314,6 +314,37 @@ def ragged_batch(sampler, flush, dev, steps: int):
                         f"{sum(Ms)} sectors, C=N/4", **res}
 
 
+def sort_section(sampler, flush, dev, steps: int):
+    """Device sort by x of unsorted input: the object batch (32 x 2048) and a
+    32768-point slab cloud, each in random storage order."""
+    import torch
+    from paper_2208_08795_gb300 import synth
+    g = np.random.Generator(np.random.PCG64(11))
+    rows = {}
+    for name, clouds in (("object_batch_32x2048", synth.object_batch(1, 32, 2048)),
+                         ("slab_32768", [synth.slab_cloud(2, 32768)])):
+        clouds = [c[g.permutation(c.shape[0])] for c in clouds]
+        xyz, off = synth.pack(clouds)
+        x = torch.from_numpy(xyz).to(dev)
+        out = torch.empty_like(x)
+        perm = torch.empty(x.shape[0], dtype=torch.int32, device=dev)
+        stream = torch.cuda.current_stream()
+        for _ in range(3):
+            sampler.sort_by_key(x, off, 0, out, perm)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            sampler.sort_by_key(x, off, 0, out, perm)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        rows[name] = {"ms": round(ms, 4), "points_per_s": round(int(off[-1]) / (ms / 1e3), 1)}
+    return {"workload": "stable radix sort by x of shuffled clouds (one CTA per cloud)", **rows}
+
+
 # ------------------------------------------------------------------ serving
 SERVING_LEVELS = [16384, 4096, 1024, 256]
 SERVING_RATES = [500.0, 2000.0, 8000.0, 32000.0]
@@ -450,6 +481,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     extra_steps = max(5, min(args.steps, 20))
     large = large_clouds(sampler, flush, dev, extra_steps) if args.configs else None
     ragged = ragged_batch(sampler, flush, dev, extra_steps) if args.configs else None
+    sorting = sort_section(sampler, flush, dev, extra_steps) if args.configs else None
     clk = clocks.stop()
     e2e_ok = bool(np.array_equal(h_out, head_out))
 
@@ -495,6 +527,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         "serving": serving_stats,
         "large_clouds": large,
         "ragged_batch": ragged,
+        "sort_by_key": sorting,
         "gpu_launches": launches,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},

@@ -158,6 +158,31 @@ int afps_gather_levels(afps_ctx* ctx, int32_t B, const int64_t* h_in_pt_off,
                        void* stream);
 
 /*
+ * Sort keys for afps_sort_by_key.  AFPS_KEY_AZIMUTH is the "diamond angle"
+ * of (x, y): a monotone stand-in for atan2(y, x) on [0, 4) defined, per
+ * quadrant, as y/(x+y), 1 - x/(-x+y), 2 - y/(-x-y), 3 + x/(x-y) (each
+ * operation rounded on its own; the origin maps to 0), so that it can be
+ * reproduced exactly on any IEEE host.
+ */
+#define AFPS_KEY_X 0
+#define AFPS_KEY_Y 1
+#define AFPS_KEY_Z 2
+#define AFPS_KEY_AZIMUTH 3
+
+/*
+ * Stable ascending sort of each cloud's points by a key, for input without
+ * dimensional locality (Sec. III-A: AFPS and NPDU assume points stored next
+ * to each other are close; binning or sorting restores that).  Cloud b is
+ * points [h_pt_off[b], h_pt_off[b+1]) of d_xyz; its sorted points go to the
+ * same range of d_xyz_sorted (must not overlap d_xyz) and d_perm[i] is the
+ * cloud-relative index of the point now at position i.  Equal keys keep
+ * their storage order; -0 and +0 are equal.  The context keeps 16 bytes of
+ * device scratch per point.
+ */
+int afps_sort_by_key(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
+                     int32_t key, float* d_xyz_sorted, int32_t* d_perm, void* stream);
+
+/*
  * Wait for the stream and report device-side errors recorded since the last
  * call (AFPS_ERR_TIMEOUT when a bounded wait gave up); clears them.
  */

@@ -163,3 +163,50 @@ def chain(xyz, levels, M: int, k: int, start: int = 0, *, library=None):
         cloud = cloud[order]
         frame_idx = frame_idx[order]
     return out
+
+
+# --------------------------------------------------------------------------
+# sorting by key (for unsorted input; binning or sorting restores the
+# dimensional locality of Sec. III-A)
+# --------------------------------------------------------------------------
+KEY_X, KEY_Y, KEY_Z, KEY_AZIMUTH = 0, 1, 2, 3
+
+
+def diamond_angle(x, y):
+    """A monotone stand-in for atan2(y, x) mapped to [0, 4): each quadrant's
+    angle is replaced by a ratio of coordinates (every operation rounded on
+    its own in fp32); the origin maps to 0."""
+    x = np.asarray(x, dtype=np.float32)
+    y = np.asarray(y, dtype=np.float32)
+    one, two, three = np.float32(1), np.float32(2), np.float32(3)
+    out = np.zeros(x.shape, dtype=np.float32)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        q0 = (y >= 0) & (x >= 0)
+        q1 = (y >= 0) & (x < 0)
+        q2 = (y < 0) & (x < 0)
+        q3 = (y < 0) & (x >= 0)
+        out[q0] = y[q0] / (x[q0] + y[q0])
+        out[q1] = one - x[q1] / (-x[q1] + y[q1])
+        out[q2] = two - y[q2] / (-x[q2] - y[q2])
+        out[q3] = three + x[q3] / (x[q3] - y[q3])
+    out[(x == 0) & (y == 0)] = 0
+    return out
+
+
+def sort_key(xyz, key: int) -> np.ndarray:
+    pts = _points(xyz)
+    if key in (KEY_X, KEY_Y, KEY_Z):
+        k = pts[:, key].copy()
+    elif key == KEY_AZIMUTH:
+        k = diamond_angle(pts[:, 0], pts[:, 1])
+    else:
+        raise ValueError("unknown key")
+    return k + np.float32(0)  # -0 becomes +0
+
+
+def sort_by_key(xyz, key: int):
+    """Stable ascending sort of the points by key: (sorted points, permutation
+    such that sorted[i] = xyz[perm[i]])."""
+    pts = _points(xyz)
+    perm = np.argsort(sort_key(pts, key), kind="stable").astype(np.int32)
+    return pts[perm], perm

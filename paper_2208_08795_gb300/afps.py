@@ -38,7 +38,8 @@ EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
            "afps_last_error", "afps_autotune_batched", "afps_save_tuning",
            "afps_describe_plan", "afps_launch_count", "afps_sample_batched_noalloc",
            "afps_server_create", "afps_server_submit", "afps_server_step", "afps_server_poll",
-           "afps_server_stats", "afps_server_clock_ms", "afps_server_destroy")
+           "afps_server_stats", "afps_server_clock_ms", "afps_server_destroy",
+           "afps_sort_by_key")
 
 
 class AfpsLibraryError(RuntimeError):
@@ -53,6 +54,7 @@ class AfpsError(RuntimeError):
 
 
 AFPS_ERR_BUSY = -8
+AFPS_KEY_X, AFPS_KEY_Y, AFPS_KEY_Z, AFPS_KEY_AZIMUTH = 0, 1, 2, 3
 AFPS_SERVER_MAX_LEVELS = 8
 
 
@@ -105,6 +107,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.afps_launch_count.restype = ctypes.c_int64
     L.afps_sample_batched_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
     L.afps_sample_batched_noalloc.restype = ctypes.c_int
+    L.afps_sort_by_key.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
+    L.afps_sort_by_key.restype = ctypes.c_int
     L.afps_server_create.argtypes = [ctypes.POINTER(vp), vp, ctypes.POINTER(afps_server_config), vp]
     L.afps_server_create.restype = ctypes.c_int
     L.afps_server_submit.argtypes = [vp, vp, i64, ctypes.c_uint64]
@@ -206,6 +210,10 @@ def afps_describe_plan(ctx, n_sector: int, c_sector: int, npdu_window: int,
 
 def afps_launch_count(ctx) -> int:
     return load().afps_launch_count(ctx)
+
+
+def afps_sort_by_key(ctx, B, h_pt_off, d_xyz, key, d_xyz_sorted, d_perm, stream) -> int:
+    return load().afps_sort_by_key(ctx, B, h_pt_off, d_xyz, key, d_xyz_sorted, d_perm, stream)
 
 
 def afps_sample_batched_noalloc(d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
@@ -342,6 +350,20 @@ class Sampler:
             in_frame.data_ptr() if in_frame is not None else None, _ptr(so), sel.data_ptr(),
             out_xyz.data_ptr(), out_frame.data_ptr() if out_frame is not None else None,
             sel_frame.data_ptr() if sel_frame is not None else None, self._stream(stream)))
+
+    def sort_by_key(self, xyz, pt_off, key: int = AFPS_KEY_X, out=None, perm=None,
+                    stream=None):
+        """Stable sort of each cloud by key; returns (sorted points, permutation)."""
+        import torch
+        xyz = self._points(xyz)
+        po = _i64(pt_off)
+        if out is None:
+            out = torch.empty_like(xyz)
+        if perm is None:
+            perm = torch.empty(xyz.shape[0], dtype=torch.int32, device=xyz.device)
+        self._check(afps_sort_by_key(self.ctx, po.size - 1, _ptr(po), xyz.data_ptr(), key,
+                                     out.data_ptr(), perm.data_ptr(), self._stream(stream)))
+        return out, perm
 
     def sync(self, stream=None):
         self._check(afps_sync(self.ctx, self._stream(stream)))

@@ -105,7 +105,7 @@ struct afps_ctx {
     std::string last_error;
     cudaEvent_t ev_done = nullptr;    // last device work that used the shared workspace
     cudaStream_t capture = nullptr;   // private stream for graph capture
-    DevBuf items, counters, xyz_stage, out_stage;
+    DevBuf items, counters, xyz_stage, out_stage, sort_scratch;
     HostBuf stage[kStageSlots];         // pinned upload ring
     cudaEvent_t stage_ev[kStageSlots] = {};  // last copy out of each slot
     int stage_next = 0;
@@ -798,6 +798,7 @@ void afps_destroy(afps_ctx* ctx) {
         ctx->counters.release();
         ctx->xyz_stage.release();
         ctx->out_stage.release();
+        ctx->sort_scratch.release();
         for (int i = 0; i < kStageSlots; ++i) {
             ctx->stage[i].release();
             if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
@@ -915,6 +916,43 @@ int afps_gather_levels(afps_ctx* ctx, int32_t B, const int64_t* h_in_pt_off,
     DeviceGuard guard(ctx->device);
     return afps::gather_run(ctx, descs.data(), B, d_in_xyz, d_in_frame, d_sel, d_out_xyz,
                             d_out_frame, d_sel_frame, static_cast<cudaStream_t>(stream));
+}
+
+int afps_sort_by_key(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
+                     int32_t key, float* d_xyz_sorted, int32_t* d_perm, void* stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    if (B < 1 || !h_pt_off || !d_xyz || !d_xyz_sorted || !d_perm || key < AFPS_KEY_X ||
+        key > AFPS_KEY_AZIMUTH || h_pt_off[0] < 0)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sort_by_key: bad argument");
+    std::vector<afps::SortDesc> descs((size_t)B);
+    for (int32_t b = 0; b < B; ++b) {
+        const int64_t n = h_pt_off[b + 1] - h_pt_off[b];
+        if (n < 0 || n > INT32_MAX) {
+            std::ostringstream os;
+            os << "afps_sort_by_key: cloud " << b << " has " << n << " points";
+            return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
+        }
+        descs[b] = afps::SortDesc{h_pt_off[b], (int32_t)n, 0};
+    }
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t total = h_pt_off[B];
+    // scratch: keys and indices, twice (ping-pong); earlier users are ordered
+    // before the reallocation by cudaFree's device synchronisation
+    AFPS_CUDA(ctx, ctx->sort_scratch.reserve((size_t)total * 16 + 16));
+    int rc = upload(ctx, ctx->items, descs.data(), descs.size() * sizeof(afps::SortDesc), st);
+    if (rc != AFPS_OK) return rc;
+    unsigned char* base = static_cast<unsigned char*>(ctx->sort_scratch.p);
+    uint32_t* keys_a = reinterpret_cast<uint32_t*>(base);
+    int32_t* idx_a = reinterpret_cast<int32_t*>(base + 4 * total);
+    uint32_t* keys_b = reinterpret_cast<uint32_t*>(base + 8 * total);
+    int32_t* idx_b = reinterpret_cast<int32_t*>(base + 12 * total);
+    cudaError_t e = afps::launch_sort(static_cast<const afps::SortDesc*>(ctx->items.p), B, d_xyz,
+                                      key, keys_a, idx_a, keys_b, idx_b, d_xyz_sorted, d_perm, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sort launch");
+    ctx->launches += 1;
+    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, st));
+    return AFPS_OK;
 }
 
 int afps_sync(afps_ctx* ctx, void* stream) {

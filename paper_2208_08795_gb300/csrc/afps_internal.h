@@ -106,6 +106,16 @@ cudaError_t launch_gather(const GatherDesc* d_descs, int32_t B, int32_t max_n,
                           cudaStream_t stream);
 constexpr int32_t kGatherMaxPoints = 65536;
 
+// Sort by key (afps_sort_by_key): one cloud per CTA.
+struct SortDesc {
+    int64_t off;  // first point of the cloud
+    int32_t n;    // points
+    int32_t pad;
+};
+cudaError_t launch_sort(const SortDesc* d_descs, int32_t B, const float* xyz, int key,
+                        uint32_t* keys_a, int32_t* idx_a, uint32_t* keys_b, int32_t* idx_b,
+                        float* xyz_out, int32_t* perm, cudaStream_t stream);
+
 }  // namespace afps
 
 // ---- runtime functions over scattered clouds (afps_api.cu), for the server
