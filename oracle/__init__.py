@@ -47,6 +47,10 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.argtypes = [vp, i64, i32, i32, i32, i64, vp]
         fn.restype = ctypes.c_int
+    for name in ("oracle_afps_ex_f32", "oracle_afps_ex_f64"):
+        fn = getattr(lib, name)
+        fn.argtypes = [vp, i64, i32, i32, i32, i64, ctypes.c_uint32, vp]
+        fn.restype = ctypes.c_int
     lib.oracle_sector_table.argtypes = [i64, i32, i32, i64, vp, vp, vp]
     lib.oracle_sector_table.restype = ctypes.c_int
     lib.oracle_coverage_radius.argtypes = [vp, i64, vp, i32]
@@ -85,20 +89,31 @@ def _points(xyz) -> np.ndarray:
     return a
 
 
+NPDU_FULL_FIRST_PASS = 1
+NPDU_WINDOW_HAS_SAMPLE = 2
+
+
 def afps(xyz, C: int, M: int = 1, k: int = 0, start: int = 0, *,
-         precision: str = "f32", library: ctypes.CDLL | None = None) -> np.ndarray:
+         precision: str = "f32", method: int = 0,
+         library: ctypes.CDLL | None = None) -> np.ndarray:
     """NPDU-AFPS of one cloud: C int32 global indices, sector-major.
 
     M = 1 and k = 0 is plain FPS (Algorithm 1); k = 0 is AFPS (Sec. III-B);
     k > 0 adds the NPDU window of Sec. III-C.  ``precision`` is "f32" (the
-    bit-exact reference for the GPU) or "f64".
+    bit-exact reference for the GPU) or "f64".  ``method`` selects other
+    readings of the NPDU window (NPDU_FULL_FIRST_PASS, NPDU_WINDOW_HAS_SAMPLE).
     """
     L = library or lib()
     pts = _points(xyz)
     out = np.full(max(int(C), 0), -1, dtype=np.int32)
-    fn = L.oracle_afps_f32 if precision == "f32" else L.oracle_afps_f64
-    rc = fn(pts.ctypes.data, pts.shape[0], int(C), int(M), int(k), int(start),
-            out.ctypes.data if out.size else None)
+    if method:
+        fn = L.oracle_afps_ex_f32 if precision == "f32" else L.oracle_afps_ex_f64
+        rc = fn(pts.ctypes.data, pts.shape[0], int(C), int(M), int(k), int(start), int(method),
+                out.ctypes.data if out.size else None)
+    else:
+        fn = L.oracle_afps_f32 if precision == "f32" else L.oracle_afps_f64
+        rc = fn(pts.ctypes.data, pts.shape[0], int(C), int(M), int(k), int(start),
+                out.ctypes.data if out.size else None)
     if rc != OK:
         raise OracleError(rc)
     return out

@@ -33,6 +33,12 @@
  *      the sector (k neighbours plus the sample itself); k = 0 means "no NPDU";
  *   R4 ties in the argmax go to the lowest index;
  *   R5 no first full pass under NPDU: points never inside a window keep 1e10.
+ * Two other readings of Sec. III-C are available as method options:
+ *   ORACLE_NPDU_FULL_FIRST_PASS   the first update (after the first sample)
+ *                                 reaches the whole sector, later ones the
+ *                                 window only;
+ *   ORACLE_NPDU_WINDOW_HAS_SAMPLE k counts the sample itself: the window is
+ *                                 [p - floor((k-1)/2), p + (k-1) - floor((k-1)/2)].
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -42,6 +48,9 @@
 #define ORACLE_ERR_INVALID_ARG (-1)
 #define ORACLE_ERR_SECTOR_TOO_SMALL (-2)
 #define ORACLE_ERR_NO_MEMORY (-3)
+
+#define ORACLE_NPDU_FULL_FIRST_PASS 1u
+#define ORACLE_NPDU_WINDOW_HAS_SAMPLE 2u
 
 /* Algorithm 1, initial value of the Distance array. */
 #define ORACLE_DIST_INIT_F32 1e10f
@@ -120,7 +129,8 @@ int oracle_sector_table(int64_t N, int32_t C, int32_t M, int64_t start_idx,
  * D is scratch of n floats.  Writes c global indices (lo + local) to out.
  */
 static void oracle_sector_fps_f32(const float* P, int64_t lo, int64_t n, int64_t c,
-                                  int64_t first, int32_t k, float* D, int32_t* out)
+                                  int64_t first, int32_t k, int64_t kl, int64_t kr,
+                                  int full_first, float* D, int32_t* out)
 {
     for (int64_t j = 0; j < n; ++j) D[j] = ORACLE_DIST_INIT_F32;
     int64_t p = first;
@@ -129,9 +139,9 @@ static void oracle_sector_fps_f32(const float* P, int64_t lo, int64_t n, int64_t
         if (t == c - 1) break;
         /* points whose distance is updated this iteration */
         int64_t a = 0, b = n - 1;
-        if (k > 0) {
-            a = p - (k / 2);
-            b = p + (k - k / 2);
+        if (k > 0 && !(full_first && t == 0)) {
+            a = p - kl;
+            b = p + kr;
             if (a < 0) a = 0;
             if (b > n - 1) b = n - 1;
         }
@@ -155,7 +165,8 @@ static void oracle_sector_fps_f32(const float* P, int64_t lo, int64_t n, int64_t
 
 /* The same loop in fp64, on inputs widened from fp32. */
 static void oracle_sector_fps_f64(const float* P, int64_t lo, int64_t n, int64_t c,
-                                  int64_t first, int32_t k, double* D, int32_t* out)
+                                  int64_t first, int32_t k, int64_t kl, int64_t kr,
+                                  int full_first, double* D, int32_t* out)
 {
     for (int64_t j = 0; j < n; ++j) D[j] = ORACLE_DIST_INIT_F64;
     int64_t p = first;
@@ -163,9 +174,9 @@ static void oracle_sector_fps_f64(const float* P, int64_t lo, int64_t n, int64_t
         out[t] = (int32_t)(lo + p);
         if (t == c - 1) break;
         int64_t a = 0, b = n - 1;
-        if (k > 0) {
-            a = p - (k / 2);
-            b = p + (k - k / 2);
+        if (k > 0 && !(full_first && t == 0)) {
+            a = p - kl;
+            b = p + kr;
             if (a < 0) a = 0;
             if (b > n - 1) b = n - 1;
         }
@@ -186,51 +197,79 @@ static void oracle_sector_fps_f64(const float* P, int64_t lo, int64_t n, int64_t
     }
 }
 
+/* Window sides of the NPDU reading selected by `method`. */
+static void oracle_window(int32_t k, uint32_t method, int64_t* kl, int64_t* kr)
+{
+    if (method & ORACLE_NPDU_WINDOW_HAS_SAMPLE) {
+        *kl = (k - 1) / 2;
+        *kr = (k - 1) - (k - 1) / 2;
+    } else {
+        *kl = k / 2;
+        *kr = k - k / 2;
+    }
+}
+
 /*
  * NPDU-AFPS on one cloud in fp32.  xyz: N points, xyz interleaved (host).
  * C samples, M sectors, k = NPDU window (0 = off), start_idx in [0, N).
  * out: C int32 global indices, sector-major.  Nothing is written on error.
  * M = 1, k = 0 is plain FPS (Algorithm 1 with a fixed start).
  */
-int oracle_afps_f32(const float* xyz, int64_t N, int32_t C, int32_t M, int32_t k,
-                    int64_t start_idx, int32_t* out)
+int oracle_afps_ex_f32(const float* xyz, int64_t N, int32_t C, int32_t M, int32_t k,
+                       int64_t start_idx, uint32_t method, int32_t* out)
 {
     int rc = oracle_check(N, C, M, k, start_idx);
     if (rc != ORACLE_OK) return rc;
-    if (!xyz || !out) return ORACLE_ERR_INVALID_ARG;
-    int64_t r;
+    if (!xyz || !out || method > 3u) return ORACLE_ERR_INVALID_ARG;
+    int64_t r, kl, kr;
     oracle_start_offset(N, C, M, start_idx, &r);
+    oracle_window(k, method, &kl, &kr);
     float* D = (float*)malloc(sizeof(float) * (size_t)N);
     if (!D) return ORACLE_ERR_NO_MEMORY;
     for (int64_t s = 0; s < M; ++s) {
         int64_t lo, n, off, c;
         oracle_sector(N, C, M, s, &lo, &n, &off, &c);
         int64_t first = r < n - 1 ? r : n - 1;
-        oracle_sector_fps_f32(xyz + 3 * lo, lo, n, c, first, k, D, out + off);
+        oracle_sector_fps_f32(xyz + 3 * lo, lo, n, c, first, k, kl, kr,
+                              (method & ORACLE_NPDU_FULL_FIRST_PASS) != 0, D, out + off);
     }
     free(D);
     return ORACLE_OK;
 }
 
-/* The same method in fp64 (for agreement rates and coverage radii). */
-int oracle_afps_f64(const float* xyz, int64_t N, int32_t C, int32_t M, int32_t k,
+int oracle_afps_f32(const float* xyz, int64_t N, int32_t C, int32_t M, int32_t k,
                     int64_t start_idx, int32_t* out)
+{
+    return oracle_afps_ex_f32(xyz, N, C, M, k, start_idx, 0u, out);
+}
+
+/* The same method in fp64 (for agreement rates and coverage radii). */
+int oracle_afps_ex_f64(const float* xyz, int64_t N, int32_t C, int32_t M, int32_t k,
+                       int64_t start_idx, uint32_t method, int32_t* out)
 {
     int rc = oracle_check(N, C, M, k, start_idx);
     if (rc != ORACLE_OK) return rc;
-    if (!xyz || !out) return ORACLE_ERR_INVALID_ARG;
-    int64_t r;
+    if (!xyz || !out || method > 3u) return ORACLE_ERR_INVALID_ARG;
+    int64_t r, kl, kr;
     oracle_start_offset(N, C, M, start_idx, &r);
+    oracle_window(k, method, &kl, &kr);
     double* D = (double*)malloc(sizeof(double) * (size_t)N);
     if (!D) return ORACLE_ERR_NO_MEMORY;
     for (int64_t s = 0; s < M; ++s) {
         int64_t lo, n, off, c;
         oracle_sector(N, C, M, s, &lo, &n, &off, &c);
         int64_t first = r < n - 1 ? r : n - 1;
-        oracle_sector_fps_f64(xyz + 3 * lo, lo, n, c, first, k, D, out + off);
+        oracle_sector_fps_f64(xyz + 3 * lo, lo, n, c, first, k, kl, kr,
+                              (method & ORACLE_NPDU_FULL_FIRST_PASS) != 0, D, out + off);
     }
     free(D);
     return ORACLE_OK;
+}
+
+int oracle_afps_f64(const float* xyz, int64_t N, int32_t C, int32_t M, int32_t k,
+                    int64_t start_idx, int32_t* out)
+{
+    return oracle_afps_ex_f64(xyz, N, C, M, k, start_idx, 0u, out);
 }
 
 /*

@@ -38,12 +38,15 @@ def sqdist32(P, j, q):
     return (dx * dx + dy * dy) + dz * dz
 
 
-def brute_force(P, C, M, k, start):
+def brute_force(P, C, M, k, start, method=0):
     """From-scratch restatement: at every step, each point's distance is the
     minimum over the 1e10 of Algorithm 1 and its distances to the earlier
     samples of its sector whose update reached it (the whole sector without
-    NPDU, the window [p - k//2, p + k - k//2] with it).  No running array is
-    kept; the next sample is the lowest-index maximum."""
+    NPDU, the window [p - k//2, p + k - k//2] with it; with method bit 2 the
+    window counts the sample, [p - (k-1)//2, p + (k-1) - (k-1)//2]; with
+    method bit 1 the first sample's update reaches the whole sector).  No
+    running array is kept; the next sample is the lowest-index maximum."""
+    kl, kr = (k // 2, k - k // 2) if not method & 2 else ((k - 1) // 2, (k - 1) - (k - 1) // 2)
     P = np.asarray(P, dtype=np.float32)
     N = P.shape[0]
     lo, off = sectors(N, C, M)
@@ -56,10 +59,10 @@ def brute_force(P, C, M, k, start):
         sel = [min(r, n - 1)]
         while len(sel) < c:
             D = np.full(n, INIT, dtype=np.float32)
-            for p in sel:
+            for t, p in enumerate(sel):
                 js = np.arange(n)
-                if k > 0:
-                    js = js[(js >= p - k // 2) & (js <= p + (k - k // 2))]
+                if k > 0 and not (method & 1 and t == 0):
+                    js = js[(js >= p - kl) & (js <= p + kr)]
                 D[js] = np.minimum(D[js], sqdist32(Q, js, p))
             sel.append(int(np.argmax(D)))  # first maximum = lowest index
         out += [lo[s] + p for p in sel]
@@ -92,6 +95,7 @@ def read_golden(name):
     else:
         P = np.array([float(v) for v in fields["points"]], dtype=np.float32).reshape(N, 3)
     args = {key: int(fields[key][0]) for key in ("C", "M", "k", "start")}
+    args["method"] = int(fields.get("method", ["0"])[0])
     expect = np.array([int(v) for v in fields["expect"]], dtype=np.int32)
     return P, args, expect
 
@@ -107,7 +111,8 @@ def pin_golden(L):
     for name in GOLDEN_FILES:
         P, a, expect = read_golden(name)
         for prec in ("f32", "f64"):
-            got = oracle.afps(P, a["C"], a["M"], a["k"], a["start"], precision=prec, library=L)
+            got = oracle.afps(P, a["C"], a["M"], a["k"], a["start"], precision=prec,
+                              method=a["method"], library=L)
             assert np.array_equal(got, expect), (name, prec, got, expect)
 
 
@@ -289,6 +294,28 @@ def pin_coverage_radius(L):
     assert abs(got - ref) <= 1e-12 * ref, (got, ref)
 
 
+def pin_npdu_readings(L):
+    """The other NPDU readings: a window that counts the sample with k + 1
+    equals the default window with k; a full first pass with a window of 2n
+    equals AFPS; both agree with the brute force restatement."""
+    P = synth.uniform_cloud(31, 200)
+    for k in (1, 2, 3, 8, 9, 16):
+        for M in (1, 4):
+            a = oracle.afps(P, 80, M, k, 0, library=L)
+            b = oracle.afps(P, 80, M, k + 1, 0, method=oracle.NPDU_WINDOW_HAS_SAMPLE, library=L)
+            assert np.array_equal(a, b), (k, M)
+    full = oracle.afps(P, 80, 4, 0, 0, library=L)
+    assert np.array_equal(oracle.afps(P, 80, 4, 400, 0, method=1, library=L), full)
+    cases = [(40, 20, 1, 2, 0), (48, 24, 3, 4, 7), (64, 32, 2, 5, 3), (33, 11, 5, 1, 12)]
+    for i, (N, C, M, k, start) in enumerate(cases):
+        Q = synth.uniform_cloud(500 + i, N)
+        for method in (1, 2, 3):
+            got = oracle.afps(Q, C, M, k, start, method=method, library=L)
+            assert np.array_equal(got, brute_force(Q, C, M, k, start, method)), (i, method)
+            got64 = oracle.afps(Q, C, M, k, start, method=method, precision="f64", library=L)
+            assert np.mean(got64 == got) > 0.5
+
+
 def pin_chain_grid(L):
     """Chained levels on the grid 0..64: FPS with 2^l + 1 samples takes the
     multiples of 2^(6-l); sorted ascending they form the next, coarser grid,
@@ -304,4 +331,4 @@ def pin_chain_grid(L):
 
 PINS = [pin_golden, pin_grid_closed_form, pin_npdu_stride_law, pin_brute_force,
         pin_brute_force_f64, pin_reductions, pin_invariants, pin_every_point, pin_metamorphic,
-        pin_errors, pin_coverage_radius, pin_chain_grid]
+        pin_errors, pin_coverage_radius, pin_chain_grid, pin_npdu_readings]

@@ -20,14 +20,17 @@ MUTANTS = [
     ("f32_tie_highest", "if (D[j] > D[best]) best = j;", "if (D[j] >= D[best]) best = j;", 0),
     ("f32_argmin", "if (D[j] > D[best]) best = j;", "if (D[j] < D[best]) best = j;", 0),
     ("f32_scan_from_1", "int64_t best = 0;", "int64_t best = 1;", 0),
-    ("f32_window_right", "b = p + (k - k / 2);", "b = p + (k / 2);", 0),
-    ("f32_window_left", "a = p - (k / 2);", "a = p - (k - k / 2);", 0),
+    ("window_right", "*kr = k - k / 2;", "*kr = k / 2;", 0),
+    ("window_left", "*kl = k / 2;", "*kl = k - k / 2;", 0),
+    ("window_has_sample", "*kr = (k - 1) - (k - 1) / 2;", "*kr = k - (k - 1) / 2;", 0),
+    ("full_first_ignored", "if (k > 0 && !(full_first && t == 0)) {", "if (k > 0) {", 0),
+    ("full_first_every_time", "if (k > 0 && !(full_first && t == 0)) {", "if (k > 0 && !full_first) {", 0),
     ("f32_window_shift", "if (a < 0) a = 0;", "if (a < 0) { b = b - a; a = 0; }", 0),
     ("f32_init", "#define ORACLE_DIST_INIT_F32 1e10f", "#define ORACLE_DIST_INIT_F32 0.5f", 0),
     ("f32_local_index", "out[t] = (int32_t)(lo + p);", "out[t] = (int32_t)(p);", 0),
     ("f64_drop_dy", "double dist = (dx * dx + dy * dy) + dz * dz;", "double dist = (dx * dx) + dz * dz;", 0),
     ("f64_tie_highest", "if (D[j] > D[best]) best = j;", "if (D[j] >= D[best]) best = j;", 1),
-    ("f64_window_right", "b = p + (k - k / 2);", "b = p + (k / 2);", 1),
+    ("f64_update_max", "if (dist <= D[j]) D[j] = dist;", "if (dist >= D[j]) D[j] = dist;", 1),
     ("sector_ceil", "int64_t lo1 = ((s + 1) * N) / M;", "int64_t lo1 = ((s + 1) * N + M - 1) / M;", 0),
     ("samples_ceil", "int64_t off1 = ((s + 1) * C) / M;", "int64_t off1 = ((s + 1) * C + M - 1) / M;", 0),
     ("start_ignored", "int64_t first = r < n - 1 ? r : n - 1;\n        oracle_sector_fps_f32",
