@@ -108,6 +108,27 @@ int afps_sample(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int32_t
                 int32_t npdu_window, int64_t start_idx, int32_t* d_out, void* stream);
 
 /*
+ * Readings of the NPDU window (Sec. III-C says only that the k points stored
+ * next to each new sample are updated), for the _ex calls.  Method 0 is the
+ * default reading above.  Bits:
+ *   AFPS_METHOD_FULL_FIRST_PASS   the update after a sector's first sample
+ *                                 reaches the whole sector; later updates the
+ *                                 window only (no stride phase of untouched
+ *                                 points);
+ *   AFPS_METHOD_WINDOW_HAS_SAMPLE k counts the sample itself: the window is
+ *                                 [p - floor((k-1)/2), p + (k-1) - floor((k-1)/2)].
+ * Both apply only with k > 0.
+ */
+#define AFPS_METHOD_FULL_FIRST_PASS 1u
+#define AFPS_METHOD_WINDOW_HAS_SAMPLE 2u
+#define AFPS_METHOD_ALL 3u
+
+/* afps_sample with an NPDU reading (AFPS_METHOD_* bits; 0 = afps_sample). */
+int afps_sample_ex(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int32_t M,
+                   int32_t npdu_window, int64_t start_idx, uint32_t method, int32_t* d_out,
+                   void* stream);
+
+/*
  * A ragged batch of B clouds in one call: cloud b is points
  * [h_pt_off[b], h_pt_off[b+1]) of d_xyz and writes h_C[b] indices at
  * d_out[h_out_off[b]], relative to its own first point.  Each cloud has its
@@ -121,6 +142,14 @@ int afps_sample_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_o
                         int32_t B, const int32_t* h_C, const int32_t* h_M,
                         const int32_t* h_win, const int64_t* h_start,
                         const int64_t* h_out_off, int32_t* d_out, void* stream);
+
+/* afps_sample_batched with a per-cloud NPDU reading (h_method: B entries of
+ * AFPS_METHOD_* bits). */
+int afps_sample_batched_ex(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_off,
+                           int32_t B, const int32_t* h_C, const int32_t* h_M,
+                           const int32_t* h_win, const int64_t* h_start,
+                           const uint32_t* h_method, const int64_t* h_out_off, int32_t* d_out,
+                           void* stream);
 
 /*
  * afps_sample_batched on HOST buffers (h_pt_off[0] = h_out_off[0] = 0):

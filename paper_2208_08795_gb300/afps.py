@@ -39,7 +39,7 @@ EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
            "afps_describe_plan", "afps_launch_count", "afps_sample_batched_noalloc",
            "afps_server_create", "afps_server_submit", "afps_server_step", "afps_server_poll",
            "afps_server_stats", "afps_server_clock_ms", "afps_server_destroy",
-           "afps_sort_by_key")
+           "afps_sort_by_key", "afps_sample_ex", "afps_sample_batched_ex")
 
 
 class AfpsLibraryError(RuntimeError):
@@ -55,6 +55,8 @@ class AfpsError(RuntimeError):
 
 AFPS_ERR_BUSY = -8
 AFPS_KEY_X, AFPS_KEY_Y, AFPS_KEY_Z, AFPS_KEY_AZIMUTH = 0, 1, 2, 3
+AFPS_METHOD_FULL_FIRST_PASS = 1
+AFPS_METHOD_WINDOW_HAS_SAMPLE = 2
 AFPS_SERVER_MAX_LEVELS = 8
 
 
@@ -107,6 +109,10 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.afps_launch_count.restype = ctypes.c_int64
     L.afps_sample_batched_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
     L.afps_sample_batched_noalloc.restype = ctypes.c_int
+    L.afps_sample_ex.argtypes = [vp, vp, i64, i32, i32, i32, i64, ctypes.c_uint32, vp, vp]
+    L.afps_sample_ex.restype = ctypes.c_int
+    L.afps_sample_batched_ex.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.afps_sample_batched_ex.restype = ctypes.c_int
     L.afps_sort_by_key.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
     L.afps_sort_by_key.restype = ctypes.c_int
     L.afps_server_create.argtypes = [ctypes.POINTER(vp), vp, ctypes.POINTER(afps_server_config), vp]
@@ -161,6 +167,17 @@ def afps_destroy(ctx: int) -> None:
 
 def afps_sample(ctx, d_xyz, N, C, M, npdu_window, start_idx, d_out, stream) -> int:
     return load().afps_sample(ctx, d_xyz, N, C, M, npdu_window, start_idx, d_out, stream)
+
+
+def afps_sample_ex(ctx, d_xyz, N, C, M, npdu_window, start_idx, method, d_out, stream) -> int:
+    return load().afps_sample_ex(ctx, d_xyz, N, C, M, npdu_window, start_idx, method, d_out,
+                                 stream)
+
+
+def afps_sample_batched_ex(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_method,
+                           h_out_off, d_out, stream) -> int:
+    return load().afps_sample_batched_ex(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start,
+                                         h_method, h_out_off, d_out, stream)
 
 
 def afps_sample_batched(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
@@ -239,10 +256,12 @@ def _ptr(a: np.ndarray) -> int:
 class BatchArgs:
     """Host arrays of a batched call, kept alive for the call's duration."""
 
-    def __init__(self, pt_off, C, M, k, start, out_off=None):
+    def __init__(self, pt_off, C, M, k, start, out_off=None, method=None):
         self.pt_off = _i64(pt_off)
         B = self.pt_off.size - 1
         self.B = B
+        self.method = (None if method is None else
+                       np.ascontiguousarray(np.broadcast_to(method, (B,)), dtype=np.uint32))
         self.C = _i32(np.broadcast_to(C, (B,)))
         self.M = _i32(np.broadcast_to(M, (B,)))
         self.k = _i32(np.broadcast_to(k, (B,)))
@@ -300,14 +319,20 @@ class Sampler:
         return xyz
 
     def sample(self, xyz, C: int, M: int = 1, k: int = 0, start: int = 0, out=None,
-               stream=None):
-        """NPDU-AFPS of one cloud; returns C int32 indices (sector-major)."""
+               stream=None, method: int = 0):
+        """NPDU-AFPS of one cloud; returns C int32 indices (sector-major).
+        ``method``: AFPS_METHOD_* reading of the NPDU window (0 = default)."""
         import torch
         xyz = self._points(xyz)
         if out is None:
             out = torch.empty(C, dtype=torch.int32, device=xyz.device)
-        self._check(afps_sample(self.ctx, xyz.data_ptr(), xyz.shape[0], C, M, k, start,
-                                out.data_ptr(), self._stream(stream)))
+        if method:
+            rc = afps_sample_ex(self.ctx, xyz.data_ptr(), xyz.shape[0], C, M, k, start, method,
+                                out.data_ptr(), self._stream(stream))
+        else:
+            rc = afps_sample(self.ctx, xyz.data_ptr(), xyz.shape[0], C, M, k, start,
+                             out.data_ptr(), self._stream(stream))
+        self._check(rc)
         return out
 
     def sample_batched(self, xyz, pt_off, C=None, M=None, k=None, start=0, out_off=None,
@@ -319,8 +344,14 @@ class Sampler:
         ba = pt_off if isinstance(pt_off, BatchArgs) else BatchArgs(pt_off, C, M, k, start, out_off)
         if out is None:
             out = torch.empty(ba.total_out, dtype=torch.int32, device=xyz.device)
-        self._check(afps_sample_batched(self.ctx, xyz.data_ptr(), *ba.args(), out.data_ptr(),
-                                        self._stream(stream)))
+        if ba.method is not None:
+            pt, B, c, m, k, st, oo = ba.args()
+            rc = afps_sample_batched_ex(self.ctx, xyz.data_ptr(), pt, B, c, m, k, st,
+                                        _ptr(ba.method), oo, out.data_ptr(), self._stream(stream))
+        else:
+            rc = afps_sample_batched(self.ctx, xyz.data_ptr(), *ba.args(), out.data_ptr(),
+                                     self._stream(stream))
+        self._check(rc)
         return out
 
     def sample_batched_host(self, h_xyz: np.ndarray, ba: "BatchArgs", h_out: np.ndarray,

@@ -158,6 +158,19 @@ inline int32_t device_window(int32_t k) {
     return (int32_t)std::min<int64_t>(k, 4LL * AFPS_MAX_SECTOR_POINTS);
 }
 
+// Window extents and item flags of the NPDU reading `method` (afps.h).
+void window_sides(int32_t k, uint32_t method, ItemDesc& d) {
+    const int32_t kk = device_window(k);
+    if (kk > 0 && (method & AFPS_METHOD_WINDOW_HAS_SAMPLE)) {
+        d.kl = (kk - 1) / 2;
+        d.kr = (kk - 1) - (kk - 1) / 2;
+    } else {
+        d.kl = kk / 2;
+        d.kr = kk - kk / 2;
+    }
+    d.flags = (kk > 0 && (method & AFPS_METHOD_FULL_FIRST_PASS)) ? afps::ITEM_FULL_FIRST : 0;
+}
+
 struct CloudCheck {
     int code = AFPS_OK;
     std::string msg;
@@ -374,7 +387,8 @@ int64_t size_bucket(int64_t n_max) {
 // indices written from out_begin[b] of the output base (out_cap[b] slots).
 int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t* n_pts,
                const int64_t* out_begin, const int64_t* out_cap, const int32_t* C,
-               const int32_t* M, const int32_t* K, const int64_t* start, BatchPlan& plan) {
+               const int32_t* M, const int32_t* K, const int64_t* start, BatchPlan& plan,
+               const uint32_t* method = nullptr) {
     if (B < 1 || !pt_begin || !n_pts || !out_begin || !out_cap || !C || !M || !K || !start)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
     struct Member {
@@ -400,6 +414,11 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
             os << "cloud " << b << ": " << chk.msg;
             return fail(ctx, chk.code, os.str());
         }
+        if (method && method[b] > AFPS_METHOD_ALL) {
+            std::ostringstream os;
+            os << "cloud " << b << ": unknown method bits " << method[b];
+            return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
+        }
         groups[{K[b] > 0 ? 1 : 0, size_bucket(chk.n_max)}].push_back(Member{b, chk});
     }
     plan.items.clear();
@@ -423,14 +442,14 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
                 d.c = (int32_t)(o1 - o0);
                 d.first = std::min<int32_t>(m.chk.start_r, d.n - 1);
                 d.lo = (int32_t)lo;
-                d.k = device_window(K[b]);
+                window_sides(K[b], method ? method[b] : 0u, d);
                 plan.items.push_back(d);
             }
         }
         cp.count = plan.items.size() - cp.first;
         // largest work first (longest-processing-time order for the queue)
         auto cost = [&](const ItemDesc& d) {
-            return cp.npdu ? (int64_t)d.c * (d.k + 1 + d.n / 32) : (int64_t)d.c * d.n;
+            return cp.npdu ? (int64_t)d.c * (d.kl + d.kr + 1 + d.n / 32) : (int64_t)d.c * d.n;
         };
         std::stable_sort(plan.items.begin() + cp.first, plan.items.end(),
                          [&](const ItemDesc& x, const ItemDesc& y) { return cost(x) > cost(y); });
@@ -461,7 +480,8 @@ int upload(afps_ctx* ctx, DevBuf& dst, const void* src, size_t bytes, cudaStream
 // outputs [out_off[b], out_off[b+1]).
 int build_plan_consecutive(afps_ctx* ctx, const int64_t* pt_off, int32_t B, const int32_t* C,
                            const int32_t* M, const int32_t* K, const int64_t* start,
-                           const int64_t* out_off, BatchPlan& plan) {
+                           const int64_t* out_off, BatchPlan& plan,
+                           const uint32_t* method = nullptr) {
     if (B < 1 || !pt_off || !out_off)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
     std::vector<int64_t> pb((size_t)B), np((size_t)B), ob((size_t)B), oc((size_t)B);
@@ -471,7 +491,8 @@ int build_plan_consecutive(afps_ctx* ctx, const int64_t* pt_off, int32_t B, cons
         ob[b] = out_off[b];
         oc[b] = out_off[b + 1] - out_off[b];
     }
-    return build_plan(ctx, B, pb.data(), np.data(), ob.data(), oc.data(), C, M, K, start, plan);
+    return build_plan(ctx, B, pb.data(), np.data(), ob.data(), oc.data(), C, M, K, start, plan,
+                      method);
 }
 
 // Run a plan out of the context's shared workspace (no graph).
@@ -495,7 +516,8 @@ int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* 
 
 std::string graph_key(const float* d_xyz, int32_t* d_out, const int64_t* pt_off, int32_t B,
                       const int32_t* C, const int32_t* M, const int32_t* K,
-                      const int64_t* start, const int64_t* out_off) {
+                      const int64_t* start, const int64_t* out_off,
+                      const uint32_t* method = nullptr) {
     std::string k;
     k.reserve(64 + (size_t)B * 40);
     auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
@@ -508,6 +530,7 @@ std::string graph_key(const float* d_xyz, int32_t* d_out, const int64_t* pt_off,
     put(M, sizeof(int32_t) * B);
     put(K, sizeof(int32_t) * B);
     put(start, sizeof(int64_t) * B);
+    if (method) put(method, sizeof(uint32_t) * B);
     return k;
 }
 
@@ -570,23 +593,24 @@ int make_graph(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t
 
 int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int32_t B,
                    const int32_t* C, const int32_t* M, const int32_t* K, const int64_t* start,
-                   const int64_t* out_off, int32_t* d_out, cudaStream_t stream) {
+                   const int64_t* out_off, int32_t* d_out, cudaStream_t stream,
+                   const uint32_t* method = nullptr) {
     if (!d_xyz || !d_out) return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: NULL device pointer");
     if (reinterpret_cast<uintptr_t>(d_xyz) % 4 || reinterpret_cast<uintptr_t>(d_out) % 4)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: xyz and out must be 4-byte aligned");
     if (!(ctx->flags & AFPS_FLAG_GRAPH)) {
         BatchPlan plan;
-        int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan);
+        int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan, method);
         if (rc != AFPS_OK) return rc;
         return run_plan(ctx, plan, d_xyz, d_out, stream);
     }
     if (B < 1 || !pt_off || !C || !M || !K || !start || !out_off)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
-    const std::string key = graph_key(d_xyz, d_out, pt_off, B, C, M, K, start, out_off);
+    const std::string key = graph_key(d_xyz, d_out, pt_off, B, C, M, K, start, out_off, method);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
         BatchPlan plan;
-        int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan);
+        int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan, method);
         if (rc != AFPS_OK) return rc;
         if (ctx->graphs.size() >= kMaxGraphs) {  // evict the least recently used
             auto victim = ctx->graphs.begin();
@@ -813,7 +837,15 @@ void afps_destroy(afps_ctx* ctx) {
 
 int afps_sample(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int32_t M,
                 int32_t npdu_window, int64_t start_idx, int32_t* d_out, void* stream) {
+    return afps_sample_ex(ctx, d_xyz, N, C, M, npdu_window, start_idx, 0u, d_out, stream);
+}
+
+int afps_sample_ex(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int32_t M,
+                   int32_t npdu_window, int64_t start_idx, uint32_t method, int32_t* d_out,
+                   void* stream) {
     if (!ctx) return AFPS_ERR_INVALID_ARG;
+    if (method > AFPS_METHOD_ALL)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sample_ex: unknown method bits");
     if (!d_xyz || !d_out)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sample: NULL device pointer");
     if (reinterpret_cast<uintptr_t>(d_xyz) % 4 || reinterpret_cast<uintptr_t>(d_out) % 4)
@@ -831,7 +863,13 @@ int afps_sample(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int32_t
     a.single.N = (int32_t)N;
     a.single.C = C;
     a.single.M = M;
-    a.single.k = device_window(npdu_window);
+    {
+        ItemDesc w{};
+        window_sides(npdu_window, method, w);
+        a.single.kl = w.kl;
+        a.single.kr = w.kr;
+        a.single.flags = w.flags;
+    }
     a.single.start_r = chk.start_r;
     a.n_items = M;
     a.out = d_out;
@@ -855,6 +893,18 @@ int afps_sample_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_o
     DeviceGuard guard(ctx->device);
     return batched_device(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, d_out,
                           static_cast<cudaStream_t>(stream));
+}
+
+int afps_sample_batched_ex(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_off,
+                           int32_t B, const int32_t* h_C, const int32_t* h_M,
+                           const int32_t* h_win, const int64_t* h_start,
+                           const uint32_t* h_method, const int64_t* h_out_off, int32_t* d_out,
+                           void* stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    if (!h_method) return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sample_batched_ex: NULL h_method");
+    DeviceGuard guard(ctx->device);
+    return batched_device(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, d_out,
+                          static_cast<cudaStream_t>(stream), h_method);
 }
 
 int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off,

@@ -138,14 +138,16 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
         float qx = gq[0], qy = gq[1], qz = gq[2];
         int32_t* out = a.out + d.dst;
         const int c = d.c;
-        const int kl = d.k >> 1;
-        const int kr = d.k - kl;
+        const int kl = d.kl;
+        const int kr = d.kr;
+        const bool full_first = (d.flags & ITEM_FULL_FIRST) != 0;
         const bool emitter = (rank == 0) && (w == 0);
         int obuf = lane == 0 ? d.lo + p : 0;
 
         for (int t = 1; t < c; ++t) {
             // 1. update + local argmax (chunk-local offsets)
-            const int wlo = p - kl - c0, whi = p + kr - c0;
+            const bool whole = full_first && t == 1;  // full first pass reading
+            const int wlo = whole ? -c0 : p - kl - c0, whi = whole ? n - 1 - c0 : p + kr - c0;
             const unsigned long long qx2 = dev::pack2(qx, qx), qy2 = dev::pack2(qy, qy),
                                      qz2 = dev::pack2(qz, qz);
             float best = -1.f;

@@ -197,7 +197,9 @@ __device__ __forceinline__ ItemDesc load_item(const LaunchArgs& a, int i) {
     d.c = (int32_t)(o1 - o0);
     d.first = s.start_r < d.n - 1 ? s.start_r : d.n - 1;
     d.lo = (int32_t)lo;
-    d.k = s.k;
+    d.kl = s.kl;
+    d.kr = s.kr;
+    d.flags = s.flags;
     d.pad = 0;
     return d;
 }

@@ -16,17 +16,23 @@ struct ItemDesc {
     int32_t c;      // samples taken from the sector
     int32_t first;  // sector offset of the first sample
     int32_t lo;     // sector's first point relative to its cloud (added to outputs)
-    int32_t k;      // NPDU window (0 = off)
+    int32_t kl;     // NPDU window: points updated left of the sample
+    int32_t kr;     // ... and right of it (kl = kr = 0 and no NPDU: whole sector)
+    int32_t flags;  // ITEM_* bits
     int32_t pad;
 };
-static_assert(sizeof(ItemDesc) == 40, "ItemDesc layout");
+static_assert(sizeof(ItemDesc) == 48, "ItemDesc layout");
+
+// ItemDesc::flags
+enum : int32_t { ITEM_FULL_FIRST = 1 };  // the first update reaches the whole sector
 
 // A single cloud described by its parameters; items are its M sectors.
 struct SingleCloud {
     int64_t pt_off;
     int64_t out_off;
-    int32_t N, C, M, k;
-    int32_t start_r;  // offset of start_idx inside its own sector
+    int32_t N, C, M;
+    int32_t kl, kr, flags;  // as in ItemDesc
+    int32_t start_r;        // offset of start_idx inside its own sector
     int32_t pad;
 };
 

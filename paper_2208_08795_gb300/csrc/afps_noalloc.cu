@@ -192,7 +192,9 @@ extern "C" int afps_sample_batched_noalloc(const float* d_xyz, const int64_t* h_
             d.c = (int32_t)(o1 - o0);
             d.first = start_r < d.n - 1 ? start_r : d.n - 1;
             d.lo = (int32_t)lo;
-            d.k = k;
+            d.kl = k / 2;  // the default NPDU window: k neighbours and the sample
+            d.kr = k - k / 2;
+            d.flags = 0;
             d.pad = 0;
         }
     }

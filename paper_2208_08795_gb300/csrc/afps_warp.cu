@@ -101,8 +101,9 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
 
         int32_t* out = a.out + d.dst;
         const int c = d.c;
-        const int kl = d.k >> 1;
-        const int kr = d.k - kl;
+        const int kl = d.kl;
+        const int kr = d.kr;
+        const bool full_first = (d.flags & ITEM_FULL_FIRST) != 0;
         int p = d.first;
         // sample t's index is kept by lane t % 32 and stored once per 32 samples
         int obuf = lane == 0 ? d.lo + p : 0;
@@ -110,9 +111,12 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
             const float qx = pts[3 * p], qy = pts[3 * p + 1], qz = pts[3 * p + 2];
             const unsigned long long qx2 = dev::pack2(qx, qx), qy2 = dev::pack2(qy, qy),
                                      qz2 = dev::pack2(qz, qz);
-            // window [p - kl, p + kr] as one unsigned range test
-            const unsigned wlo = (unsigned)(p - kl);
-            const unsigned wspan = (unsigned)(kl + kr);
+            // window [wl, wh] as one unsigned range test; the whole sector at
+            // the first update under the full-first-pass reading
+            const bool whole = full_first && t == 1;
+            const int wl = whole ? 0 : p - kl, wh = whole ? n - 1 : p + kr;
+            const unsigned wlo = (unsigned)wl;
+            const unsigned wspan = (unsigned)(wh - wl);
             float best = -1.f;
             int bi = 0;
 #pragma unroll
@@ -122,8 +126,7 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
                     // NPDU: every row pair is computed and the window applied as
                     // a mask, or (npdu_skip) pairs the window misses are skipped
                     // by a warp-uniform test; never a divergent branch.
-                    const bool hit = !NPDU || !a.npdu_skip ||
-                                     (32 * i0 + 63 >= p - kl && 32 * i0 <= p + kr);
+                    const bool hit = !NPDU || !a.npdu_skip || (32 * i0 + 63 >= wl && 32 * i0 <= wh);
                     if (hit) {
                         float d0, d1;
                         dev::sqdist2(X2[h], Y2[h], Z2[h], qx2, qy2, qz2, d0, d1);

@@ -212,6 +212,35 @@ def test_forced_variant(tmp_path, row):
         s.close()
 
 
+# --------------------------------------------------------------- NPDU readings
+READINGS = [(2048, 512, 32, 16), (2048, 512, 4, 8), (16384, 4096, 1, 8), (5000, 1000, 6, 9),
+            (1000, 250, 3, 1), (40000, 2000, 1, 5)]
+
+
+@pytest.mark.parametrize("method", [1, 2, 3])
+@pytest.mark.parametrize("N,C,M,k", READINGS)
+def test_npdu_readings(S, N, C, M, k, method):
+    """The other readings of the NPDU window, on warp, CTA and cluster paths."""
+    P = synth.uniform_cloud(N + method, N)
+    x = torch.from_numpy(P).cuda()
+    out = S.sample(x, C, M, k, 3, method=method)
+    S.sync()
+    assert_same(out.cpu().numpy(), oracle.afps(P, C, M, k, 3, method=method), f"method={method}")
+
+
+def test_npdu_readings_mixed_batch(S, objects):
+    clouds = objects[:6]
+    Ms, ks, methods = [32, 16, 4, 1, 32, 8], [16, 16, 8, 4, 1, 0], [1, 2, 3, 1, 2, 0]
+    xyz, off = synth.pack(clouds)
+    ba = B.BatchArgs(off, 512, Ms, ks, 0, method=methods)
+    out = S.sample_batched(torch.from_numpy(xyz).cuda(), ba)
+    S.sync()
+    o = out.cpu().numpy()
+    for b, P in enumerate(clouds):
+        ref = oracle.afps(P, 512, Ms[b], ks[b], 0, method=methods[b])
+        assert_same(o[ba.out_off[b]:ba.out_off[b + 1]], ref, f"cloud {b}")
+
+
 # --------------------------------------------------------------- batching
 def test_graph_replay_and_launch_count(objects):
     build_mod.build()
