@@ -212,6 +212,20 @@ int afps_sort_by_key(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const fl
                      int32_t key, float* d_xyz_sorted, int32_t* d_perm, void* stream);
 
 /*
+ * Coverage radius of sample sets: for each of B clouds, d_radius[b] =
+ * max over the cloud's points of the Euclidean distance to the nearest of
+ * its samples d_sel[h_sel_off[b] .. h_sel_off[b+1]) (indices relative to the
+ * cloud; out-of-range entries are clamped into it).  This is the quantity
+ * FPS greedily shrinks (property P1, Sec. II-B) and scores sampling variants
+ * without a trained network.  Computed in fp64 from the fp32 points with
+ * separately rounded operations, so any IEEE host reproduces it exactly.
+ * 1 <= B <= 65535.
+ */
+int afps_coverage_radius(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
+                         const int64_t* h_sel_off, const int32_t* d_sel, double* d_radius,
+                         void* stream);
+
+/*
  * Wait for the stream and report device-side errors recorded since the last
  * call (AFPS_ERR_TIMEOUT when a bounded wait gave up); clears them.
  */

@@ -39,7 +39,8 @@ EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
            "afps_describe_plan", "afps_launch_count", "afps_sample_batched_noalloc",
            "afps_server_create", "afps_server_submit", "afps_server_step", "afps_server_poll",
            "afps_server_stats", "afps_server_clock_ms", "afps_server_destroy",
-           "afps_sort_by_key", "afps_sample_ex", "afps_sample_batched_ex")
+           "afps_sort_by_key", "afps_sample_ex", "afps_sample_batched_ex",
+           "afps_coverage_radius")
 
 
 class AfpsLibraryError(RuntimeError):
@@ -114,6 +115,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.afps_sample_batched_ex.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.afps_sample_batched_ex.restype = ctypes.c_int
     L.afps_sort_by_key.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
+    L.afps_coverage_radius.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+    L.afps_coverage_radius.restype = ctypes.c_int
     L.afps_sort_by_key.restype = ctypes.c_int
     L.afps_server_create.argtypes = [ctypes.POINTER(vp), vp, ctypes.POINTER(afps_server_config), vp]
     L.afps_server_create.restype = ctypes.c_int
@@ -231,6 +234,10 @@ def afps_launch_count(ctx) -> int:
 
 def afps_sort_by_key(ctx, B, h_pt_off, d_xyz, key, d_xyz_sorted, d_perm, stream) -> int:
     return load().afps_sort_by_key(ctx, B, h_pt_off, d_xyz, key, d_xyz_sorted, d_perm, stream)
+
+
+def afps_coverage_radius(ctx, B, h_pt_off, d_xyz, h_sel_off, d_sel, d_radius, stream) -> int:
+    return load().afps_coverage_radius(ctx, B, h_pt_off, d_xyz, h_sel_off, d_sel, d_radius, stream)
 
 
 def afps_sample_batched_noalloc(d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
@@ -395,6 +402,16 @@ class Sampler:
         self._check(afps_sort_by_key(self.ctx, po.size - 1, _ptr(po), xyz.data_ptr(), key,
                                      out.data_ptr(), perm.data_ptr(), self._stream(stream)))
         return out, perm
+
+    def coverage_radius(self, xyz, pt_off, sel, sel_off, stream=None):
+        """fp64 coverage radius of each cloud's samples (a float64 tensor of B)."""
+        import torch
+        xyz = self._points(xyz)
+        po, so = _i64(pt_off), _i64(sel_off)
+        out = torch.empty(po.size - 1, dtype=torch.float64, device=xyz.device)
+        self._check(afps_coverage_radius(self.ctx, po.size - 1, _ptr(po), xyz.data_ptr(), _ptr(so),
+                                         sel.data_ptr(), out.data_ptr(), self._stream(stream)))
+        return out
 
     def sync(self, stream=None):
         self._check(afps_sync(self.ctx, self._stream(stream)))

@@ -105,7 +105,7 @@ struct afps_ctx {
     std::string last_error;
     cudaEvent_t ev_done = nullptr;    // last device work that used the shared workspace
     cudaStream_t capture = nullptr;   // private stream for graph capture
-    DevBuf items, counters, xyz_stage, out_stage, sort_scratch;
+    DevBuf items, counters, xyz_stage, out_stage, sort_scratch, cov_scratch;
     HostBuf stage[kStageSlots];         // pinned upload ring
     cudaEvent_t stage_ev[kStageSlots] = {};  // last copy out of each slot
     int stage_next = 0;
@@ -823,6 +823,7 @@ void afps_destroy(afps_ctx* ctx) {
         ctx->xyz_stage.release();
         ctx->out_stage.release();
         ctx->sort_scratch.release();
+        ctx->cov_scratch.release();
         for (int i = 0; i < kStageSlots; ++i) {
             ctx->stage[i].release();
             if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
@@ -1001,6 +1002,41 @@ int afps_sort_by_key(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const fl
                                       key, keys_a, idx_a, keys_b, idx_b, d_xyz_sorted, d_perm, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sort launch");
     ctx->launches += 1;
+    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, st));
+    return AFPS_OK;
+}
+
+int afps_coverage_radius(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
+                         const int64_t* h_sel_off, const int32_t* d_sel, double* d_radius,
+                         void* stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    if (B < 1 || B > 65535 || !h_pt_off || !h_sel_off || !d_xyz || !d_sel || !d_radius)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_coverage_radius: bad argument (1 <= B <= 65535)");
+    std::vector<afps::CoverageDesc> descs((size_t)B);
+    int32_t max_n = 1;
+    for (int32_t b = 0; b < B; ++b) {
+        const int64_t n = h_pt_off[b + 1] - h_pt_off[b];
+        const int64_t c = h_sel_off[b + 1] - h_sel_off[b];
+        if (n < 1 || n > INT32_MAX || c < 1 || c > INT32_MAX || h_pt_off[b] < 0 ||
+            h_sel_off[b] < 0) {
+            std::ostringstream os;
+            os << "afps_coverage_radius: cloud " << b << " has " << n << " points and " << c
+               << " samples (need both >= 1)";
+            return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
+        }
+        descs[b] = afps::CoverageDesc{h_pt_off[b], h_sel_off[b], (int32_t)n, (int32_t)c};
+        max_n = std::max<int32_t>(max_n, (int32_t)n);
+    }
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    AFPS_CUDA(ctx, ctx->cov_scratch.reserve(sizeof(unsigned long long) * (size_t)B));
+    int rc = upload(ctx, ctx->items, descs.data(), descs.size() * sizeof(afps::CoverageDesc), st);
+    if (rc != AFPS_OK) return rc;
+    cudaError_t e = afps::launch_coverage(
+        static_cast<const afps::CoverageDesc*>(ctx->items.p), B, max_n, d_xyz, d_sel,
+        static_cast<unsigned long long*>(ctx->cov_scratch.p), d_radius, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "coverage launch");
+    ctx->launches += 2;
     AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, st));
     return AFPS_OK;
 }

@@ -112,6 +112,17 @@ cudaError_t launch_gather(const GatherDesc* d_descs, int32_t B, int32_t max_n,
                           cudaStream_t stream);
 constexpr int32_t kGatherMaxPoints = 65536;
 
+// Coverage radius (afps_coverage_radius).
+struct CoverageDesc {
+    int64_t pt_off;   // first point of the cloud
+    int64_t sel_off;  // first sample index
+    int32_t n;        // points
+    int32_t c;        // samples
+};
+cudaError_t launch_coverage(const CoverageDesc* d_descs, int32_t B, int32_t max_n,
+                            const float* xyz, const int32_t* sel,
+                            unsigned long long* max_bits, double* radius, cudaStream_t stream);
+
 // Sort by key (afps_sort_by_key): one cloud per CTA.
 struct SortDesc {
     int64_t off;  // first point of the cloud
