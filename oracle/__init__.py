@@ -225,3 +225,23 @@ def sort_by_key(xyz, key: int):
     pts = _points(xyz)
     perm = np.argsort(sort_key(pts, key), kind="stable").astype(np.int32)
     return pts[perm], perm
+
+
+def ball_query(xyz, centroids, radius: float, K: int, *, library=None) -> np.ndarray:
+    """First K points (storage order) within `radius` of each centroid,
+    padded with the first one found: (C, K) int32."""
+    L = library or lib()
+    if not hasattr(L, "_bq"):
+        L.oracle_ball_query.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
+                                        ctypes.c_void_p]
+        L.oracle_ball_query.restype = ctypes.c_int
+        L._bq = True
+    pts = _points(xyz)
+    c = np.ascontiguousarray(centroids, dtype=np.int32)
+    out = np.full((c.size, int(K)), -1, dtype=np.int32)
+    rc = L.oracle_ball_query(pts.ctypes.data, pts.shape[0], c.ctypes.data, c.size,
+                             float(radius), int(K), out.ctypes.data)
+    if rc != OK:
+        raise OracleError(rc)
+    return out

@@ -297,3 +297,36 @@ double oracle_coverage_radius(const float* xyz, int64_t N, const int32_t* idx, i
     }
     return sqrt(worst);
 }
+
+/*
+ * Ball query (the grouping step that follows sampling in a PointNet++ set
+ * abstraction, Sec. I-II; the paper does not define it, this is the usual
+ * reading): for each of the C centroids (indices into the cloud), the first
+ * K points in storage order whose squared distance to the centroid,
+ * (dx*dx + dy*dy) + dz*dz in fp32, is below radius*radius (fp32); when fewer
+ * than K are found the remaining slots repeat the first one found (or -1 if
+ * none).  out: C x K int32.  Returns ORACLE_OK or ORACLE_ERR_INVALID_ARG.
+ */
+int oracle_ball_query(const float* xyz, int64_t N, const int32_t* centroids, int32_t C,
+                      float radius, int32_t K, int32_t* out)
+{
+    if (!xyz || !centroids || !out || N < 1 || C < 0 || K < 1 || !(radius > 0.0f))
+        return ORACLE_ERR_INVALID_ARG;
+    const float r2 = radius * radius;
+    for (int32_t s = 0; s < C; ++s) {
+        const int64_t q = centroids[s];
+        if (q < 0 || q >= N) return ORACLE_ERR_INVALID_ARG;
+        const float cx = xyz[3 * q + 0], cy = xyz[3 * q + 1], cz = xyz[3 * q + 2];
+        int32_t cnt = 0;
+        for (int64_t j = 0; j < N && cnt < K; ++j) {
+            float dx = xyz[3 * j + 0] - cx;
+            float dy = xyz[3 * j + 1] - cy;
+            float dz = xyz[3 * j + 2] - cz;
+            float d2 = (dx * dx + dy * dy) + dz * dz;
+            if (d2 < r2) out[(int64_t)s * K + cnt++] = (int32_t)j;
+        }
+        const int32_t fill = cnt > 0 ? out[(int64_t)s * K] : -1;
+        for (int32_t i = cnt; i < K; ++i) out[(int64_t)s * K + i] = fill;
+    }
+    return ORACLE_OK;
+}

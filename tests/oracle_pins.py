@@ -329,6 +329,34 @@ def pin_chain_grid(L):
         assert list(got[j]) == expect, (j, list(got[j]), expect)
 
 
+def pin_ball_query(L):
+    """Ball query: closed form on the integer grid (radius 2.5 holds the
+    points i-2 .. i+2), and a vectorised numpy restatement on clouds."""
+    P = np.zeros((50, 3), dtype=np.float32)
+    P[:, 0] = np.arange(50)
+    cen = np.array([0, 1, 10, 48, 49])
+    got = oracle.ball_query(P, cen, 2.5, 6, library=L)
+    for row, i in zip(got, cen):
+        near = [j for j in range(i - 2, i + 3) if 0 <= j < 50]
+        assert list(row) == near + [near[0]] * (6 - len(near)), (i, row)
+    got = oracle.ball_query(P, cen, 2.5, 3, library=L)
+    assert [list(r) for r in got] == [[0, 1, 2], [0, 1, 2], [8, 9, 10], [46, 47, 48], [47, 48, 49]]
+    # radius exactly 2: the points at distance 2 lie on the sphere and are excluded
+    got = oracle.ball_query(P, np.array([10]), 2.0, 4, library=L)
+    assert list(got[0]) == [9, 10, 11, 9]
+    for seed, (N, C, r, K) in enumerate([(500, 40, 0.15, 16), (300, 30, 0.3, 64), (200, 10, 0.02, 8)]):
+        Q = synth.uniform_cloud(700 + seed, N, None)
+        cen = np.arange(0, N, N // C)[:C]
+        got = oracle.ball_query(Q, cen, r, K, library=L)
+        r2 = np.float32(r) * np.float32(r)
+        for row, c in zip(got, cen):
+            d = Q - Q[c]
+            d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+            hit = np.nonzero(d2 < r2)[0][:K]
+            want = list(hit) + [hit[0]] * (K - len(hit)) if len(hit) else [-1] * K
+            assert list(row) == want, (seed, c)
+
+
 PINS = [pin_golden, pin_grid_closed_form, pin_npdu_stride_law, pin_brute_force,
         pin_brute_force_f64, pin_reductions, pin_invariants, pin_every_point, pin_metamorphic,
-        pin_errors, pin_coverage_radius, pin_chain_grid, pin_npdu_readings]
+        pin_errors, pin_coverage_radius, pin_chain_grid, pin_npdu_readings, pin_ball_query]

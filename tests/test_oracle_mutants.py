@@ -38,6 +38,10 @@ MUTANTS = [
     ("start_unclipped", "first[s] = l + (r < n - 1 ? r : n - 1);", "first[s] = l + r;", 0),
     ("too_small_unchecked", "if (c > n) return ORACLE_ERR_SECTOR_TOO_SMALL;", "", 0),
     ("coverage_max", "if (d < best) best = d;", "if (d > best && best != INFINITY) best = d;", 0),
+    ("ball_le", "if (d2 < r2) out", "if (d2 <= r2) out", 0),
+    ("ball_pad_last", "const int32_t fill = cnt > 0 ? out[(int64_t)s * K] : -1;",
+     "const int32_t fill = cnt > 0 ? out[(int64_t)s * K + cnt - 1] : -1;", 0),
+    ("ball_drop_dz", "float d2 = (dx * dx + dy * dy) + dz * dz;", "float d2 = (dx * dx + dy * dy);", 0),
 ]
 
 
