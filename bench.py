@@ -345,6 +345,35 @@ def sort_section(sampler, flush, dev, steps: int):
     return {"workload": "stable radix sort by x of shuffled clouds (one CTA per cloud)", **rows}
 
 
+def group_section(sampler, x, off, flush, dev, steps: int):
+    """Ball query after sampling on the object batch: the NPDU-AFPS samples
+    (C = 512 per cloud) as centroids, radius 0.2, K = 32; full scan against
+    the range-limited scan that the x-sorted storage allows."""
+    import torch
+    from paper_2208_08795_gb300 import afps as A
+    ba = A.BatchArgs(off, C_SAMPLES, M_SECTORS, K_WINDOW, 0)
+    sel = sampler.sample_batched(x, ba)
+    grp = torch.empty((ba.total_out, 32), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    rows = {}
+    for name, axis in (("full_scan", -1), ("sorted_range_scan", 0)):
+        for _ in range(3):
+            sampler.ball_query(x, off, sel, ba.out_off, 0.2, 32, axis, grp)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            sampler.ball_query(x, off, sel, ba.out_off, 0.2, 32, axis, grp)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        rows[name] = {"ms": round(ms, 4), "clouds_per_s": round(B_CLOUDS / (ms / 1e3), 1)}
+    return {"workload": "ball query r=0.2 K=32 around the 512 NPDU-AFPS samples of each of "
+                        "32 x 2048-point clouds", **rows}
+
+
 # ------------------------------------------------------------------ serving
 SERVING_LEVELS = [16384, 4096, 1024, 256]
 SERVING_RATES = [500.0, 2000.0, 8000.0, 32000.0]
@@ -482,6 +511,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     large = large_clouds(sampler, flush, dev, extra_steps) if args.configs else None
     ragged = ragged_batch(sampler, flush, dev, extra_steps) if args.configs else None
     sorting = sort_section(sampler, flush, dev, extra_steps) if args.configs else None
+    grouping = group_section(sampler, x, off, flush, dev, extra_steps) if args.configs else None
     clk = clocks.stop()
     e2e_ok = bool(np.array_equal(h_out, head_out))
 
@@ -528,6 +558,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         "large_clouds": large,
         "ragged_batch": ragged,
         "sort_by_key": sorting,
+        "ball_query": grouping,
         "gpu_launches": launches,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},

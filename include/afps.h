@@ -226,6 +226,22 @@ int afps_coverage_radius(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, cons
                          void* stream);
 
 /*
+ * Ball query, the grouping step that follows sampling in a PointNet++ set
+ * abstraction (Sec. I-II; the paper does not define it, this is the usual
+ * reading).  For each centroid d_sel[i] (cloud-relative, i in
+ * [h_sel_off[b], h_sel_off[b+1]) for cloud b, clamped into the cloud):
+ * d_group[i*K .. i*K+K) = the first K points of the cloud in storage order
+ * whose fp32 squared distance (dx*dx + dy*dy) + dz*dz is below
+ * radius*radius, the remaining slots repeating the first one found (-1 if
+ * none).  sorted_axis = 0, 1, 2 promises the cloud is sorted ascending along
+ * x, y or z, which lets the scan cover only the index range that can hold
+ * hits (same result as a full scan); -1 scans every point.  1 <= B <= 65535.
+ */
+int afps_ball_query(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
+                    const int64_t* h_sel_off, const int32_t* d_sel, float radius, int32_t K,
+                    int32_t sorted_axis, int32_t* d_group, void* stream);
+
+/*
  * Wait for the stream and report device-side errors recorded since the last
  * call (AFPS_ERR_TIMEOUT when a bounded wait gave up); clears them.
  */

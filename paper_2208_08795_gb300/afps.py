@@ -40,7 +40,7 @@ EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
            "afps_server_create", "afps_server_submit", "afps_server_step", "afps_server_poll",
            "afps_server_stats", "afps_server_clock_ms", "afps_server_destroy",
            "afps_sort_by_key", "afps_sample_ex", "afps_sample_batched_ex",
-           "afps_coverage_radius")
+           "afps_coverage_radius", "afps_ball_query")
 
 
 class AfpsLibraryError(RuntimeError):
@@ -116,6 +116,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.afps_sample_batched_ex.restype = ctypes.c_int
     L.afps_sort_by_key.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp]
     L.afps_coverage_radius.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+    L.afps_ball_query.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.c_float, i32, i32, vp, vp]
+    L.afps_ball_query.restype = ctypes.c_int
     L.afps_coverage_radius.restype = ctypes.c_int
     L.afps_sort_by_key.restype = ctypes.c_int
     L.afps_server_create.argtypes = [ctypes.POINTER(vp), vp, ctypes.POINTER(afps_server_config), vp]
@@ -238,6 +240,12 @@ def afps_sort_by_key(ctx, B, h_pt_off, d_xyz, key, d_xyz_sorted, d_perm, stream)
 
 def afps_coverage_radius(ctx, B, h_pt_off, d_xyz, h_sel_off, d_sel, d_radius, stream) -> int:
     return load().afps_coverage_radius(ctx, B, h_pt_off, d_xyz, h_sel_off, d_sel, d_radius, stream)
+
+
+def afps_ball_query(ctx, B, h_pt_off, d_xyz, h_sel_off, d_sel, radius, K, sorted_axis, d_group,
+                    stream) -> int:
+    return load().afps_ball_query(ctx, B, h_pt_off, d_xyz, h_sel_off, d_sel, radius, K,
+                                  sorted_axis, d_group, stream)
 
 
 def afps_sample_batched_noalloc(d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
@@ -411,6 +419,19 @@ class Sampler:
         out = torch.empty(po.size - 1, dtype=torch.float64, device=xyz.device)
         self._check(afps_coverage_radius(self.ctx, po.size - 1, _ptr(po), xyz.data_ptr(), _ptr(so),
                                          sel.data_ptr(), out.data_ptr(), self._stream(stream)))
+        return out
+
+    def ball_query(self, xyz, pt_off, sel, sel_off, radius: float, K: int,
+                   sorted_axis: int = -1, out=None, stream=None):
+        """First K points within `radius` of every centroid: (sum C, K) int32."""
+        import torch
+        xyz = self._points(xyz)
+        po, so = _i64(pt_off), _i64(sel_off)
+        if out is None:
+            out = torch.empty((int(so[-1]), K), dtype=torch.int32, device=xyz.device)
+        self._check(afps_ball_query(self.ctx, po.size - 1, _ptr(po), xyz.data_ptr(), _ptr(so),
+                                    sel.data_ptr(), radius, K, sorted_axis, out.data_ptr(),
+                                    self._stream(stream)))
         return out
 
     def sync(self, stream=None):

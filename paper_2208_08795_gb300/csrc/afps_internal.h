@@ -123,6 +123,17 @@ cudaError_t launch_coverage(const CoverageDesc* d_descs, int32_t B, int32_t max_
                             const float* xyz, const int32_t* sel,
                             unsigned long long* max_bits, double* radius, cudaStream_t stream);
 
+// Ball query (afps_ball_query).
+struct GroupDesc {
+    int64_t pt_off;   // first point of the cloud
+    int64_t sel_off;  // first centroid (and output row)
+    int32_t n;        // points
+    int32_t c;        // centroids
+};
+cudaError_t launch_ball_query(const GroupDesc* d_descs, int32_t B, int32_t max_c,
+                              const float* xyz, const int32_t* sel, float radius, int32_t K,
+                              int32_t axis, int32_t* out, cudaStream_t stream);
+
 // Sort by key (afps_sort_by_key): one cloud per CTA.
 struct SortDesc {
     int64_t off;  // first point of the cloud
