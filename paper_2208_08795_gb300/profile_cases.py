@@ -9,6 +9,9 @@ Cases (inputs from `synth`, kernel variants from the default planner):
   npdu32k      the same cloud, NPDU-AFPS M = 32, k = 16
   ragged       256 clouds of 2K-32K points, C = N/4, sectors of ~256 points, k = 16 (persistent)
   chain        one LiDAR-like frame, levels 16384 -> 4096 -> 1024 -> 256, M = 32, k = 16
+  sort         the object batch in random storage order, sorted by x
+  group        ball query (r = 0.2, K = 32) around the headline samples of the batch
+  coverage     coverage radius of the headline samples of the batch
 """
 from __future__ import annotations
 
@@ -19,7 +22,8 @@ import torch
 
 from . import afps, build, synth
 
-CASES = ("headline", "fps2048", "cluster32k", "npdu32k", "ragged", "chain")
+CASES = ("headline", "fps2048", "cluster32k", "npdu32k", "ragged", "chain", "sort", "group",
+         "coverage")
 
 
 def run(case: str, reps: int) -> None:
@@ -44,6 +48,24 @@ def run(case: str, reps: int) -> None:
         M, k = (1, 0) if case == "cluster32k" else (32, 16)
         for _ in range(reps):
             s.sample(x, 8192, M, k, 0)
+    elif case in ("sort", "group", "coverage"):
+        clouds = synth.object_batch(1, 32, 2048)
+        if case == "sort":
+            g = synth.rng(11)
+            clouds = [c[g.permutation(c.shape[0])] for c in clouds]
+        xyz, off = synth.pack(clouds)
+        x = torch.from_numpy(xyz).to(dev)
+        if case == "sort":
+            for _ in range(reps):
+                s.sort_by_key(x, off, afps.AFPS_KEY_X)
+        else:
+            ba = afps.BatchArgs(off, 512, 32, 16, 0)
+            sel = s.sample_batched(x, ba)
+            for _ in range(reps):
+                if case == "group":
+                    s.ball_query(x, off, sel, ba.out_off, 0.2, 32, 0)
+                else:
+                    s.coverage_radius(x, off, sel, ba.out_off)
     elif case == "chain":
         frame = torch.from_numpy(synth.lidar_frame(5)).to(dev)
         for _ in range(reps):
