@@ -343,6 +343,8 @@ typedef struct afps_server_config {
     int32_t M;                 /* sectors per level (capped at the level's size) */
     int32_t npdu_window;       /* k >= 0 (0 = no NPDU) */
     int32_t max_steps_ahead;   /* <= 0: 2 */
+    int32_t pad;
+    int64_t host_pool_bytes;   /* page-locked staging for queued frames; <= 0: 64 MiB */
 } afps_server_config;
 
 typedef struct afps_server_result {
@@ -360,9 +362,11 @@ typedef struct afps_server_result {
 int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_config* cfg,
                        void* stream);
 
-/* Queue one frame (N points, host memory, copied before return).  Needs
- * levels[0] <= N <= 65536 and the request to fit the arena on its own.
- * Returns AFPS_ERR_BUSY when max_queued frames are waiting. */
+/* Queue one frame (N points, host memory, copied into the server's
+ * page-locked pool before return, so that admission is an asynchronous DMA).
+ * Needs levels[0] <= N <= 65536 and the request to fit the arena on its own.
+ * Returns AFPS_ERR_BUSY when max_queued frames are waiting or the pool is
+ * full. */
 int afps_server_submit(afps_server* srv, const float* h_xyz, int64_t N, uint64_t tag);
 
 /* One continuous-batching step (see above).  Returns the number of requests

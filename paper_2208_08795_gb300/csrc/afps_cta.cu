@@ -57,23 +57,25 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
     Rec* recs = reinterpret_cast<Rec*>(smem + 32);
     unsigned char* buf = smem + 32 + 2 * E * sizeof(Rec);
     const uint32_t bar = dev::smem_u32(barp);
-    const uint32_t xbar[2] = {dev::smem_u32(barp + 1), dev::smem_u32(barp + 2)};
+    const uint32_t xbar0 = dev::smem_u32(barp + 1), xbar1 = dev::smem_u32(barp + 2);
     const uint32_t xbytes = (uint32_t)(E * sizeof(Rec));  // expected per exchange
     if (tid == 0) {
         dev::mbar_init(bar, 1);
         if (CLUSTER) {
-            dev::mbar_init(xbar[0], 1);
-            dev::mbar_init(xbar[1], 1);
+            dev::mbar_init(xbar0, 1);
+            dev::mbar_init(xbar1, 1);
         }
         dev::fence_mbar_init();
         if (CLUSTER) {
-            dev::mbar_arrive_expect_tx(xbar[0], xbytes);
-            dev::mbar_arrive_expect_tx(xbar[1], xbytes);
+            dev::mbar_arrive_expect_tx(xbar0, xbytes);
+            dev::mbar_arrive_expect_tx(xbar1, xbytes);
         }
     }
     __syncthreads();
     if (CLUSTER) dev::cluster_sync();  // every peer's barriers exist before any remote store
-    uint32_t xphase[2] = {0u, 0u};
+    // barrier addresses and phases in scalars: a two-element array indexed
+    // by the exchange parity would live in a local-memory stack frame
+    uint32_t xphase0 = 0u, xphase1 = 0u;
 
     uint32_t phase = 0;
     uint32_t xchg = 0;  // exchange counter: record buffer parity
@@ -144,7 +146,61 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
         const bool emitter = (rank == 0) && (w == 0);
         int obuf = lane == 0 ? d.lo + p : 0;
 
-        for (int t = 1; t < c; ++t) {
+        int t0 = 1;
+        if (NPDU && !CLUSTER && !full_first && p <= kl && kl <= kr) {
+            // Stride phase of the literal NPDU reading (Sec. III-C; distances
+            // start at 1e10): while points past the last window are untouched
+            // they hold the maximum, so the lowest-index argmax is the first of
+            // them and the samples are p, p + q, p + 2q, ... (q = kr + 1) until
+            // a window reaches the sector's end.  Their window updates run here
+            // at once (with kl <= kr a point lies in at most two windows); the
+            // argmax rounds they replace are decided in advance provided every
+            // windowed distance is below 1e10, else the serial loop runs from
+            // the start.
+            const int q = kr + 1;
+            const int x = n - 1 - kr - p;
+            const int ts = x <= 0 ? 1 : (x + q - 1) / q + 1;  // samples of the stride
+            const int tn = min(ts, c);                        // of them emitted
+            const int tw = min(ts, c - 1);                    // whose window is applied
+            bool ok = true;  // D is updated in place and reset if the test fails
+#pragma unroll
+            for (int i = 0; i < 2 * PP; ++i) {
+                const int j = tid + T * i;
+                if (i < P && j < n) {
+                    const float px = pts[3 * j], py = pts[3 * j + 1], pz = pts[3 * j + 2];
+                    const int y = j - kr - p;
+                    const int tlo = y <= 0 ? 0 : (y + q - 1) / q;
+                    const int thi = min(tw - 1, (j + kl - p) / q);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (tlo + u <= thi) {
+                            const int sj = p + (tlo + u) * q;
+                            const float dd = dev::sqdist(px, py, pz, pts[3 * sj],
+                                                         pts[3 * sj + 1], pts[3 * sj + 2]);
+                            ok = ok && dd < 1e10f;
+                            D[i] = fminf(D[i], dd);
+                        }
+                    }
+                }
+            }
+            if (__syncthreads_and(ok)) {
+                if (emitter) {
+                    for (int r0 = 0; r0 + 32 <= tn; r0 += 32)
+                        out[r0 + lane] = d.lo + p + (r0 + lane) * q;
+                    obuf = d.lo + p + (((tn - 1) & ~31) + lane) * q;
+                }
+                p += (tn - 1) * q;
+                qx = pts[3 * p];
+                qy = pts[3 * p + 1];
+                qz = pts[3 * p + 2];
+                t0 = tn;  // re-applying the last window is a no-op
+            } else {
+#pragma unroll
+                for (int i = 0; i < 2 * PP; ++i) D[i] = (i < P && tid + T * i < n) ? 1e10f : 0.f;
+            }
+        }
+
+        for (int t = t0; t < c; ++t) {
             // 1. update + local argmax (chunk-local offsets)
             const bool whole = full_first && t == 1;  // full first pass reading
             const int wlo = whole ? -c0 : p - kl - c0, whi = whole ? n - 1 - c0 : p + kr - c0;
@@ -194,13 +250,14 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             const unsigned jw = __reduce_min_sync(dev::kFull, cand);  // chunk-local
             const uint32_t jinv = 0xffffffffu - (uint32_t)(c0 + (int)jw);
             const uint32_t xb = xchg & 1u;
+            const uint32_t xbar = xb ? xbar1 : xbar0;
             Rec* R = recs + xb * E;
             if (CLUSTER) {
                 if (lane < CS) {
                     const float wx = pts[3 * jw], wy = pts[3 * jw + 1], wz = pts[3 * jw + 2];
                     const uint32_t slot = dev::smem_u32(&R[rank * W + w]);
                     const uint32_t remote = dev::mapa(slot, (uint32_t)lane);
-                    const uint32_t rbar = dev::mapa(xbar[xb], (uint32_t)lane);
+                    const uint32_t rbar = dev::mapa(xbar, (uint32_t)lane);
                     dev::st_async_v4(remote, rbar, m, jinv, __float_as_uint(wx), __float_as_uint(wy));
                     dev::st_async_v4(remote + 16, rbar, __float_as_uint(wz), 0u, 0u, 0u);
                 }
@@ -210,9 +267,12 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
 
             // 3. wait for every record of this exchange
             if (CLUSTER) {
-                if (!dev::mbar_wait_bounded(xbar[xb], xphase[xb], a.timeout_ns))
+                if (!dev::mbar_wait_bounded(xbar, xb ? xphase1 : xphase0, a.timeout_ns))
                     dev::record_status(a.status, DEV_TIMEOUT_EXCHANGE);
-                xphase[xb] ^= 1u;
+                if (xb)
+                    xphase1 ^= 1u;
+                else
+                    xphase0 ^= 1u;
             } else {
                 __syncthreads();
             }
@@ -243,7 +303,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             }
             if (CLUSTER) {  // re-arm this buffer once every local reader is done
                 __syncthreads();
-                if (tid == 0) dev::mbar_arrive_expect_tx(xbar[xb], xbytes);
+                if (tid == 0) dev::mbar_arrive_expect_tx(xbar, xbytes);
             }
             ++xchg;
             if (emitter) {

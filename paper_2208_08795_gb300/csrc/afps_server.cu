@@ -81,7 +81,7 @@ enum State { QUEUED, ACTIVE, COMPLETING, DONE };
 struct Request {
     uint64_t tag = 0;
     int64_t N = 0;
-    std::vector<float> frame;  // host copy until admission
+    Block staged;              // the frame in the page-locked pool until admitted
     State state = QUEUED;
     int level = 0;             // next level to sample
     Block block;
@@ -106,6 +106,11 @@ struct afps_server {
     int device = 0;
     unsigned char* arena_base = nullptr;
     std::unique_ptr<Arena> arena;
+    unsigned char* pool_base = nullptr;  // page-locked staging of queued frames
+    std::unique_ptr<Arena> pool;
+    // pool blocks whose host->device copy was issued in a step, with that
+    // step's event: they are free once the event completes
+    std::deque<std::pair<cudaEvent_t, std::vector<Block>>> pool_pending;
     int32_t* pinned = nullptr;  // max_inflight result slots
     std::vector<int> free_slots;
     std::deque<std::unique_ptr<Request>> queue;
@@ -254,6 +259,17 @@ int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_confi
     }
     s->pinned = static_cast<int32_t*>(h);
     for (int i = s->cfg.max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
+    if (s->cfg.host_pool_bytes <= 0) s->cfg.host_pool_bytes = 64ll << 20;
+    void* hp = nullptr;
+    if (cudaMallocHost(&hp, (size_t)s->cfg.host_pool_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(h);
+        cudaFree(p);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        return AFPS_ERR_NO_MEMORY;
+    }
+    s->pool_base = static_cast<unsigned char*>(hp);
+    s->pool.reset(new Arena(s->cfg.host_pool_bytes / kBlockAlign * kBlockAlign));
     *out = s.release();
     return AFPS_OK;
 }
@@ -262,11 +278,24 @@ int afps_server_submit(afps_server* s, const float* h_xyz, int64_t N, uint64_t t
     if (!s || !h_xyz || N < s->levels[0] || N > 65536) return AFPS_ERR_INVALID_ARG;
     if (footprint(s, N) > s->cfg.hbm_budget_bytes) return AFPS_ERR_INVALID_ARG;
     if ((int64_t)s->queue.size() >= s->cfg.max_queued) return AFPS_ERR_BUSY;
+    // release staging blocks whose copies have completed
+    while (!s->pool_pending.empty() && cudaEventQuery(s->pool_pending.front().first) == cudaSuccess) {
+        for (const Block& b : s->pool_pending.front().second) s->pool->release(b);
+        give_event(s, s->pool_pending.front().first);
+        s->pool_pending.pop_front();
+    }
+    cudaGetLastError();
+    const Block staged = s->pool->alloc(12 * N);
+    if (staged.off < 0) return AFPS_ERR_BUSY;
     std::unique_ptr<Request> r(new (std::nothrow) Request());
-    if (!r) return AFPS_ERR_NO_MEMORY;
+    if (!r) {
+        s->pool->release(staged);
+        return AFPS_ERR_NO_MEMORY;
+    }
     r->tag = tag;
     r->N = N;
-    r->frame.assign(h_xyz, h_xyz + 3 * N);
+    r->staged = staged;
+    memcpy(s->pool_base + staged.off, h_xyz, (size_t)(12 * N));
     r->t_submit = s->now();
     s->queue.push_back(std::move(r));
     return AFPS_OK;
@@ -292,17 +321,24 @@ int afps_server_step(afps_server* s) {
     // admission, first come first served, by arena footprint and slots
     float* xyz = reinterpret_cast<float*>(s->arena_base);
     int32_t* ints = reinterpret_cast<int32_t*>(s->arena_base);
+    std::vector<Block> copied;  // staging blocks read by this step's copies
     while (!s->queue.empty() && (int)s->active.size() < s->cfg.max_inflight) {
         Request& r = *s->queue.front();
         if (!admit_one(s, r)) break;
-        if (cudaMemcpyAsync(xyz + 3 * r.xyz_pt[0], r.frame.data(), r.frame.size() * sizeof(float),
-                            cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+        if (cudaMemcpyAsync(xyz + 3 * r.xyz_pt[0], s->pool_base + r.staged.off,
+                            (size_t)(12 * r.N), cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
             cudaGetLastError();
             return AFPS_ERR_CUDA;
         }
-        std::vector<float>().swap(r.frame);
+        copied.push_back(r.staged);
+        r.staged = Block{};
         s->active.push_back(std::move(s->queue.front()));
         s->queue.pop_front();
+    }
+    if (!copied.empty()) {
+        cudaEvent_t ce = take_event(s);
+        if (!ce || cudaEventRecord(ce, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
+        s->pool_pending.emplace_back(ce, std::move(copied));
     }
 
     // one batched sampling launch over every active request's current level
@@ -418,6 +454,8 @@ void afps_server_destroy(afps_server* s) {
     for (auto& r : s->active)
         if (r && r->done_ev) cudaEventDestroy(r->done_ev);
     for (cudaEvent_t e : s->step_events) cudaEventDestroy(e);
+    for (auto& pp : s->pool_pending) cudaEventDestroy(pp.first);
+    if (s->pool_base) cudaFreeHost(s->pool_base);
     for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
     if (s->arena_base) cudaFree(s->arena_base);
     if (s->pinned) cudaFreeHost(s->pinned);

@@ -107,7 +107,54 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         int p = d.first;
         // sample t's index is kept by lane t % 32 and stored once per 32 samples
         int obuf = lane == 0 ? d.lo + p : 0;
-        for (int t = 1; t < c; ++t) {
+        int t0 = 1;
+        if (NPDU && !full_first && p <= kl && kl <= kr) {
+            // Stride phase of the literal NPDU reading (distances start at
+            // 1e10, Sec. III-C): while points past the last window are
+            // untouched they hold the maximum 1e10, so the lowest-index argmax
+            // is the first of them and the samples are p, p + q, p + 2q, ...
+            // (q = kr + 1) until a window reaches the sector's end.  Their
+            // window updates are independent and run here at once; the argmax
+            // scans they replace are decided in advance, provided every
+            // windowed distance is below 1e10 (else the serial loop runs from
+            // the start).  With kl <= kr a point lies in at most two windows.
+            const int q = kr + 1;
+            const int x = n - 1 - kr - p;
+            const int ts = x <= 0 ? 1 : (x + q - 1) / q + 1;  // samples of the stride
+            const int tn = min(ts, c);                        // of them emitted
+            const int tw = min(ts, c - 1);                    // whose window is applied
+            bool ok = true;  // D is updated in place and reset if the test fails
+#pragma unroll
+            for (int i = 0; i < 2 * PP; ++i) {
+                const int j = lane + 32 * i;
+                if (i < P && j < n) {
+                    const float px = pts[3 * j], py = pts[3 * j + 1], pz = pts[3 * j + 2];
+                    const int y = j - kr - p;
+                    const int tlo = y <= 0 ? 0 : (y + q - 1) / q;
+                    const int thi = min(tw - 1, (j + kl - p) / q);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (tlo + u <= thi) {
+                            const int sj = p + (tlo + u) * q;
+                            const float dd = dev::sqdist(px, py, pz, pts[3 * sj],
+                                                         pts[3 * sj + 1], pts[3 * sj + 2]);
+                            ok = ok && dd < 1e10f;
+                            D[i] = fminf(D[i], dd);
+                        }
+                    }
+                }
+            }
+            if (__all_sync(dev::kFull, ok)) {
+                for (int r0 = 0; r0 + 32 <= tn; r0 += 32) out[r0 + lane] = d.lo + p + (r0 + lane) * q;
+                obuf = d.lo + p + (((tn - 1) & ~31) + lane) * q;
+                p += (tn - 1) * q;
+                t0 = tn;  // re-applying the last window is a no-op
+            } else {
+#pragma unroll
+                for (int i = 0; i < 2 * PP; ++i) D[i] = (i < P && lane + 32 * i < n) ? 1e10f : 0.f;
+            }
+        }
+        for (int t = t0; t < c; ++t) {
             const float qx = pts[3 * p], qy = pts[3 * p + 1], qz = pts[3 * p + 2];
             const unsigned long long qx2 = dev::pack2(qx, qx), qy2 = dev::pack2(qy, qy),
                                      qz2 = dev::pack2(qz, qz);

@@ -212,6 +212,65 @@ def test_forced_variant(tmp_path, row):
         s.close()
 
 
+# --------------------------------------------------------------- NPDU stride phase
+# Under the literal NPDU reading (distances start at 1e10) the first samples of
+# a sector started at offset r <= floor(k/2) are r, r + q, r + 2q, ... with
+# q = k - floor(k/2) + 1, until a window reaches the sector's end; the kernels
+# apply those windows at once and skip the argmax rounds whose outcome that
+# fixes, unless a windowed distance reaches 1e10 (then they run the serial
+# loop from the start).  The cases put the number of samples on either side
+# of the stride's length, on a 32-sample row boundary, with starts inside and
+# outside the half window, the other window reading, and coordinates far
+# enough apart to reach 1e10.
+STRIDE_KERNELS = [(0, 2, 4, 1), (0, 8, 2, 1), (1, 2, 8, 1), (1, 8, 4, 1), (1, 16, 8, 1)]
+
+
+def stride_len(n, k, r, method=0):
+    kl, kr = ((k - 1) // 2, (k - 1) - (k - 1) // 2) if method == 2 else (k // 2, k - k // 2)
+    x = n - 1 - kr - r
+    return 1 if x <= 0 else (x + kr) // (kr + 1) + 1
+
+
+def stride_cases(n):
+    ts = stride_len(n, 16, 0)
+    rows = [(16, 0, 0, max(1, ts - 1), 1.0), (16, 0, 0, ts, 1.0), (16, 0, 3, ts + 1, 1.0),
+            (16, 0, 8, min(n, stride_len(n, 16, 8) + 40), 1.0),
+            (16, 0, 9, min(n, ts + 5), 1.0), (8, 2, 1, min(n, 2 * stride_len(n, 8, 1, 2)), 1.0),
+            (16, 0, 0, min(n, ts + 7), 3e5), (2, 0, 1, n, 1.0), (16, 0, 0, 1, 1.0)]
+    # a stride of exactly 32 samples ends on a row boundary: n = 31 q + kr + 1
+    if n >= 288:
+        rows.append((16, 0, 0, 40, 1.0))
+    return rows
+
+
+@pytest.mark.parametrize("kern", STRIDE_KERNELS, ids=[str(k) for k in STRIDE_KERNELS])
+def test_npdu_stride_phase(tmp_path, kern):
+    kind, Pp, W, CS = kern
+    build_mod.build()
+    cap = 32 * Pp if kind == 0 else 32 * W * Pp
+    sizes = [cap - 3] + ([288] if cap >= 288 else [])
+    for n in sizes:
+        M = 3
+        N = M * n
+        for (k, method, r, c, scale) in stride_cases(n):
+            if n == 288 and (k, c) != (16, 40):
+                continue
+            C = M * c
+            key = f"npdu:n{n}:c{c}:i{pow2(M)}"
+            path = tmp_path / "tune.txt"
+            path.write_text(f"{key} {kind} {Pp} {W} {CS} 0 0\n")
+            s = B.Sampler(0, tune_cache=str(path))
+            try:
+                P = (synth.uniform_cloud(7 * n + k + r, N) * scale).astype(np.float32)
+                out = s.sample(torch.from_numpy(P).cuda(), C, M, k, r, method=method)
+                s.sync()
+                ref = oracle.afps(P, C, M, k, r, method=method)
+                assert_same(out.cpu().numpy(), ref,
+                            f"{s.describe_plan(n, c, k, M)} n={n} c={c} k={k} r={r} m={method} x{scale}")
+            finally:
+                s.close()
+
+
 # --------------------------------------------------------------- NPDU readings
 READINGS = [(2048, 512, 32, 16), (2048, 512, 4, 8), (16384, 4096, 1, 8), (5000, 1000, 6, 9),
             (1000, 250, 3, 1), (40000, 2000, 1, 5)]

@@ -89,3 +89,34 @@ def test_submit_rejects_bad_frames(sampler):
         drain(srv, 1)
     finally:
         srv.close()
+
+
+def test_host_pool_recycles_blocks(sampler):
+    """Queued frames wait in a page-locked pool of two frames' size: a third
+    submit is refused until admission has copied a frame out, and the blocks
+    are reused for a stream of frames without changing any result."""
+    frames = [synth.lidar_frame(s) for s in range(6)]
+    n_max = max(f.shape[0] for f in frames)
+    pool = 2 * ((12 * n_max + 47) // 48 * 48)
+    srv = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=64 << 20, host_pool_bytes=pool)
+    try:
+        assert srv.submit(frames[0], 0) == 0
+        assert srv.submit(frames[1], 1) == 0
+        assert srv.submit(frames[2], 2) == B.AFPS_ERR_BUSY  # pool holds two frames
+        done = {}
+        t = 2
+        for _ in range(10_000):
+            if t < len(frames) and srv.submit(frames[t], t) == 0:
+                t += 1
+            srv.step()
+            for r in srv.poll():
+                done[r.tag] = r
+            if len(done) == len(frames):
+                break
+    finally:
+        srv.close()
+    assert sorted(done) == list(range(len(frames)))
+    for t in (0, 3, 5):
+        ref = oracle.chain(frames[t], LEVELS, 32, 16)
+        for l in range(len(LEVELS)):
+            assert np.array_equal(done[t].levels[l], ref[l]), (t, l)
