@@ -77,6 +77,11 @@ struct ClassPlan {
     Variant v{};
     size_t first = 0;  // first item in the concatenated table
     size_t count = 0;
+    // every cloud of the class has the same N, C, M, window and start, and
+    // they are stored back to back: the kernel computes its items
+    bool uniform = false;
+    afps::SingleCloud single{};
+    const afps::SingleCloud* run() const { return uniform ? &single : nullptr; }
 };
 
 struct BatchPlan {
@@ -347,10 +352,12 @@ int grid_for(const Variant& v, size_t count) {
 
 int launch_class(afps_ctx* ctx, const Variant& v, bool npdu, const ItemDesc* d_items,
                  size_t count, unsigned int* d_counter, const float* xyz, int32_t* out,
-                 cudaStream_t stream, bool host_resident = false) {
+                 cudaStream_t stream, bool host_resident = false,
+                 const afps::SingleCloud* run = nullptr) {
     LaunchArgs a{};
     a.xyz = xyz;
-    a.items = d_items;
+    a.items = run ? nullptr : d_items;
+    if (run) a.single = *run;
     a.n_items = (int32_t)count;
     a.out = out;
     // The dynamic queue is needed only when the grid is capped below one
@@ -447,6 +454,37 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
             }
         }
         cp.count = plan.items.size() - cp.first;
+        // a run of equal clouds stored back to back: items computed on the device
+        {
+            const Member& m0 = g.second.front();
+            const int32_t b0 = m0.b;
+            const uint32_t meth0 = method ? method[b0] : 0u;
+            bool same = true;
+            for (size_t j = 0; j < g.second.size() && same; ++j) {
+                const Member& m = g.second[j];
+                const int32_t b = m.b;
+                same = n_pts[b] == n_pts[b0] && C[b] == C[b0] && M[b] == M[b0] &&
+                       K[b] == K[b0] && (method ? method[b] : 0u) == meth0 &&
+                       m.chk.start_r == m0.chk.start_r &&
+                       pt_begin[b] == pt_begin[b0] + (int64_t)j * n_pts[b0] &&
+                       out_begin[b] == out_begin[b0] + (int64_t)j * C[b0];
+            }
+            if (same && n_pts[b0] <= INT32_MAX) {
+                ItemDesc w{};
+                window_sides(K[b0], meth0, w);
+                cp.uniform = true;
+                cp.single.pt_off = pt_begin[b0];
+                cp.single.out_off = out_begin[b0];
+                cp.single.N = (int32_t)n_pts[b0];
+                cp.single.C = C[b0];
+                cp.single.M = M[b0];
+                cp.single.kl = w.kl;
+                cp.single.kr = w.kr;
+                cp.single.flags = w.flags;
+                cp.single.start_r = m0.chk.start_r;
+                cp.single.wide = (int64_t)M[b0] * n_pts[b0] > (int64_t)UINT32_MAX ? 1 : 0;
+            }
+        }
         // largest work first (longest-processing-time order for the queue)
         auto cost = [&](const ItemDesc& d) {
             return cp.npdu ? (int64_t)d.c * (d.kl + d.kr + 1 + d.n / 32) : (int64_t)d.c * d.n;
@@ -500,14 +538,18 @@ int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* 
              cudaStream_t stream) {
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);
     AFPS_CUDA(ctx, ctx->counters.reserve(plan.classes.size() * sizeof(unsigned int)));
-    int urc = upload(ctx, ctx->items, plan.items.data(), bytes, stream);
-    if (urc != AFPS_OK) return urc;
+    bool table = false;  // some class reads the item table
+    for (const ClassPlan& cp : plan.classes) table = table || !cp.uniform;
+    if (table) {
+        int urc = upload(ctx, ctx->items, plan.items.data(), bytes, stream);
+        if (urc != AFPS_OK) return urc;
+    }
     const ItemDesc* d_items = static_cast<const ItemDesc*>(ctx->items.p);
     unsigned int* counters = static_cast<unsigned int*>(ctx->counters.p);
     for (size_t i = 0; i < plan.classes.size(); ++i) {
         const ClassPlan& cp = plan.classes[i];
-        int rc = launch_class(ctx, cp.v, cp.npdu, d_items + cp.first, cp.count, counters + i,
-                              d_xyz, d_out, stream);
+        int rc = launch_class(ctx, cp.v, cp.npdu, cp.uniform ? nullptr : d_items + cp.first,
+                              cp.count, counters + i, d_xyz, d_out, stream, false, cp.run());
         if (rc != AFPS_OK) return rc;
     }
     AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, stream));
@@ -570,7 +612,7 @@ int make_graph(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t
     for (size_t i = 0; i < plan.classes.size() && rc == AFPS_OK; ++i) {
         const ClassPlan& cp = plan.classes[i];
         rc = launch_class(ctx, cp.v, cp.npdu, d_items + cp.first, cp.count, counters + i, d_xyz,
-                          d_out, ctx->capture, host_resident);
+                          d_out, ctx->capture, host_resident, cp.run());
     }
     if (rc == AFPS_OK && h_out &&
         cudaMemcpyAsync(h_out, d_out, out_bytes, cudaMemcpyDeviceToHost, ctx->capture) !=
@@ -872,6 +914,7 @@ int afps_sample_ex(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int3
         a.single.flags = w.flags;
     }
     a.single.start_r = chk.start_r;
+    a.single.wide = (int64_t)M * N > (int64_t)UINT32_MAX ? 1 : 0;
     a.n_items = M;
     a.out = d_out;
     a.counter = nullptr;
@@ -1130,8 +1173,10 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
             bool ok = true;
             for (int rep = 0; rep < 4 && ok; ++rep) {  // one warm-up, three timed
                 if (cudaEventRecord(e0, st) != cudaSuccess) ok = false;
-                if (ok && launch_class(ctx, v, cp.npdu, d_items + cp.first, cp.count,
-                                       counters + i, d_xyz, d_out, st) != AFPS_OK)
+                if (ok && launch_class(ctx, v, cp.npdu,
+                                       cp.uniform ? nullptr : d_items + cp.first, cp.count,
+                                       counters + i, d_xyz, d_out, st, false,
+                                       cp.run()) != AFPS_OK)
                     ok = false;
                 if (ok && cudaEventRecord(e1, st) != cudaSuccess) ok = false;
                 float ms = 0.f;

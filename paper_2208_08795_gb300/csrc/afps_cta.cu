@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             // the start.
             const int q = kr + 1;
             const int x = n - 1 - kr - p;
-            const int ts = x <= 0 ? 1 : (x + q - 1) / q + 1;  // samples of the stride
+            const int ts = x <= 0 ? 1 : (int)((unsigned)(x + q - 1) / (unsigned)q) + 1;  // stride length
             const int tn = min(ts, c);                        // of them emitted
             const int tw = min(ts, c - 1);                    // whose window is applied
             bool ok = true;  // D is updated in place and reset if the test fails
@@ -169,8 +169,9 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
                 if (i < P && j < n) {
                     const float px = pts[3 * j], py = pts[3 * j + 1], pz = pts[3 * j + 2];
                     const int y = j - kr - p;
-                    const int tlo = y <= 0 ? 0 : (y + q - 1) / q;
-                    const int thi = min(tw - 1, (j + kl - p) / q);
+                    // unsigned divisions: both operands are >= 0 (p <= kl)
+                    const int tlo = y <= 0 ? 0 : (int)((unsigned)(y + q - 1) / (unsigned)q);
+                    const int thi = min(tw - 1, (int)((unsigned)(j + kl - p) / (unsigned)q));
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         if (tlo + u <= thi) {

@@ -181,18 +181,31 @@ __device__ __forceinline__ void sqdist2(unsigned long long x, unsigned long long
     d1 = __fadd_rn(__fadd_rn(x1, y1), z1);
 }
 
-// Item `i` of a launch: from the device table, or computed from the single
-// cloud's parameters with the sector rule floor(s*N/M), floor(s*C/M).
+// Item `i` of a launch: from the device table, or computed from the
+// parameters of a run of equal clouds stored back to back (cloud i / M,
+// sector i % M) with the sector rule floor(s*N/M), floor(s*C/M).  Computing
+// it saves the dependent load of a table entry ahead of the stage-in.
 __device__ __forceinline__ ItemDesc load_item(const LaunchArgs& a, int i) {
     if (a.items) return a.items[i];
     const SingleCloud& s = a.single;
-    const int64_t lo = (int64_t)i * s.N / s.M;
-    const int64_t hi = (int64_t)(i + 1) * s.N / s.M;
-    const int64_t o0 = (int64_t)i * s.C / s.M;
-    const int64_t o1 = (int64_t)(i + 1) * s.C / s.M;
+    const uint32_t M = (uint32_t)s.M;
+    const uint32_t b = (uint32_t)i / M;
+    const uint32_t sec = (uint32_t)i - b * M;
+    int64_t lo, hi, o0, o1;
+    if (s.wide) {  // M * N does not fit in 32 bits
+        lo = (int64_t)sec * s.N / s.M;
+        hi = (int64_t)(sec + 1) * s.N / s.M;
+        o0 = (int64_t)sec * s.C / s.M;
+        o1 = (int64_t)(sec + 1) * s.C / s.M;
+    } else {  // 32-bit unsigned divisions: a few instructions instead of a call
+        lo = sec * (uint32_t)s.N / M;
+        hi = (sec + 1) * (uint32_t)s.N / M;
+        o0 = sec * (uint32_t)s.C / M;
+        o1 = (sec + 1) * (uint32_t)s.C / M;
+    }
     ItemDesc d;
-    d.src = s.pt_off + lo;
-    d.dst = s.out_off + o0;
+    d.src = s.pt_off + (int64_t)b * s.N + lo;
+    d.dst = s.out_off + (int64_t)b * s.C + o0;
     d.n = (int32_t)(hi - lo);
     d.c = (int32_t)(o1 - o0);
     d.first = s.start_r < d.n - 1 ? s.start_r : d.n - 1;

@@ -27,13 +27,16 @@ static_assert(sizeof(ItemDesc) == 48, "ItemDesc layout");
 enum : int32_t { ITEM_FULL_FIRST = 1 };  // the first update reaches the whole sector
 
 // A single cloud described by its parameters; items are its M sectors.
+// A run of equal clouds (N points, C samples, M sectors each) stored back to
+// back from point pt_off, their outputs back to back from out_off; a launch
+// over it has (number of clouds) x M items.
 struct SingleCloud {
     int64_t pt_off;
     int64_t out_off;
     int32_t N, C, M;
     int32_t kl, kr, flags;  // as in ItemDesc
     int32_t start_r;        // offset of start_idx inside its own sector
-    int32_t pad;
+    int32_t wide;           // M * N >= 2^32: sector bounds in 64-bit arithmetic
 };
 
 enum Kind : int32_t { KIND_WARP = 0, KIND_CTA = 1 };

@@ -271,6 +271,64 @@ def test_npdu_stride_phase(tmp_path, kern):
                 s.close()
 
 
+# --------------------------------------------------------------- runs of equal clouds
+# A class whose clouds share N, C, M, window, reading and start and sit back
+# to back (points and outputs) has its items computed in the kernel instead
+# of read from a table; anything else takes the table.  Both must agree with
+# the oracle, and output slots outside [out_off[b], out_off[b] + C) stay
+# untouched.
+def _batched(S, clouds, C, M, k, start, out_off=None, method=None):
+    xyz, off = synth.pack(clouds)
+    ba = B.BatchArgs(off, C, M, k, start, out_off=out_off, method=method)
+    out = torch.full((ba.total_out,), -1, dtype=torch.int32, device="cuda")
+    S.sample_batched(torch.from_numpy(xyz).cuda(), ba, out=out)
+    S.sync()
+    return out.cpu().numpy(), ba
+
+
+@pytest.mark.parametrize("method", [0, 2])
+def test_equal_cloud_run(S, method):
+    clouds = [synth.uniform_cloud(300 + i, 1500) for i in range(40)]
+    o, ba = _batched(S, clouds, 300, 12, 16, 5, method=method)
+    for b, P in enumerate(clouds):
+        assert_same(o[ba.out_off[b]:ba.out_off[b + 1]],
+                    oracle.afps(P, 300, 12, 16, 5, method=method), f"cloud {b}")
+
+
+def test_equal_clouds_with_output_gaps(S):
+    clouds = [synth.uniform_cloud(400 + i, 1000) for i in range(9)]
+    out_off = np.arange(10, dtype=np.int64) * (200 + 7)
+    o, ba = _batched(S, clouds, 200, 4, 8, 0, out_off=out_off)
+    for b, P in enumerate(clouds):
+        assert_same(o[out_off[b]:out_off[b] + 200], oracle.afps(P, 200, 4, 8, 0), f"cloud {b}")
+        assert np.all(o[out_off[b] + 200:out_off[b + 1]] == -1)
+
+
+def test_equal_run_broken_inside_a_class(S):
+    """Same sector sizes (one class) but one cloud with another C, another
+    start, and one of another size class: no run, every cloud still exact."""
+    clouds = [synth.uniform_cloud(500 + i, 2048) for i in range(8)] + [synth.uniform_cloud(9, 4000)]
+    Cs = [512] * 8 + [800]
+    Cs[3] = 480
+    starts = [0] * 9
+    starts[5] = 3
+    o, ba = _batched(S, clouds, Cs, [32] * 8 + [8], 16, starts)
+    for b, P in enumerate(clouds):
+        M = 32 if b < 8 else 8
+        assert_same(o[ba.out_off[b]:ba.out_off[b + 1]], oracle.afps(P, Cs[b], M, 16, starts[b]),
+                    f"cloud {b}")
+
+
+def test_equal_run_persistent_queue(S):
+    """1200 clouds x 32 sectors: more items than resident warps, so the
+    dynamic queue hands out computed items."""
+    clouds = synth.object_batch(3, 1200, 2048)
+    o, ba = _batched(S, clouds, 512, 32, 16, 0)
+    for b in range(0, 1200, 7):
+        assert_same(o[ba.out_off[b]:ba.out_off[b + 1]], oracle.afps(clouds[b], 512, 32, 16, 0),
+                    f"cloud {b}")
+
+
 # --------------------------------------------------------------- NPDU readings
 READINGS = [(2048, 512, 32, 16), (2048, 512, 4, 8), (16384, 4096, 1, 8), (5000, 1000, 6, 9),
             (1000, 250, 3, 1), (40000, 2000, 1, 5)]
