@@ -1,8 +1,13 @@
 """Single sampling workloads, run a few times, for profiling with ncu.
 
-    python -m paper_2208_08795_gb300.profile_cases <case> [--reps R]
+    python -m paper_2208_08795_gb300.profile_cases <case> [--reps R] [--tune-cache PATH]
 
-Cases (inputs from `synth`, kernel variants from the default planner):
+With --tune-cache, a batched case whose cache file does not exist yet is
+autotuned (as bench.py does) and the choice saved; a later run with the same
+file replays the tuned variant without autotuning, so a profiler can capture
+the exact kernel the benchmark times.
+
+Cases (inputs from `synth`; kernel variants from the planner or the cache):
   headline     32 object clouds x 2048 points, C = 512, NPDU-AFPS M = 32, k = 16 (batched)
   fps2048      the same batch, plain FPS (M = 1)
   cluster32k   one 32768-point slab cloud, C = 8192, plain FPS (one thread-block cluster)
@@ -26,9 +31,11 @@ CASES = ("headline", "fps2048", "cluster32k", "npdu32k", "ragged", "chain", "sor
          "coverage")
 
 
-def run(case: str, reps: int) -> None:
+def run(case: str, reps: int, tune_cache: str | None = None) -> None:
+    import os
     build.build()
-    s = afps.Sampler(0)
+    tune = bool(tune_cache) and not os.path.exists(tune_cache)
+    s = afps.Sampler(0, tune_cache=tune_cache)
     dev = torch.device("cuda", 0)
     if case in ("headline", "fps2048", "ragged"):
         if case == "ragged":
@@ -41,8 +48,14 @@ def run(case: str, reps: int) -> None:
         x = torch.from_numpy(xyz).to(dev)
         ba = afps.BatchArgs(off, C, M, k, 0)
         out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
+        if tune:
+            s.autotune_batched(x, ba, out)
+            s.sync()
+            afps.afps_save_tuning(s.ctx, None)
         for _ in range(reps):
             s.sample_batched(x, ba, out=out)
+        if case != "ragged":
+            print("variant:", s.describe_plan(-(-2048 // M), -(-C // M), k, 32 * M))
     elif case in ("cluster32k", "npdu32k"):
         x = torch.from_numpy(synth.slab_cloud(2, 32768)).to(dev)
         M, k = (1, 0) if case == "cluster32k" else (32, 16)
@@ -88,8 +101,9 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("case", choices=CASES)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--tune-cache", default=None)
     a = ap.parse_args(argv)
-    run(a.case, a.reps)
+    run(a.case, a.reps, a.tune_cache)
     return 0
 
 
