@@ -227,6 +227,27 @@ def sort_by_key(xyz, key: int):
     return pts[perm], perm
 
 
+def knn(xyz, centroids, K: int, *, library=None, with_d2: bool = False):
+    """The K nearest points of each centroid, nearest first, ties to the lower
+    index: (C, K) int32 (and the (C, K) float32 squared distances)."""
+    L = library or lib()
+    if not hasattr(L, "_knn"):
+        L.oracle_knn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                 ctypes.c_void_p]
+        L.oracle_knn.restype = ctypes.c_int
+        L._knn = True
+    pts = _points(xyz)
+    c = np.ascontiguousarray(centroids, dtype=np.int32)
+    out = np.full((c.size, int(K)), -1, dtype=np.int32)
+    d2 = np.zeros((c.size, int(K)), dtype=np.float32)
+    rc = L.oracle_knn(pts.ctypes.data, pts.shape[0], c.ctypes.data, c.size, int(K),
+                      out.ctypes.data, d2.ctypes.data)
+    if rc != OK:
+        raise OracleError(rc)
+    return (out, d2) if with_d2 else out
+
+
 def ball_query(xyz, centroids, radius: float, K: int, *, library=None) -> np.ndarray:
     """First K points (storage order) within `radius` of each centroid,
     padded with the first one found: (C, K) int32."""

@@ -330,3 +330,58 @@ int oracle_ball_query(const float* xyz, int64_t N, const int32_t* centroids, int
     }
     return ORACLE_OK;
 }
+
+/*
+ * k nearest neighbours (the other grouping step used after sampling in
+ * point-cloud networks, Sec. I-II; the paper does not define it, this is the
+ * plain reading): for each of the C centroids, the K points with the
+ * smallest squared distance (dx*dx + dy*dy) + dz*dz in fp32, ties to the
+ * lower index, listed nearest first.  Every point's key (distance, index)
+ * is formed and the keys are sorted; the first K are kept.  out: C x K
+ * int32; d2 (optional): the matching squared distances.  Needs 1 <= K <= N.
+ * Returns ORACLE_OK, ORACLE_ERR_INVALID_ARG or ORACLE_ERR_NO_MEMORY.
+ */
+typedef struct {
+    float d;
+    int64_t j;
+} oracle_knn_key;
+
+static int oracle_knn_cmp(const void* a, const void* b)
+{
+    const oracle_knn_key* x = (const oracle_knn_key*)a;
+    const oracle_knn_key* y = (const oracle_knn_key*)b;
+    if (x->d < y->d) return -1;
+    if (x->d > y->d) return 1;
+    return (x->j > y->j) - (x->j < y->j);
+}
+
+int oracle_knn(const float* xyz, int64_t N, const int32_t* centroids, int32_t C, int32_t K,
+               int32_t* out, float* d2)
+{
+    if (!xyz || !centroids || !out || N < 1 || C < 0 || K < 1 || K > N)
+        return ORACLE_ERR_INVALID_ARG;
+    oracle_knn_key* keys = (oracle_knn_key*)malloc((size_t)N * sizeof(oracle_knn_key));
+    if (!keys) return ORACLE_ERR_NO_MEMORY;
+    for (int32_t s = 0; s < C; ++s) {
+        const int64_t q = centroids[s];
+        if (q < 0 || q >= N) {
+            free(keys);
+            return ORACLE_ERR_INVALID_ARG;
+        }
+        const float cx = xyz[3 * q + 0], cy = xyz[3 * q + 1], cz = xyz[3 * q + 2];
+        for (int64_t j = 0; j < N; ++j) {
+            float ex = xyz[3 * j + 0] - cx;
+            float ey = xyz[3 * j + 1] - cy;
+            float ez = xyz[3 * j + 2] - cz;
+            keys[j].d = (ex * ex + ey * ey) + ez * ez;
+            keys[j].j = j;
+        }
+        qsort(keys, (size_t)N, sizeof(oracle_knn_key), oracle_knn_cmp);
+        for (int32_t i = 0; i < K; ++i) {
+            out[(int64_t)s * K + i] = (int32_t)keys[i].j;
+            if (d2) d2[(int64_t)s * K + i] = keys[i].d;
+        }
+    }
+    free(keys);
+    return ORACLE_OK;
+}

@@ -357,6 +357,65 @@ def pin_ball_query(L):
             assert list(row) == want, (seed, c)
 
 
+def knn_grid_closed_form(n, i, K):
+    """Nearest-first order on the integer grid 0..n-1 from point i: i, then
+    i-1, i+1, i-2, i+2, ... (the lower index first at equal distance),
+    skipping points off the grid."""
+    order = [i]
+    for r in range(1, n):
+        order += [j for j in (i - r, i + r) if 0 <= j < n]
+    return order[:K]
+
+
+def knn_brute_force(P, c, K):
+    """Pure-Python loops with float32 scalars: the key (distance, index) of
+    every point, sorted, the first K."""
+    f = np.float32
+    cx, cy, cz = (f(v) for v in P[c])
+    keys = []
+    for j in range(P.shape[0]):
+        ex, ey, ez = f(P[j, 0]) - cx, f(P[j, 1]) - cy, f(P[j, 2]) - cz
+        keys.append((f(f(ex * ex) + f(ey * ey)) + f(ez * ez), j))
+    return [j for _, j in sorted(keys)[:K]]
+
+
+def pin_knn(L):
+    """k nearest neighbours: the closed form on an integer grid (ties to the
+    lower index), brute force on small clouds, invariants (K = N is a
+    permutation sorted by distance, the returned distances recompute), exact
+    metamorphic scaling, and the argument checks."""
+    P = np.zeros((40, 3), dtype=np.float32)
+    P[:, 0] = np.arange(40)
+    cen = np.array([0, 1, 17, 38, 39])
+    for K in (1, 2, 5, 9, 40):
+        got = oracle.knn(P, cen, K, library=L)
+        for row, i in zip(got, cen):
+            assert list(row) == knn_grid_closed_form(40, int(i), K), (K, i, list(row))
+    for seed, (N, C, K) in enumerate([(60, 7, 5), (33, 33, 33), (90, 5, 17)]):
+        Q = synth.uniform_cloud(900 + seed, N, None)
+        if seed == 1:
+            Q[5] = Q[20]  # a duplicate point: equal keys resolve by index
+        cen = np.arange(0, N, max(1, N // C))[:C]
+        got, d2 = oracle.knn(Q, cen, K, library=L, with_d2=True)
+        for row, c in zip(got, cen):
+            assert list(row) == knn_brute_force(Q, int(c), K), (seed, c)
+        for row, dd, c in zip(got, d2, cen):
+            e = Q[row] - Q[c]
+            assert np.array_equal(dd, (e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1]) + e[:, 2] * e[:, 2])
+            key = list(zip(dd.tolist(), row.tolist()))
+            assert key == sorted(key)
+        if K == N:
+            assert all(sorted(r) == list(range(N)) for r in got)
+        assert np.array_equal(oracle.knn(Q * np.float32(8.0), cen, K, library=L), got)
+    for bad in ((P, [0], 0), (P, [0], 41), (P, [40], 3), (P, [-1], 3)):
+        try:
+            oracle.knn(*bad, library=L)
+        except oracle.OracleError:
+            continue
+        raise AssertionError(f"accepted {bad[1:]}")
+
+
 PINS = [pin_golden, pin_grid_closed_form, pin_npdu_stride_law, pin_brute_force,
         pin_brute_force_f64, pin_reductions, pin_invariants, pin_every_point, pin_metamorphic,
-        pin_errors, pin_coverage_radius, pin_chain_grid, pin_npdu_readings, pin_ball_query]
+        pin_errors, pin_coverage_radius, pin_chain_grid, pin_npdu_readings, pin_ball_query,
+        pin_knn]

@@ -42,6 +42,11 @@ MUTANTS = [
     ("ball_pad_last", "const int32_t fill = cnt > 0 ? out[(int64_t)s * K] : -1;",
      "const int32_t fill = cnt > 0 ? out[(int64_t)s * K + cnt - 1] : -1;", 0),
     ("ball_drop_dz", "float d2 = (dx * dx + dy * dy) + dz * dz;", "float d2 = (dx * dx + dy * dy);", 0),
+    ("knn_tie_high", "return (x->j > y->j) - (x->j < y->j);", "return (x->j < y->j) - (x->j > y->j);", 0),
+    ("knn_drop_dz", "keys[j].d = (ex * ex + ey * ey) + ez * ez;", "keys[j].d = (ex * ex + ey * ey);", 0),
+    ("knn_sign_ey", "float ey = xyz[3 * j + 1] - cy;", "float ey = xyz[3 * j + 1] + cy;", 0),
+    ("knn_farthest", "if (x->d < y->d) return -1;\n    if (x->d > y->d) return 1;",
+     "if (x->d < y->d) return 1;\n    if (x->d > y->d) return -1;", 0),
 ]
 
 
