@@ -370,8 +370,27 @@ def group_section(sampler, x, off, flush, dev, steps: int):
         torch.cuda.synchronize()
         ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
         rows[name] = {"ms": round(ms, 4), "clouds_per_s": round(B_CLOUDS / (ms / 1e3), 1)}
-    return {"workload": "ball query r=0.2 K=32 around the 512 NPDU-AFPS samples of each of "
-                        "32 x 2048-point clouds", **rows}
+    out = {"workload": "ball query r=0.2 K=32 around the 512 NPDU-AFPS samples of each of "
+                       "32 x 2048-point clouds", **rows}
+    # k nearest neighbours (K = 32) around the same centroids
+    nn = torch.empty((ba.total_out, 32), dtype=torch.int32, device=dev)
+    krows = {}
+    for name, axis in (("full_scan", -1), ("sorted_outward_scan", 0)):
+        for _ in range(3):
+            sampler.knn(x, off, sel, ba.out_off, 32, axis, nn)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            sampler.knn(x, off, sel, ba.out_off, 32, axis, nn)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        krows[name] = {"ms": round(ms, 4), "clouds_per_s": round(B_CLOUDS / (ms / 1e3), 1)}
+    out["knn"] = {"workload": "32 nearest neighbours of the same centroids", **krows}
+    return out
 
 
 # ------------------------------------------------------------------ serving

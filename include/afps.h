@@ -242,6 +242,25 @@ int afps_ball_query(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const flo
                     int32_t sorted_axis, int32_t* d_group, void* stream);
 
 /*
+ * k nearest neighbours, the other grouping step used after sampling in
+ * point-cloud networks (Sec. I-II; the paper does not define it, this is the
+ * plain reading).  For each centroid d_sel[i] (cloud-relative, i in
+ * [h_sel_off[b], h_sel_off[b+1]) for cloud b, clamped into the cloud):
+ * d_group[i*K .. i*K+K) = the K points of the cloud with the smallest fp32
+ * squared distance (dx*dx + dy*dy) + dz*dz (dx = point - centroid, every
+ * operation rounded on its own), ties to the lower index, nearest first,
+ * as cloud-relative indices; d_dist2 (may be NULL) receives the matching
+ * squared distances.  sorted_axis = 0, 1, 2 promises the cloud is sorted
+ * ascending along x, y or z, which lets the scan stop early on each side
+ * (same result as a full scan); -1 scans every point.  Needs 1 <= K <= 64,
+ * K <= every cloud's point count and 1 <= B <= 65535; device buffers are the
+ * caller's; AFPS_ERR_INVALID_ARG otherwise (nothing launched).
+ */
+int afps_knn(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
+             const int64_t* h_sel_off, const int32_t* d_sel, int32_t K, int32_t sorted_axis,
+             int32_t* d_group, float* d_dist2, void* stream);
+
+/*
  * Wait for the stream and report device-side errors recorded since the last
  * call (AFPS_ERR_TIMEOUT when a bounded wait gave up); clears them.
  */

@@ -40,7 +40,7 @@ EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
            "afps_server_create", "afps_server_submit", "afps_server_step", "afps_server_poll",
            "afps_server_stats", "afps_server_clock_ms", "afps_server_destroy",
            "afps_sort_by_key", "afps_sample_ex", "afps_sample_batched_ex",
-           "afps_coverage_radius", "afps_ball_query")
+           "afps_coverage_radius", "afps_ball_query", "afps_knn")
 
 
 class AfpsLibraryError(RuntimeError):
@@ -119,6 +119,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.afps_coverage_radius.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
     L.afps_ball_query.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.c_float, i32, i32, vp, vp]
     L.afps_ball_query.restype = ctypes.c_int
+    L.afps_knn.argtypes = [vp, i32, vp, vp, vp, vp, i32, i32, vp, vp, vp]
+    L.afps_knn.restype = ctypes.c_int
     L.afps_coverage_radius.restype = ctypes.c_int
     L.afps_sort_by_key.restype = ctypes.c_int
     L.afps_server_create.argtypes = [ctypes.POINTER(vp), vp, ctypes.POINTER(afps_server_config), vp]
@@ -247,6 +249,12 @@ def afps_ball_query(ctx, B, h_pt_off, d_xyz, h_sel_off, d_sel, radius, K, sorted
                     stream) -> int:
     return load().afps_ball_query(ctx, B, h_pt_off, d_xyz, h_sel_off, d_sel, radius, K,
                                   sorted_axis, d_group, stream)
+
+
+def afps_knn(ctx, B, h_pt_off, d_xyz, h_sel_off, d_sel, K, sorted_axis, d_group, d_dist2,
+             stream) -> int:
+    return load().afps_knn(ctx, B, h_pt_off, d_xyz, h_sel_off, d_sel, K, sorted_axis, d_group,
+                           d_dist2, stream)
 
 
 def afps_sample_batched_noalloc(d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
@@ -433,6 +441,22 @@ class Sampler:
         self._check(afps_ball_query(self.ctx, po.size - 1, _ptr(po), xyz.data_ptr(), _ptr(so),
                                     sel.data_ptr(), radius, K, sorted_axis, out.data_ptr(),
                                     self._stream(stream)))
+        return out
+
+    def knn(self, xyz, pt_off, sel, sel_off, K: int, sorted_axis: int = -1, out=None,
+            dist2=None, stream=None):
+        """The K nearest points of every centroid, nearest first: (sum C, K)
+        int32; ``dist2`` (optional, (sum C, K) float32) gets the squared
+        distances."""
+        import torch
+        xyz = self._points(xyz)
+        po, so = _i64(pt_off), _i64(sel_off)
+        if out is None:
+            out = torch.empty((int(so[-1]), K), dtype=torch.int32, device=xyz.device)
+        self._check(afps_knn(self.ctx, po.size - 1, _ptr(po), xyz.data_ptr(), _ptr(so),
+                             sel.data_ptr(), K, sorted_axis, out.data_ptr(),
+                             dist2.data_ptr() if dist2 is not None else None,
+                             self._stream(stream)))
         return out
 
     def sync(self, stream=None):

@@ -15,7 +15,8 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIBRARY = os.path.join(PKG, "libafps.so")
 HEADER = os.path.join(ROOT, "include", "afps.h")
 SOURCES = ["afps_warp.cu", "afps_cta.cu", "afps_gather.cu", "afps_api.cu", "afps_noalloc.cu",
-           "afps_server.cu", "afps_sort.cu", "afps_coverage.cu", "afps_group.cu"]
+           "afps_server.cu", "afps_sort.cu", "afps_coverage.cu", "afps_group.cu",
+           "afps_knn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-Wall", "-I", os.path.join(ROOT, "include")]

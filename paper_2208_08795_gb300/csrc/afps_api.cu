@@ -1121,6 +1121,41 @@ int afps_ball_query(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const flo
     return AFPS_OK;
 }
 
+int afps_knn(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
+             const int64_t* h_sel_off, const int32_t* d_sel, int32_t K, int32_t sorted_axis,
+             int32_t* d_group, float* d_dist2, void* stream) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    if (B < 1 || B > 65535 || !h_pt_off || !h_sel_off || !d_xyz || !d_sel || !d_group || K < 1 ||
+        K > 64 || sorted_axis < -1 || sorted_axis > 2)
+        return fail(ctx, AFPS_ERR_INVALID_ARG,
+                    "afps_knn: bad argument (1 <= B <= 65535, 1 <= K <= 64, sorted_axis in -1..2)");
+    std::vector<afps::GroupDesc> descs((size_t)B);
+    int32_t max_c = 0;
+    for (int32_t b = 0; b < B; ++b) {
+        const int64_t n = h_pt_off[b + 1] - h_pt_off[b];
+        const int64_t c = h_sel_off[b + 1] - h_sel_off[b];
+        if (n < K || n > INT32_MAX || c < 0 || c > INT32_MAX || h_pt_off[b] < 0 ||
+            h_sel_off[b] < 0) {
+            std::ostringstream os;
+            os << "afps_knn: cloud " << b << " has " << n << " points (K = " << K << ") and "
+               << c << " centroids";
+            return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
+        }
+        descs[b] = afps::GroupDesc{h_pt_off[b], h_sel_off[b], (int32_t)n, (int32_t)c};
+        max_c = std::max<int32_t>(max_c, (int32_t)c);
+    }
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = upload(ctx, ctx->items, descs.data(), descs.size() * sizeof(afps::GroupDesc), st);
+    if (rc != AFPS_OK) return rc;
+    cudaError_t e = afps::launch_knn(static_cast<const afps::GroupDesc*>(ctx->items.p), B, max_c,
+                                     d_xyz, d_sel, K, sorted_axis, d_group, d_dist2, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "knn launch");
+    if (max_c > 0) ctx->launches += 1;
+    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, st));
+    return AFPS_OK;
+}
+
 int afps_sync(afps_ctx* ctx, void* stream) {
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     DeviceGuard guard(ctx->device);

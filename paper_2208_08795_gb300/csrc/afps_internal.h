@@ -136,6 +136,10 @@ struct GroupDesc {
 cudaError_t launch_ball_query(const GroupDesc* d_descs, int32_t B, int32_t max_c,
                               const float* xyz, const int32_t* sel, float radius, int32_t K,
                               int32_t axis, int32_t* out, cudaStream_t stream);
+// k nearest neighbours (afps_knn): one warp per centroid, 1 <= K <= 64.
+cudaError_t launch_knn(const GroupDesc* d_descs, int32_t B, int32_t max_c, const float* xyz,
+                       const int32_t* sel, int32_t K, int32_t axis, int32_t* out, float* dist2,
+                       cudaStream_t stream);
 
 // Sort by key (afps_sort_by_key): one cloud per CTA.
 struct SortDesc {

@@ -16,6 +16,7 @@ Cases (inputs from `synth`; kernel variants from the planner or the cache):
   chain        one LiDAR-like frame, levels 16384 -> 4096 -> 1024 -> 256, M = 32, k = 16
   sort         the object batch in random storage order, sorted by x
   group        ball query (r = 0.2, K = 32) around the headline samples of the batch
+  knn          32 nearest neighbours of the same centroids (outward scan of the x-sorted clouds)
   coverage     coverage radius of the headline samples of the batch
 """
 from __future__ import annotations
@@ -28,7 +29,7 @@ import torch
 from . import afps, build, synth
 
 CASES = ("headline", "fps2048", "cluster32k", "npdu32k", "ragged", "chain", "sort", "group",
-         "coverage")
+         "knn", "coverage")
 
 
 def run(case: str, reps: int, tune_cache: str | None = None) -> None:
@@ -61,7 +62,7 @@ def run(case: str, reps: int, tune_cache: str | None = None) -> None:
         M, k = (1, 0) if case == "cluster32k" else (32, 16)
         for _ in range(reps):
             s.sample(x, 8192, M, k, 0)
-    elif case in ("sort", "group", "coverage"):
+    elif case in ("sort", "group", "knn", "coverage"):
         clouds = synth.object_batch(1, 32, 2048)
         if case == "sort":
             g = synth.rng(11)
@@ -77,6 +78,8 @@ def run(case: str, reps: int, tune_cache: str | None = None) -> None:
             for _ in range(reps):
                 if case == "group":
                     s.ball_query(x, off, sel, ba.out_off, 0.2, 32, 0)
+                elif case == "knn":
+                    s.knn(x, off, sel, ba.out_off, 32, 0)
                 else:
                     s.coverage_radius(x, off, sel, ba.out_off)
     elif case == "chain":
