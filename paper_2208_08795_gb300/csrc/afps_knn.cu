@@ -6,14 +6,15 @@
 // dx = point - centroid and every operation rounded on its own; ties go to
 // the lower index; nearest first.
 //
-// One warp per centroid keeps the K best keys sorted across its lanes:
-// element l of the list lives in lane l % 32 of slot l / 32 (S slots,
-// K <= 32 S).  Each 32-point chunk ballots the points whose key is below the
-// current K-th key, and they enter one at a time: the rank is the number of
-// list keys below the new key (one ballot per slot) and the elements from
-// the rank on move up by one (shuffles).  Keys are unique (the index is part
-// of them), so the list equals the first K of the fully sorted keys whatever
-// the scan order.
+// One warp per centroid keeps the smallest keys seen so far sorted across
+// its lanes: element l of the list lives in lane l % 32 of slot l / 32
+// (S slots, K <= 32 S).  Each 32-point chunk ballots the points whose key is
+// below the current K-th key, and they enter one at a time: the rank is the
+// number of list keys below the new key (one ballot per slot) and the
+// elements from the rank on move up by one (shuffles).  With one slot and
+// many candidates the chunk is bitonic-sorted and merged instead.  Keys are
+// unique (the index is part of them), so the first K elements equal the
+// first K of the fully sorted keys whatever the scan order.
 //
 // On a cloud sorted ascending along `axis` (dimensional locality, Sec.
 // III-A) the scan starts at the centroid's chunk and grows outward, nearer
@@ -39,6 +40,35 @@ __device__ __forceinline__ unsigned long long shfl64_up(unsigned long long v) {
     const unsigned lo = __shfl_up_sync(dev::kFull, (unsigned)v, 1);
     const unsigned hi = __shfl_up_sync(dev::kFull, (unsigned)(v >> 32), 1);
     return ((unsigned long long)hi << 32) | lo;
+}
+
+__device__ __forceinline__ unsigned long long shfl64_xor(unsigned long long v, int m) {
+    const unsigned lo = __shfl_xor_sync(dev::kFull, (unsigned)v, m);
+    const unsigned hi = __shfl_xor_sync(dev::kFull, (unsigned)(v >> 32), m);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+__device__ __forceinline__ unsigned long long min64(unsigned long long a, unsigned long long b) {
+    return a < b ? a : b;
+}
+
+__device__ __forceinline__ unsigned long long max64(unsigned long long a, unsigned long long b) {
+    return a < b ? b : a;
+}
+
+// Bitonic sort of one key per lane, ascending with the lane.
+__device__ __forceinline__ unsigned long long warp_sort(unsigned long long v, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long o = shfl64_xor(v, j);
+            // lower lane of an ascending block (or upper of a descending) keeps the min
+            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+            v = keep_min ? min64(v, o) : max64(v, o);
+        }
+    }
+    return v;
 }
 
 template <int S>
@@ -75,7 +105,28 @@ struct KnnList {
         for (int s = 1; s < S; ++s) t = kslot == s ? key[s] : t;
         thr = shfl64(t, kl);
     }
+
+    // One slot only: merge a whole chunk's keys (any order, one per lane).
+    // The 32 smallest of list and chunk are the elementwise minimum of the
+    // ascending list and the descending chunk (a bitonic sequence), which a
+    // bitonic merge then sorts.
+    __device__ __forceinline__ void merge(unsigned long long ck, int lane) {
+        const unsigned long long c = shfl64(warp_sort(ck, lane), 31 - lane);
+        unsigned long long v = min64(key[0], c);
+#pragma unroll
+        for (int j = 16; j > 0; j >>= 1) {
+            const unsigned long long o = shfl64_xor(v, j);
+            v = (lane & j) == 0 ? min64(v, o) : max64(v, o);
+        }
+        key[0] = v;
+        thr = shfl64(v, kl);
+    }
 };
+
+// Candidates in one chunk at or above which the one-slot list merges the
+// whole chunk instead of inserting them one by one (a sort and a merge cost
+// about as much as five insertions).
+constexpr int kMergeAt = 6;
 
 // Points [a, b) of the cloud (b - a <= 32) against the list.
 template <int S>
@@ -88,6 +139,10 @@ __device__ __forceinline__ void knn_chunk(KnnList<S>& L, const float* P, int a, 
         ck = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)j;
     }
     unsigned m = __ballot_sync(dev::kFull, ck < L.thr);
+    if (S == 1 && __popc(m) >= kMergeAt) {
+        L.merge(ck, lane);
+        return;
+    }
     while (m) {
         const int src = __ffs(m) - 1;
         m &= m - 1;
