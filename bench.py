@@ -8,6 +8,14 @@ one batched call (graph-replayed).  Beside it, in the same run: plain FPS
 off/on, the end-to-end time through host buffers, the roofline of the
 sampling kernel, and the CPU oracle on the host's cores.
 
+Timing.  Throughput (`value`, `ms_per_step`): K steps back to back on one
+stream between two CUDA events, each step on the next of R resident copies
+of the batch (R copies span twice the L2), so every timed step reads cold
+points without a flush; a fixed-length sleep kernel ahead of the first event
+holds the stream while the host enqueues the K steps, so the GPU runs them
+back to back (the host path is what `e2e` measures).  Latency (`p50_ms`, `p99_ms`): isolated steps, each
+after a 256 MB write that flushes the L2, with its own pair of events.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line (rank 0).  Under torchrun each rank samples its own
@@ -38,6 +46,7 @@ B_CLOUDS, N_POINTS, C_SAMPLES, M_SECTORS, K_WINDOW = 32, 2048, 512, 32, 16
 WORKLOAD = (f"object batch {B_CLOUDS} x {N_POINTS} pts, C={C_SAMPLES}, "
             f"NPDU-AFPS M={M_SECTORS} k={K_WINDOW}")
 L2_FLUSH_BYTES = 256 << 20
+L2_BYTES = 129 << 20  # GB300 L2
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -187,6 +196,69 @@ def time_device(sampler, x, ba, out, steps: int, warmup: int, flush):
     torch.cuda.synchronize()
     sampler.sync()
     return [a.elapsed_time(b) for a, b in evs], sampler.launch_count - n0
+
+
+def rotation(x, total_out: int, dev):
+    """Copies of the batch in as many resident slots as cover twice the L2
+    (points and outputs), so that a step that visits a slot for the first time
+    in more than 2 x L2 of traffic reads its points from DRAM."""
+    import torch
+    slot_bytes = x.numel() * 4 + total_out * 4
+    R = max(8, -(-2 * L2_BYTES // slot_bytes))
+    xr = x.unsqueeze(0).repeat(R, *([1] * x.dim())).contiguous()
+    outr = torch.full((R, total_out), -1, dtype=torch.int32, device=dev)
+    return xr, outr
+
+
+def time_stream(sampler, xr, outr, ba, steps: int, warmup: int):
+    """Whole-job throughput: K steps issued back to back on one stream through
+    the C ABI (afps_sample_batched on a context without graphs: one direct
+    kernel launch per step; hundreds of distinct graphs, one per slot, were
+    measured to launch slower than that when queued), each on the next
+    resident slot of the rotation, timed by one pair of CUDA events around
+    the K steps.  Every slot is run once first (untimed); the timed steps
+    start at the least recently used slot, so every one of them reads cold
+    points.  Returns (ms per step, launches in the timed region, last slot
+    used, enqueue information)."""
+    import torch
+    from paper_2208_08795_gb300 import afps as A
+    fn = A.load().afps_sample_batched
+    stream = torch.cuda.current_stream()
+    R = xr.shape[0]
+    args = [(sampler.ctx, xr[i].data_ptr(), *ba.args(), outr[i].data_ptr(), stream.cuda_stream)
+            for i in range(R)]
+
+    def call(i):
+        if fn(*args[i % R]) != 0:
+            raise A.AfpsError(-1, A.afps_last_error(sampler.ctx))
+
+    for i in range(R):  # every slot once
+        call(i)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(warmup):
+        call(i)
+    torch.cuda.synchronize()
+    per_call = (time.perf_counter() - t0) / warmup
+    # Hold the stream (a fixed-length sleep kernel, outside the events) while
+    # the K steps are enqueued, so that the GPU runs them back to back and the
+    # host's per-call cost does not set the pace.
+    hold_s = 3.0 * per_call * steps + 1e-3
+    torch.cuda._sleep(int(hold_s * 2.07e9))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = sampler.launch_count
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for i in range(warmup, warmup + steps):
+        call(i)
+    e1.record(stream)
+    enqueue_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    sampler.sync()
+    info = {"host_enqueue_ms": round(enqueue_s * 1e3, 3), "hold_ms": round(hold_s * 1e3, 3),
+            "enqueued_within_hold": enqueue_s < hold_s}
+    return (e0.elapsed_time(e1) / steps, sampler.launch_count - n0, (warmup + steps - 1) % R,
+            info)
 
 
 def time_e2e(sampler, h_xyz, ba, h_out, steps: int, warmup: int):
@@ -482,30 +554,55 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
 
     plans = {}
 
-    def run(M, k, steps, warmup):
+    rot = {}
+
+    def run(M, k, steps, warmup, latency=False):
+        """Throughput over the rotation (back to back), and with latency=True
+        also per-step latency of isolated steps after an L2 flush."""
         ba = A.BatchArgs(off, C_SAMPLES, M, k, 0)
         out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
-        # untimed: the autotuner picks the kernel variant for this batch
+        # untimed: the autotuner picks the kernel variant (and writes the result)
         sampler.autotune_batched(x, ba, out)
         sampler.sync()
         n_s, c_s = -(-N_POINTS // M), -(-C_SAMPLES // M)
         plans[f"M{M}_{'npdu' if k else 'full'}"] = sampler.describe_plan(n_s, c_s, k, B_CLOUDS * M)
-        barrier()
-        ms, launches = time_device(sampler, x, ba, out, steps, warmup, flush)
-        barrier()
-        return ba, out, ms, launches
+        xr, outr = rotation(x, ba.total_out, dev)
+        rot["slots"], rot["mb"] = xr.shape[0], (xr.numel() + outr.numel()) * 4 / 2**20
+        # a context without graphs for the throughput, with the variant just tuned
+        tune = os.path.join(tempfile.gettempdir(), f"afps_bench_tune_{os.getpid()}.txt")
+        A.afps_save_tuning(sampler.ctx, tune)
+        direct = A.Sampler(local, tune_cache=tune)
+        try:
+            if direct.describe_plan(n_s, c_s, k, B_CLOUDS * M) != plans[f"M{M}_{'npdu' if k else 'full'}"]:
+                raise RuntimeError("the throughput context did not load the tuned variant")
+            barrier()
+            ms, launches, last, rot["enqueue"] = time_stream(direct, xr, outr, ba, steps, warmup)
+            barrier()
+        finally:
+            direct.close()
+            os.unlink(tune)
+        if not torch.equal(outr[last], out):
+            raise RuntimeError(f"M={M} k={k}: a rotated step differs from the single call")
+        del xr, outr
+        lat = None
+        if latency:
+            lat, _ = time_device(sampler, x, ba, out, steps, warmup, flush)
+            barrier()
+        return ba, out, ms, lat, launches
 
     # headline: NPDU-AFPS M=32 k=16
-    ba, out, ms, launches = run(M_SECTORS, K_WINDOW, args.steps, args.warmup)
-    ms_step = max_over_ranks(float(np.mean(ms)), world, dev)
-    p99 = max_over_ranks(pct(ms, 99), world, dev)
-    p50 = max_over_ranks(pct(ms, 50), world, dev)
+    ba, out, ms, lat, launches = run(M_SECTORS, K_WINDOW, args.steps, args.warmup, latency=True)
+    ms_step = max_over_ranks(ms, world, dev)
+    p99 = max_over_ranks(pct(lat, 99), world, dev)
+    p50 = max_over_ranks(pct(lat, 50), world, dev)
+    iso_ms = max_over_ranks(float(np.mean(lat)), world, dev)
     value = B_CLOUDS * world / (ms_step / 1e3)
     head_out = out.cpu().numpy()
+    head_enqueue = dict(rot["enqueue"])
 
     # plain FPS on the same batch, same protocol
-    _, _, ms_f, _ = run(1, 0, args.steps, args.warmup)
-    ms_fps = max_over_ranks(float(np.mean(ms_f)), world, dev)
+    _, _, ms_f, _, _ = run(1, 0, args.steps, args.warmup)
+    ms_fps = max_over_ranks(ms_f, world, dev)
     fps_value = B_CLOUDS * world / (ms_fps / 1e3)
 
     # sweep of the paper's M values, NPDU off / on
@@ -514,8 +611,8 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     for M in (1, 4, 16, 32):
         for npdu in (False, True):
             k = k_rule(M) if npdu else 0
-            _, _, ms_s, _ = run(M, k, sw_steps, max(3, args.warmup // 2))
-            m = max_over_ranks(float(np.mean(ms_s)), world, dev)
+            _, _, ms_s, _, _ = run(M, k, sw_steps, max(3, args.warmup // 2))
+            m = max_over_ranks(ms_s, world, dev)
             sweep[f"M{M}_{'npdu' if npdu else 'full'}"] = round(B_CLOUDS * world / (m / 1e3), 1)
 
     # end to end through host buffers
@@ -537,7 +634,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     # roofline of the sampling kernel (one launch per step)
     peak, peak_kind = measured_hbm_peak()
     hbm_bytes = 12 * int(off[-1]) + 4 * int(ba.total_out)
-    kernel_s = float(np.mean(ms)) / 1e3
+    kernel_s = ms / 1e3  # average launch duration over the timed region (one launch per step)
     achieved = hbm_bytes / kernel_s / 1e9
     evals, compares = npdu_work(head_out, ba, K_WINDOW)
     sm_mhz = clk["sm_mhz"] or 2070.0
@@ -553,9 +650,16 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "clouds_per_gpu": B_CLOUDS, "N": N_POINTS,
                    "C": C_SAMPLES, "M": M_SECTORS, "k": K_WINDOW,
-                   "l2": "flushed before every step (256 MB write)",
+                   "l2": f"inputs larger than L2: the {rot['slots']} resident copies of the batch "
+                         f"({rot['mb']:.0f} MB with their outputs) are visited in turn, so each "
+                         "timed step reads points untouched for more than 2 x L2 of traffic; "
+                         "p50/p99 are isolated steps, each after a 256 MB L2 flush",
+                   "timing": "value and ms_per_step: K steps back to back between two CUDA "
+                             "events on the launching stream, enqueued while a sleep kernel "
+                             "(before the first event) holds the stream; p50/p99: per-step events",
                    "parallelism": f"replicas x{world}",
-                   "launch": "CUDA graph replay, kernel variant chosen by the autotuner (untimed)"},
+                   "launch": "throughput: one direct kernel launch per step; latency: CUDA graph "
+                             "replay; kernel variant chosen by the autotuner (untimed)"},
         "kernel_variants": plans,
         "sampled_points_per_s": value * C_SAMPLES,
         "fps_baseline": {"value": fps_value, "unit": UNIT, "ms_per_step": ms_fps,
@@ -579,6 +683,8 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         "sort_by_key": sorting,
         "ball_query": grouping,
         "gpu_launches": launches,
+        "isolated_step_ms": iso_ms,
+        "enqueue": head_enqueue,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
     }

@@ -136,7 +136,9 @@ int afps_sample_ex(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int3
  * B+1 nondecreasing entries with h_out_off[b+1] - h_out_off[b] >= h_C[b]).
  * All (cloud, sector) work items run in one launch per kernel shape class;
  * with AFPS_FLAG_GRAPH the launches are captured once per distinct argument
- * set (pointers included) and replayed.  Host arrays are read before return.
+ * set (pointers included) and replayed; a context keeps up to 512 such
+ * graphs, evicting the least recently used.  Host arrays are read before
+ * return.
  */
 int afps_sample_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_off,
                         int32_t B, const int32_t* h_C, const int32_t* h_M,

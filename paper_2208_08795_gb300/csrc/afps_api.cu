@@ -25,7 +25,7 @@ using afps::Variant;
 namespace {
 
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
-constexpr size_t kMaxGraphs = 32;
+constexpr size_t kMaxGraphs = 512;  // cached graphs per context (least recently used evicted)
 constexpr int kStageSlots = 4;  // pinned upload buffers in flight
 
 // ---------------------------------------------------------------- buffers
@@ -184,11 +184,13 @@ struct CloudCheck {
     int32_t start_r = 0;
 };
 
+// (The message streams are built on the error paths only: constructing one
+// costs about a microsecond, once per cloud of every call.)
 CloudCheck check_cloud(int64_t N, int32_t C, int32_t M, int32_t k, int64_t start) {
     CloudCheck r;
-    std::ostringstream os;
     if (N < 1 || N > INT32_MAX || C < 1 || (int64_t)C > N || M < 1 || M > C || k < 0 ||
         start < 0 || start >= N) {
+        std::ostringstream os;
         os << "invalid arguments: N=" << N << " C=" << C << " M=" << M << " k=" << k
            << " start=" << start << " (need 1<=C<=N<2^31, 1<=M<=C, k>=0, 0<=start<N)";
         r.code = AFPS_ERR_INVALID_ARG;
@@ -200,6 +202,7 @@ CloudCheck check_cloud(int64_t N, int32_t C, int32_t M, int32_t k, int64_t start
         const int64_t lo = sec_lo(N, M, s), hi = sec_lo(N, M, s + 1);
         const int64_t c = sec_off(C, M, s + 1) - sec_off(C, M, s);
         if (c > hi - lo) {
+            std::ostringstream os;
             os << "sector " << s << " has " << (hi - lo) << " points but " << c
                << " samples (N=" << N << " C=" << C << " M=" << M << ")";
             r.code = AFPS_ERR_SECTOR_TOO_SMALL;
@@ -212,6 +215,7 @@ CloudCheck check_cloud(int64_t N, int32_t C, int32_t M, int32_t k, int64_t start
     }
     r.start_r = (int32_t)(start - sec_lo(N, M, s0));
     if (r.n_max > AFPS_MAX_SECTOR_POINTS) {
+        std::ostringstream os;
         os << "sector of " << r.n_max << " points exceeds AFPS_MAX_SECTOR_POINTS ("
            << AFPS_MAX_SECTOR_POINTS << ")";
         r.code = AFPS_ERR_UNSUPPORTED;
@@ -434,26 +438,6 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
         ClassPlan cp;
         cp.npdu = g.first.first == 1;
         cp.first = plan.items.size();
-        for (const Member& m : g.second) {
-            const int32_t b = m.b;
-            const int64_t N = n_pts[b];
-            cp.n_max = std::max(cp.n_max, m.chk.n_max);
-            cp.c_max = std::max(cp.c_max, m.chk.c_max);
-            for (int64_t s = 0; s < M[b]; ++s) {
-                const int64_t lo = sec_lo(N, M[b], s), hi = sec_lo(N, M[b], s + 1);
-                const int64_t o0 = sec_off(C[b], M[b], s), o1 = sec_off(C[b], M[b], s + 1);
-                ItemDesc d{};
-                d.src = pt_begin[b] + lo;
-                d.dst = out_begin[b] + o0;
-                d.n = (int32_t)(hi - lo);
-                d.c = (int32_t)(o1 - o0);
-                d.first = std::min<int32_t>(m.chk.start_r, d.n - 1);
-                d.lo = (int32_t)lo;
-                window_sides(K[b], method ? method[b] : 0u, d);
-                plan.items.push_back(d);
-            }
-        }
-        cp.count = plan.items.size() - cp.first;
         // a run of equal clouds stored back to back: items computed on the device
         {
             const Member& m0 = g.second.front();
@@ -483,8 +467,34 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
                 cp.single.flags = w.flags;
                 cp.single.start_r = m0.chk.start_r;
                 cp.single.wide = (int64_t)M[b0] * n_pts[b0] > (int64_t)UINT32_MAX ? 1 : 0;
+                cp.n_max = m0.chk.n_max;
+                cp.c_max = m0.chk.c_max;
+                cp.count = g.second.size() * (size_t)M[b0];
+                cp.v = choose_variant(ctx, cp.npdu, cp.n_max, cp.c_max, cp.count);
+                plan.classes.push_back(cp);
+                continue;
             }
         }
+        for (const Member& m : g.second) {
+            const int32_t b = m.b;
+            const int64_t N = n_pts[b];
+            cp.n_max = std::max(cp.n_max, m.chk.n_max);
+            cp.c_max = std::max(cp.c_max, m.chk.c_max);
+            for (int64_t s = 0; s < M[b]; ++s) {
+                const int64_t lo = sec_lo(N, M[b], s), hi = sec_lo(N, M[b], s + 1);
+                const int64_t o0 = sec_off(C[b], M[b], s), o1 = sec_off(C[b], M[b], s + 1);
+                ItemDesc d{};
+                d.src = pt_begin[b] + lo;
+                d.dst = out_begin[b] + o0;
+                d.n = (int32_t)(hi - lo);
+                d.c = (int32_t)(o1 - o0);
+                d.first = std::min<int32_t>(m.chk.start_r, d.n - 1);
+                d.lo = (int32_t)lo;
+                window_sides(K[b], method ? method[b] : 0u, d);
+                plan.items.push_back(d);
+            }
+        }
+        cp.count = plan.items.size() - cp.first;
         // largest work first (longest-processing-time order for the queue)
         auto cost = [&](const ItemDesc& d) {
             return cp.npdu ? (int64_t)d.c * (d.kl + d.kr + 1 + d.n / 32) : (int64_t)d.c * d.n;
@@ -600,7 +610,8 @@ int make_graph(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);
     AFPS_CUDA(ctx, g.items.reserve(bytes));
     AFPS_CUDA(ctx, g.counters.reserve(plan.classes.size() * sizeof(unsigned int)));
-    AFPS_CUDA(ctx, cudaMemcpy(g.items.p, plan.items.data(), bytes, cudaMemcpyHostToDevice));
+    if (bytes)  // classes of equal-cloud runs need no table
+        AFPS_CUDA(ctx, cudaMemcpy(g.items.p, plan.items.data(), bytes, cudaMemcpyHostToDevice));
     const ItemDesc* d_items = static_cast<const ItemDesc*>(g.items.p);
     unsigned int* counters = static_cast<unsigned int*>(g.counters.p);
     AFPS_CUDA(ctx, cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));

@@ -28,6 +28,11 @@
 //      Records are double-buffered by exchange parity, so a record is never
 //      overwritten before every reader passed the barrier that follows its
 //      read.
+#include <map>
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "afps_device.cuh"
 
 namespace afps {
@@ -357,14 +362,33 @@ static SectorKernel kernel_for(const Variant& v, bool npdu) {
     return cta_kernel_for(v.P, npdu, v.CS > 1);
 }
 
+// Function attributes for a launch, set only when they must grow: the
+// dynamic shared-memory attribute is an upper bound, so each (device,
+// kernel) keeps the largest value set so far, and the non-portable cluster
+// permission is set once.  Setting them on every launch costs host time.
 static cudaError_t prepare(SectorKernel fn, const Variant& v, size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> smem_set;
+    static std::set<std::pair<int, const void*>> wide_set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (v.kind == KIND_CTA && v.CS > 8)
-        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
-                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    return e;
+    const void* f = reinterpret_cast<const void*>(fn);
+    const auto key = std::make_pair(dev, f);
+    const bool wide = v.kind == KIND_CTA && v.CS > 8;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = smem_set.find(key);
+    if (it == smem_set.end() || it->second < smem) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set[key] = smem;
+    }
+    if (wide && !wide_set.count(key)) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        wide_set.insert(key);
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_sector(const Variant& v, bool npdu, const LaunchArgs& a, int grid,
