@@ -65,7 +65,10 @@ extern "C" {
 
 /* afps_config.flags */
 #define AFPS_FLAG_GRAPH 1u     /* replay afps_sample_batched from cached CUDA graphs */
-#define AFPS_FLAG_AUTOTUNE 2u  /* time kernel variants on first use of a shape class */
+/* The first batched call with an argument set that has a shape class
+ * without a tuned variant runs afps_autotune_batched on it (synchronously),
+ * then samples as usual. */
+#define AFPS_FLAG_AUTOTUNE 2u
 /* Fault injection for tests of failure detection: the stage-in arms its
  * shared-memory barrier but never issues the bulk copy, so every bounded
  * wait runs out (after timeout_ns) and afps_sync returns AFPS_ERR_TIMEOUT.

@@ -12,6 +12,7 @@
 #include <sstream>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/afps.h"
@@ -26,6 +27,7 @@ namespace {
 
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
 constexpr size_t kMaxGraphs = 512;  // cached graphs per context (least recently used evicted)
+constexpr size_t kMaxPlans = 256;   // cached batch plans per context (cleared when full)
 constexpr int kStageSlots = 4;  // pinned upload buffers in flight
 
 // ---------------------------------------------------------------- buffers
@@ -115,6 +117,8 @@ struct afps_ctx {
     cudaEvent_t stage_ev[kStageSlots] = {};  // last copy out of each slot
     int stage_next = 0;
     std::unordered_map<std::string, GraphEntry> graphs;
+    std::unordered_map<std::string, BatchPlan> plans;  // batched calls without graphs
+    std::unordered_set<std::string> checked;  // argument sets whose classes are tuned (AUTOTUNE)
     std::map<std::string, Variant> tuned;
     int64_t launches = 0;
     uint64_t tick = 0;
@@ -549,7 +553,12 @@ int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* 
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);
     AFPS_CUDA(ctx, ctx->counters.reserve(plan.classes.size() * sizeof(unsigned int)));
     bool table = false;  // some class reads the item table
-    for (const ClassPlan& cp : plan.classes) table = table || !cp.uniform;
+    bool queue = false;  // some class uses a work-queue counter
+    for (const ClassPlan& cp : plan.classes) {
+        table = table || !cp.uniform;
+        queue = queue || (cp.v.kind == afps::KIND_WARP &&
+                          (size_t)grid_for(cp.v, cp.count) * (size_t)cp.v.W < cp.count);
+    }
     if (table) {
         int urc = upload(ctx, ctx->items, plan.items.data(), bytes, stream);
         if (urc != AFPS_OK) return urc;
@@ -562,7 +571,8 @@ int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* 
                               cp.count, counters + i, d_xyz, d_out, stream, false, cp.run());
         if (rc != AFPS_OK) return rc;
     }
-    AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, stream));
+    // the workspace's last use, for ordering its next upload (none used: no record)
+    if (table || queue) AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, stream));
     return AFPS_OK;
 }
 
@@ -644,6 +654,30 @@ int make_graph(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t
     return AFPS_OK;
 }
 
+// AFPS_FLAG_AUTOTUNE: the first call with an argument set any of whose shape
+// classes has no tuned variant yet runs the autotuner on it (synchronously;
+// the call then samples as usual).
+int tune_if_new(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int32_t B,
+                const int32_t* C, const int32_t* M, const int32_t* K, const int64_t* start,
+                const int64_t* out_off, int32_t* d_out, cudaStream_t stream,
+                const uint32_t* method) {
+    const std::string key = graph_key(nullptr, nullptr, pt_off, B, C, M, K, start, out_off, method);
+    if (ctx->checked.count(key)) return AFPS_OK;
+    BatchPlan plan;
+    int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan, method);
+    if (rc != AFPS_OK) return rc;
+    bool tuned = true;
+    for (const ClassPlan& cp : plan.classes)
+        tuned = tuned && ctx->tuned.count(class_key(cp.npdu, cp.n_max, cp.c_max, cp.count)) > 0;
+    if (!tuned) {
+        rc = afps_autotune_batched(ctx, d_xyz, pt_off, B, C, M, K, start, out_off, d_out, stream);
+        if (rc < 0) return rc;
+    }
+    if (ctx->checked.size() >= kMaxPlans) ctx->checked.clear();
+    ctx->checked.insert(key);
+    return AFPS_OK;
+}
+
 int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int32_t B,
                    const int32_t* C, const int32_t* M, const int32_t* K, const int64_t* start,
                    const int64_t* out_off, int32_t* d_out, cudaStream_t stream,
@@ -651,14 +685,27 @@ int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int
     if (!d_xyz || !d_out) return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: NULL device pointer");
     if (reinterpret_cast<uintptr_t>(d_xyz) % 4 || reinterpret_cast<uintptr_t>(d_out) % 4)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: xyz and out must be 4-byte aligned");
-    if (!(ctx->flags & AFPS_FLAG_GRAPH)) {
-        BatchPlan plan;
-        int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan, method);
-        if (rc != AFPS_OK) return rc;
-        return run_plan(ctx, plan, d_xyz, d_out, stream);
-    }
     if (B < 1 || !pt_off || !C || !M || !K || !start || !out_off)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
+    if (ctx->flags & AFPS_FLAG_AUTOTUNE) {
+        int rc = tune_if_new(ctx, d_xyz, pt_off, B, C, M, K, start, out_off, d_out, stream, method);
+        if (rc != AFPS_OK) return rc;
+    }
+    if (!(ctx->flags & AFPS_FLAG_GRAPH)) {
+        // plans depend on the host arrays (and the tuning) only, not on the
+        // device pointers: a repeated argument set skips validation and planning
+        const std::string key =
+            graph_key(nullptr, nullptr, pt_off, B, C, M, K, start, out_off, method);
+        auto it = ctx->plans.find(key);
+        if (it == ctx->plans.end()) {
+            BatchPlan plan;
+            int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan, method);
+            if (rc != AFPS_OK) return rc;
+            if (ctx->plans.size() >= kMaxPlans) ctx->plans.clear();
+            it = ctx->plans.emplace(key, std::move(plan)).first;
+        }
+        return run_plan(ctx, it->second, d_xyz, d_out, stream);
+    }
     const std::string key = graph_key(d_xyz, d_out, pt_off, B, C, M, K, start, out_off, method);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
@@ -1247,6 +1294,7 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     clear_graphs(ctx);  // graphs captured earlier may use other variants
+    ctx->plans.clear();  // and so may cached plans
     ctx->last_error.clear();
     rc = run_plan(ctx, plan, d_xyz, d_out, st);
     return rc == AFPS_OK ? tuned : rc;

@@ -78,6 +78,12 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
     }
     __syncthreads();
     if (CLUSTER) dev::cluster_sync();  // every peer's barriers exist before any remote store
+    // Programmatic dependent launch: wait until the previous kernel of the
+    // stream has completed (no global memory access before this), then let
+    // the next one be scheduled: one kernel waits behind a running one, and
+    // the chain never grows deeper than that.
+    dev::pdl_wait();
+    dev::pdl_launch_dependents();
     // barrier addresses and phases in scalars: a two-element array indexed
     // by the exchange parity would live in a local-memory stack frame
     uint32_t xphase0 = 0u, xphase1 = 0u;
@@ -404,17 +410,31 @@ cudaError_t launch_sector(const Variant& v, bool npdu, const LaunchArgs& a, int 
         cfg.blockDim = dim3((unsigned)(32 * v.W), 1, 1);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = stream;
-        cudaLaunchAttribute attr[1];
+        cudaLaunchAttribute attr[2];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = (unsigned)v.CS;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = 2;
         return cudaLaunchKernelEx(&cfg, fn, a);
     }
-    fn<<<grid, 32 * v.W, smem, stream>>>(a);
-    return cudaGetLastError();
+    // Programmatic dependent launch: the kernels wait (griddepcontrol.wait)
+    // before touching global memory, so they may be scheduled while the
+    // previous kernel of the stream is still running.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)(32 * v.W), 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
 int max_active_clusters(const Variant& v) {

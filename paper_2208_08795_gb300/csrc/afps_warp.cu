@@ -38,6 +38,12 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         dev::fence_mbar_init();
     }
     __syncwarp();
+    // Programmatic dependent launch: wait until the previous kernel of the
+    // stream has completed (no global memory access before this), then let
+    // the next one be scheduled: one kernel waits behind a running one, and
+    // the chain never grows deeper than that.
+    dev::pdl_wait();
+    dev::pdl_launch_dependents();
     uint32_t phase = 0;
 
     const int nwarps = gridDim.x * W;

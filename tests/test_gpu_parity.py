@@ -446,6 +446,50 @@ def test_autotune(objects, tmp_path):
         s.close()
 
 
+def test_autotune_on_first_use(objects, tmp_path):
+    """AFPS_FLAG_AUTOTUNE: the first batched call of a new argument set tunes
+    its classes (then samples); later calls reuse the choice."""
+    build_mod.build()
+    path = tmp_path / "t.txt"
+    s = B.Sampler(0, flags=B.AFPS_FLAG_AUTOTUNE, tune_cache=str(path))
+    try:
+        xyz, off = synth.pack(objects)
+        x = torch.from_numpy(xyz).cuda()
+        ba = B.BatchArgs(off, 512, 32, 16, 0)
+        for _ in range(2):
+            o = s.sample_batched(x, ba).cpu().numpy()
+            for b in (0, 5, len(objects) - 1):
+                assert_same(o[ba.out_off[b]:ba.out_off[b + 1]], oracle.afps(objects[b], 512, 32, 16),
+                            f"cloud {b}")
+        assert B.afps_save_tuning(s.ctx, None) == 0
+        assert "npdu:n64:c16:i1024" in path.read_text()
+    finally:
+        s.close()
+
+
+def test_cached_plan_with_new_buffers(objects):
+    """Without graphs a repeated argument set reuses its plan: other device
+    buffers and other points must still give each set's own result, also
+    after the autotuner has changed the variants."""
+    build_mod.build()
+    s = B.Sampler(0)
+    try:
+        sets = [objects[:8], [synth.object_batch(9, 8, 2048)[i] for i in range(8)]]
+        bas = [B.BatchArgs(synth.pack(c)[1], 512, 16, 16, 0) for c in sets]
+        xs = [torch.from_numpy(synth.pack(c)[0]).cuda() for c in sets]
+        for rep in range(2):
+            for c, ba, x in zip(sets, bas, xs):
+                o = s.sample_batched(x, ba).cpu().numpy()
+                for b in (0, 7):
+                    assert_same(o[ba.out_off[b]:ba.out_off[b + 1]], oracle.afps(c[b], 512, 16, 16),
+                                f"rep {rep} cloud {b}")
+            if rep == 0:
+                s.autotune_batched(xs[0], bas[0], torch.empty(bas[0].total_out, dtype=torch.int32,
+                                                                device="cuda"))
+    finally:
+        s.close()
+
+
 # --------------------------------------------------------------- failure detection
 def test_bounded_wait_reports_timeout_and_context_survives():
     """Fault injection on the host side of the barrier: the copy is never
