@@ -34,12 +34,14 @@ constexpr int kStageSlots = 4;  // pinned upload buffers in flight
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    // Grows to at least twice its size: each growth frees (which waits for
+    // the device) and allocates, so a slowly rising need must not pay it often.
     cudaError_t reserve(size_t want) {
         if (want <= bytes) return cudaSuccess;
+        const size_t cap = std::max({want, 2 * bytes, (size_t)4096});
         if (p) cudaFree(p);
         p = nullptr;
         bytes = 0;
-        size_t cap = std::max(want, (size_t)4096);
         cudaError_t e = cudaMalloc(&p, cap);
         if (e == cudaSuccess) bytes = cap;
         return e;
@@ -54,12 +56,13 @@ struct DevBuf {
 struct HostBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    // Grows to at least twice its size (page-locked allocations are slow).
     cudaError_t reserve(size_t want) {
         if (want <= bytes) return cudaSuccess;
+        const size_t cap = std::max({want, 2 * bytes, (size_t)4096});
         if (p) cudaFreeHost(p);
         p = nullptr;
         bytes = 0;
-        size_t cap = std::max(want, (size_t)4096);
         cudaError_t e = cudaMallocHost(&p, cap);
         if (e == cudaSuccess) bytes = cap;
         return e;
@@ -851,6 +854,18 @@ int gather_run(afps_ctx* ctx, const GatherDesc* descs, int32_t B, const float* i
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
     ctx->launches += 1;
     AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, stream));
+    return AFPS_OK;
+}
+
+// Reserve the shared workspace (device item table and every slot of the
+// pinned upload ring) for tables of up to `bytes`, so that a runtime whose
+// tables grow over time (the server) does not reallocate them mid-stream.
+int reserve_workspace(afps_ctx* ctx, size_t bytes) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    DeviceGuard guard(ctx->device);
+    AFPS_CUDA(ctx, cudaDeviceSynchronize());  // nothing may still read the old buffers
+    AFPS_CUDA(ctx, ctx->items.reserve(bytes));
+    for (int s = 0; s < kStageSlots; ++s) AFPS_CUDA(ctx, ctx->stage[s].reserve(bytes));
     return AFPS_OK;
 }
 

@@ -78,6 +78,19 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
     }
     __syncthreads();
     if (CLUSTER) dev::cluster_sync();  // every peer's barriers exist before any remote store
+    // A computed first item (no table) needs no memory access, so this CTA's
+    // part of its points can be prefetched into L2 while the previous kernel
+    // of the stream still runs.
+    {
+        const int g0 = CLUSTER ? (int)dev::cluster_id_x() : (int)blockIdx.x;
+        if (!a.items && !a.host_resident && g0 < a.n_items) {
+            const ItemDesc d0 = dev::load_item(a, g0);
+            const int ch = CLUSTER ? (d0.n + CS - 1) / CS : d0.n;
+            const int p0 = rank * ch, pn = max(0, min(d0.n - p0, ch));
+            const char* g = reinterpret_cast<const char*>(a.xyz + 3 * (d0.src + p0));
+            for (int off = 128 * tid; off < 12 * pn; off += 128 * T) dev::prefetch_l2(g + off);
+        }
+    }
     // Programmatic dependent launch: wait until the previous kernel of the
     // stream has completed (no global memory access before this), then let
     // the next one be scheduled: one kernel waits behind a running one, and

@@ -24,6 +24,11 @@
 #include "../../include/afps.h"
 #include "afps_internal.h"
 
+namespace afps {
+// afps_api.cu: reserve the context's shared workspace for tables of `bytes`.
+int reserve_workspace(afps_ctx* ctx, size_t bytes);
+}  // namespace afps
+
 namespace {
 
 constexpr int64_t kBlockAlign = 48;
@@ -270,6 +275,19 @@ int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_confi
     }
     s->pool_base = static_cast<unsigned char*>(hp);
     s->pool.reset(new Arena(s->cfg.host_pool_bytes / kBlockAlign * kBlockAlign));
+    // the largest step table: every slot's request at its widest level
+    int32_t widest = 1;
+    for (int l = 0; l < s->cfg.n_levels; ++l) widest = std::max(widest, std::min(s->cfg.M, s->levels[l]));
+    const size_t table = std::max((size_t)s->cfg.max_inflight * widest * sizeof(afps::ItemDesc),
+                                  (size_t)s->cfg.max_inflight * sizeof(afps::GatherDesc));
+    const int rc = afps::reserve_workspace(ctx, table);
+    if (rc != AFPS_OK) {
+        cudaFreeHost(hp);
+        cudaFreeHost(h);
+        cudaFree(p);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        return rc;
+    }
     *out = s.release();
     return AFPS_OK;
 }
