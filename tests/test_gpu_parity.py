@@ -490,6 +490,64 @@ def test_cached_plan_with_new_buffers(objects):
         s.close()
 
 
+# --------------------------------------------------------------- stream ordering
+# The sector kernels are launched with programmatic stream serialization:
+# they may become resident while the previous kernel of the stream runs, and
+# wait for it before touching global memory (an L2 prefetch hint is the only
+# access issued earlier).  Points produced by the kernel right before, and
+# outputs written by the call right before, must still be ordered.
+def test_points_written_by_the_previous_kernel(objects):
+    build_mod.build()
+    for graph in (False, True):
+        s = B.Sampler(0, graph=graph)
+        try:
+            xyz, off = synth.pack(objects[:8])
+            base = torch.from_numpy(xyz).cuda()
+            ba = B.BatchArgs(off, 512, 32, 16, 0)
+            out = torch.empty(ba.total_out, dtype=torch.int32, device="cuda")
+            x = torch.empty_like(base)
+            for rep in range(3):
+                # a long sampling call is still running when the points are rewritten
+                s.sample_batched(base, B.BatchArgs(off, 512, 1, 0, 0))
+                torch.mul(base, float(2 ** rep), out=x)  # exact scaling: same indices
+                s.sample_batched(x, ba, out=out)
+                o = out.cpu().numpy()
+                for b in (0, 7):
+                    assert_same(o[ba.out_off[b]:ba.out_off[b + 1]],
+                                oracle.afps(objects[b], 512, 32, 16), f"graph={graph} rep {rep}")
+        finally:
+            s.close()
+
+
+def test_back_to_back_calls_on_one_output(objects):
+    """Calls on different clouds write the same output buffer one after the
+    other; the last call's result must be what remains, for every pair."""
+    build_mod.build()
+    s = B.Sampler(0)
+    try:
+        sets = [objects[:8], objects[8:16], objects[16:24]]
+        xs = [torch.from_numpy(synth.pack(c)[0]).cuda() for c in sets]
+        ba = B.BatchArgs(synth.pack(sets[0])[1], 512, 32, 16, 0)
+        out = torch.empty(ba.total_out, dtype=torch.int32, device="cuda")
+        refs = [[oracle.afps(P, 512, 32, 16) for P in c] for c in sets]
+        for order in ((0, 1, 2), (2, 0, 1), (1, 2, 0, 1)):
+            for i in order:
+                s.sample_batched(xs[i], ba, out=out)
+            o = out.cpu().numpy()
+            last = order[-1]
+            for b in range(8):
+                assert_same(o[ba.out_off[b]:ba.out_off[b + 1]], refs[last][b], f"order {order}")
+        # a long chain of calls, each checked through its own output
+        outs = [torch.empty(ba.total_out, dtype=torch.int32, device="cuda") for _ in range(60)]
+        for j, o in enumerate(outs):
+            s.sample_batched(xs[j % 3], ba, out=o)
+        for j, o in enumerate(outs):
+            oo = o.cpu().numpy()
+            assert_same(oo[ba.out_off[5]:ba.out_off[6]], refs[j % 3][5], f"chain {j}")
+    finally:
+        s.close()
+
+
 # --------------------------------------------------------------- failure detection
 def test_bounded_wait_reports_timeout_and_context_survives():
     """Fault injection on the host side of the barrier: the copy is never
