@@ -173,6 +173,18 @@ int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h
                              const int64_t* h_out_off, int32_t* h_out, void* stream);
 
 /*
+ * afps_sample_batched_host without the final wait: the call returns once the
+ * work is queued on the stream, so consecutive calls (on other buffers)
+ * overlap.  Both buffers must be page-locked (AFPS_ERR_INVALID_ARG
+ * otherwise) and stay untouched until the stream has reached the call
+ * (afps_sync or a stream synchronisation); h_out holds the indices then.
+ */
+int afps_sample_batched_host_async(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off,
+                                   int32_t B, const int32_t* h_C, const int32_t* h_M,
+                                   const int32_t* h_win, const int64_t* h_start,
+                                   const int64_t* h_out_off, int32_t* h_out, void* stream);
+
+/*
  * Gather for chained sampling levels (the PointNet++ set-abstraction
  * hierarchy the paper targets, Sec. I-II): for each of B clouds, take the
  * samples d_sel[h_sel_off[b] .. h_sel_off[b+1]) (indices relative to the

@@ -40,7 +40,8 @@ EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
            "afps_server_create", "afps_server_submit", "afps_server_step", "afps_server_poll",
            "afps_server_stats", "afps_server_clock_ms", "afps_server_destroy",
            "afps_sort_by_key", "afps_sample_ex", "afps_sample_batched_ex",
-           "afps_coverage_radius", "afps_ball_query", "afps_knn")
+           "afps_coverage_radius", "afps_ball_query", "afps_knn",
+           "afps_sample_batched_host_async")
 
 
 class AfpsLibraryError(RuntimeError):
@@ -94,7 +95,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.afps_sample.argtypes = [vp, vp, i64, i32, i32, i32, i64, vp, vp]
     L.afps_sample.restype = ctypes.c_int
     batched = [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
-    for name in ("afps_sample_batched", "afps_sample_batched_host", "afps_autotune_batched"):
+    for name in ("afps_sample_batched", "afps_sample_batched_host",
+                 "afps_sample_batched_host_async", "afps_autotune_batched"):
         getattr(L, name).argtypes = batched
         getattr(L, name).restype = ctypes.c_int
     L.afps_gather_levels.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -198,6 +200,12 @@ def afps_sample_batched_host(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, 
                              h_out, stream) -> int:
     return load().afps_sample_batched_host(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win,
                                            h_start, h_out_off, h_out, stream)
+
+
+def afps_sample_batched_host_async(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win, h_start,
+                                   h_out_off, h_out, stream) -> int:
+    return load().afps_sample_batched_host_async(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win,
+                                                 h_start, h_out_off, h_out, stream)
 
 
 def afps_autotune_batched(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
@@ -384,6 +392,18 @@ class Sampler:
         assert h_xyz.dtype == np.float32 and h_xyz.flags.c_contiguous
         assert h_out.dtype == np.int32 and h_out.flags.c_contiguous
         self._check(load().afps_sample_batched_host(
+            self.ctx, h_xyz.ctypes.data, _ptr(ba.pt_off), ba.B, _ptr(ba.C), _ptr(ba.M),
+            _ptr(ba.k), _ptr(ba.start), _ptr(ba.out_off), h_out.ctypes.data,
+            self._stream(stream)))
+        return h_out
+
+    def sample_batched_host_async(self, h_xyz: np.ndarray, ba: "BatchArgs", h_out: np.ndarray,
+                                  stream=None):
+        """Page-locked host buffers in and out, returning once queued; h_out
+        is valid after `sync` (keep both buffers alive and unchanged until then)."""
+        assert h_xyz.dtype == np.float32 and h_xyz.flags.c_contiguous
+        assert h_out.dtype == np.int32 and h_out.flags.c_contiguous
+        self._check(load().afps_sample_batched_host_async(
             self.ctx, h_xyz.ctypes.data, _ptr(ba.pt_off), ba.B, _ptr(ba.C), _ptr(ba.M),
             _ptr(ba.k), _ptr(ba.start), _ptr(ba.out_off), h_out.ctypes.data,
             self._stream(stream)))

@@ -552,7 +552,7 @@ int build_plan_consecutive(afps_ctx* ctx, const int64_t* pt_off, int32_t B, cons
 
 // Run a plan out of the context's shared workspace (no graph).
 int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* d_out,
-             cudaStream_t stream) {
+             cudaStream_t stream, bool host_resident = false) {
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);
     AFPS_CUDA(ctx, ctx->counters.reserve(plan.classes.size() * sizeof(unsigned int)));
     bool table = false;  // some class reads the item table
@@ -571,7 +571,8 @@ int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* 
     for (size_t i = 0; i < plan.classes.size(); ++i) {
         const ClassPlan& cp = plan.classes[i];
         int rc = launch_class(ctx, cp.v, cp.npdu, cp.uniform ? nullptr : d_items + cp.first,
-                              cp.count, counters + i, d_xyz, d_out, stream, false, cp.run());
+                              cp.count, counters + i, d_xyz, d_out, stream, host_resident,
+                              cp.run());
         if (rc != AFPS_OK) return rc;
     }
     // the workspace's last use, for ordering its next upload (none used: no record)
@@ -684,17 +685,17 @@ int tune_if_new(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int32_
 int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int32_t B,
                    const int32_t* C, const int32_t* M, const int32_t* K, const int64_t* start,
                    const int64_t* out_off, int32_t* d_out, cudaStream_t stream,
-                   const uint32_t* method = nullptr) {
+                   const uint32_t* method = nullptr, bool host_resident = false) {
     if (!d_xyz || !d_out) return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: NULL device pointer");
     if (reinterpret_cast<uintptr_t>(d_xyz) % 4 || reinterpret_cast<uintptr_t>(d_out) % 4)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: xyz and out must be 4-byte aligned");
     if (B < 1 || !pt_off || !C || !M || !K || !start || !out_off)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
-    if (ctx->flags & AFPS_FLAG_AUTOTUNE) {
+    if ((ctx->flags & AFPS_FLAG_AUTOTUNE) && !host_resident) {  // the tuner stages by bulk copy
         int rc = tune_if_new(ctx, d_xyz, pt_off, B, C, M, K, start, out_off, d_out, stream, method);
         if (rc != AFPS_OK) return rc;
     }
-    if (!(ctx->flags & AFPS_FLAG_GRAPH)) {
+    if (!(ctx->flags & AFPS_FLAG_GRAPH) || host_resident) {
         // plans depend on the host arrays (and the tuning) only, not on the
         // device pointers: a repeated argument set skips validation and planning
         const std::string key =
@@ -707,7 +708,7 @@ int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int
             if (ctx->plans.size() >= kMaxPlans) ctx->plans.clear();
             it = ctx->plans.emplace(key, std::move(plan)).first;
         }
-        return run_plan(ctx, it->second, d_xyz, d_out, stream);
+        return run_plan(ctx, it->second, d_xyz, d_out, stream, host_resident);
     }
     const std::string key = graph_key(d_xyz, d_out, pt_off, B, C, M, K, start, out_off, method);
     auto it = ctx->graphs.find(key);
@@ -757,7 +758,7 @@ bool is_pinned(const void* p) {
 int host_graph_call(afps_ctx* ctx, const float* h_xyz, const int64_t* pt_off, int32_t B,
                     const int32_t* C, const int32_t* M, const int32_t* K, const int64_t* start,
                     const int64_t* out_off, int32_t* h_out, size_t xyz_bytes, size_t out_bytes,
-                    cudaStream_t stream) {
+                    cudaStream_t stream, bool sync) {
     std::string key = "H" + graph_key(h_xyz, h_out, pt_off, B, C, M, K, start, out_off);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
@@ -801,7 +802,7 @@ int host_graph_call(afps_ctx* ctx, const float* h_xyz, const int64_t* pt_off, in
     it->second.last_use = ++ctx->tick;
     AFPS_CUDA(ctx, cudaGraphLaunch(it->second.exec, stream));
     ctx->launches += it->second.kernels;
-    AFPS_CUDA(ctx, cudaStreamSynchronize(stream));
+    if (sync) AFPS_CUDA(ctx, cudaStreamSynchronize(stream));
     return AFPS_OK;
 }
 
@@ -1024,23 +1025,50 @@ int afps_sample_batched_ex(afps_ctx* ctx, const float* d_xyz, const int64_t* h_p
                           static_cast<cudaStream_t>(stream), h_method);
 }
 
-int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off,
-                             int32_t B, const int32_t* h_C, const int32_t* h_M,
-                             const int32_t* h_win, const int64_t* h_start,
-                             const int64_t* h_out_off, int32_t* h_out, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// afps_sample_batched_host(_async).  Page-locked buffers: a cached graph
+// (AFPS_FLAG_GRAPH) or, when the buffers are mapped, direct launches whose
+// kernels read the points and write the indices in host memory; otherwise
+// copies through context-owned device staging (pageable memory: sync only).
+int host_call(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off, int32_t B,
+              const int32_t* h_C, const int32_t* h_M, const int32_t* h_win,
+              const int64_t* h_start, const int64_t* h_out_off, int32_t* h_out, void* stream,
+              bool sync, const char* name) {
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     if (!h_xyz || !h_out || !h_pt_off || !h_out_off || B < 1)
-        return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sample_batched_host: NULL argument or B < 1");
+        return fail(ctx, AFPS_ERR_INVALID_ARG, std::string(name) + ": NULL argument or B < 1");
     if (h_pt_off[0] != 0 || h_out_off[0] != 0)
         return fail(ctx, AFPS_ERR_INVALID_ARG,
-                    "afps_sample_batched_host: h_pt_off[0] and h_out_off[0] must be 0");
+                    std::string(name) + ": h_pt_off[0] and h_out_off[0] must be 0");
     DeviceGuard guard(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t xyz_bytes = (size_t)h_pt_off[B] * 3 * sizeof(float);
     const size_t out_bytes = (size_t)h_out_off[B] * sizeof(int32_t);
-    if ((ctx->flags & AFPS_FLAG_GRAPH) && is_pinned(h_xyz) && is_pinned(h_out))
+    const bool pinned = is_pinned(h_xyz) && is_pinned(h_out);
+    if (!sync && !pinned)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, std::string(name) + ": needs page-locked buffers");
+    if ((ctx->flags & AFPS_FLAG_GRAPH) && pinned)
         return host_graph_call(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
-                               h_out, xyz_bytes, out_bytes, st);
+                               h_out, xyz_bytes, out_bytes, st, sync);
+    if (pinned) {
+        void* dx = nullptr;
+        void* dout = nullptr;
+        const bool mapped =
+            cudaHostGetDevicePointer(&dx, const_cast<float*>(h_xyz), 0) == cudaSuccess &&
+            cudaHostGetDevicePointer(&dout, h_out, 0) == cudaSuccess && dx && dout;
+        cudaGetLastError();
+        if (mapped) {
+            int rc = batched_device(ctx, static_cast<const float*>(dx), h_pt_off, B, h_C, h_M,
+                                    h_win, h_start, h_out_off, static_cast<int32_t*>(dout), st,
+                                    nullptr, true);
+            if (rc != AFPS_OK) return rc;
+            if (sync) AFPS_CUDA(ctx, cudaStreamSynchronize(st));
+            return AFPS_OK;
+        }
+    }
     AFPS_CUDA(ctx, ctx->xyz_stage.reserve(xyz_bytes));
     AFPS_CUDA(ctx, ctx->out_stage.reserve(out_bytes));
     AFPS_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_done, 0));
@@ -1054,8 +1082,28 @@ int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h
     }
     AFPS_CUDA(ctx, cudaMemcpyAsync(h_out, ctx->out_stage.p, out_bytes, cudaMemcpyDeviceToHost, st));
     AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, st));
-    AFPS_CUDA(ctx, cudaStreamSynchronize(st));
+    if (sync) AFPS_CUDA(ctx, cudaStreamSynchronize(st));
     return AFPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off,
+                             int32_t B, const int32_t* h_C, const int32_t* h_M,
+                             const int32_t* h_win, const int64_t* h_start,
+                             const int64_t* h_out_off, int32_t* h_out, void* stream) {
+    return host_call(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, h_out, stream,
+                     true, "afps_sample_batched_host");
+}
+
+int afps_sample_batched_host_async(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off,
+                                   int32_t B, const int32_t* h_C, const int32_t* h_M,
+                                   const int32_t* h_win, const int64_t* h_start,
+                                   const int64_t* h_out_off, int32_t* h_out, void* stream) {
+    return host_call(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, h_out, stream,
+                     false, "afps_sample_batched_host_async");
 }
 
 int afps_gather_levels(afps_ctx* ctx, int32_t B, const int64_t* h_in_pt_off,

@@ -393,6 +393,34 @@ def test_host_buffers_match_device(S, objects):
         assert_same(h_out[ba.out_off[b]:ba.out_off[b + 1]], oracle.afps(P, 512, 16, 16), f"cloud {b}")
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_host_buffers_async_pipelined(objects, graph):
+    """afps_sample_batched_host_async: several calls queued back to back on
+    page-locked buffers (inputs rotating over three, one output each), one
+    synchronisation at the end; every output must be its own batch's."""
+    build_mod.build()
+    s = B.Sampler(0, graph=graph)
+    try:
+        sets = [objects[:8], objects[8:16], objects[16:24]]
+        packs = [synth.pack(c) for c in sets]
+        ba = B.BatchArgs(packs[0][1], 512, 32, 16, 0)
+        hx = [torch.from_numpy(p[0]).pin_memory().numpy() for p in packs]
+        ho = [torch.full((ba.total_out,), -1, dtype=torch.int32).pin_memory().numpy()
+              for _ in range(12)]
+        for j, o in enumerate(ho):
+            s.sample_batched_host_async(hx[j % 3], ba, o)
+        s.sync()
+        for j, o in enumerate(ho):
+            for b in (0, 7):
+                assert_same(o[ba.out_off[b]:ba.out_off[b + 1]],
+                            oracle.afps(sets[j % 3][b], 512, 32, 16), f"call {j} cloud {b}")
+        with pytest.raises(B.AfpsError) as ei:  # pageable buffers cannot be queued
+            s.sample_batched_host_async(packs[0][0], ba, np.zeros(ba.total_out, dtype=np.int32))
+        assert ei.value.code == B.AFPS_ERR_INVALID_ARG
+    finally:
+        s.close()
+
+
 def test_host_buffers_graph_replay(objects):
     """Pinned host buffers with graphs: copies and launches replay as one graph."""
     build_mod.build()
