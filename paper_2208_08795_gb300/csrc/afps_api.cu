@@ -739,13 +739,18 @@ int batched_device(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int
 }
 
 // Tuning cache: one line per class, "key kind P W CS occ [skip]".
-bool is_pinned(const void* p) {
+// Page-locked host memory: true, with *dev its device address when it is
+// mapped into the device's address space (else nullptr).  One driver query.
+bool pinned_address(const void* p, void** dev) {
+    *dev = nullptr;
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeHost;
+    if (at.type != cudaMemoryTypeHost) return false;
+    *dev = at.devicePointer;
+    return true;
 }
 
 // afps_sample_batched_host with pinned buffers and AFPS_FLAG_GRAPH: one graph
@@ -1047,20 +1052,16 @@ int host_call(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off, int32_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t xyz_bytes = (size_t)h_pt_off[B] * 3 * sizeof(float);
     const size_t out_bytes = (size_t)h_out_off[B] * sizeof(int32_t);
-    const bool pinned = is_pinned(h_xyz) && is_pinned(h_out);
+    void* dx = nullptr;
+    void* dout = nullptr;
+    const bool pinned = pinned_address(h_xyz, &dx) && pinned_address(h_out, &dout);
     if (!sync && !pinned)
         return fail(ctx, AFPS_ERR_INVALID_ARG, std::string(name) + ": needs page-locked buffers");
     if ((ctx->flags & AFPS_FLAG_GRAPH) && pinned)
         return host_graph_call(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
                                h_out, xyz_bytes, out_bytes, st, sync);
     if (pinned) {
-        void* dx = nullptr;
-        void* dout = nullptr;
-        const bool mapped =
-            cudaHostGetDevicePointer(&dx, const_cast<float*>(h_xyz), 0) == cudaSuccess &&
-            cudaHostGetDevicePointer(&dout, h_out, 0) == cudaSuccess && dx && dout;
-        cudaGetLastError();
-        if (mapped) {
+        if (dx && dout) {  // mapped: the kernels work in host memory
             int rc = batched_device(ctx, static_cast<const float*>(dx), h_pt_off, B, h_C, h_M,
                                     h_win, h_start, h_out_off, static_cast<int32_t*>(dout), st,
                                     nullptr, true);
