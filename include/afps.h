@@ -405,6 +405,13 @@ int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_confi
  * full. */
 int afps_server_submit(afps_server* srv, const float* h_xyz, int64_t N, uint64_t tag);
 
+/* Queue one frame that already lies in page-locked host memory, without
+ * copying it: admission reads it there by DMA.  The frame must stay
+ * allocated and unchanged until its result has been returned by
+ * afps_server_poll.  Same limits as afps_server_submit; AFPS_ERR_INVALID_ARG
+ * for memory that is not page-locked. */
+int afps_server_submit_pinned(afps_server* srv, const float* h_xyz, int64_t N, uint64_t tag);
+
 /* One continuous-batching step (see above).  Returns the number of requests
  * it advanced by one level (0 when idle), or a negative error. */
 int afps_server_step(afps_server* srv);

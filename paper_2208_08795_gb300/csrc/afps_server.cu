@@ -87,6 +87,7 @@ struct Request {
     uint64_t tag = 0;
     int64_t N = 0;
     Block staged;              // the frame in the page-locked pool until admitted
+    const float* borrowed = nullptr;  // or the caller's page-locked frame (submit_pinned)
     State state = QUEUED;
     int level = 0;             // next level to sample
     Block block;
@@ -319,6 +320,25 @@ int afps_server_submit(afps_server* s, const float* h_xyz, int64_t N, uint64_t t
     return AFPS_OK;
 }
 
+int afps_server_submit_pinned(afps_server* s, const float* h_xyz, int64_t N, uint64_t tag) {
+    if (!s || !h_xyz || N < s->levels[0] || N > 65536) return AFPS_ERR_INVALID_ARG;
+    if (footprint(s, N) > s->cfg.hbm_budget_bytes) return AFPS_ERR_INVALID_ARG;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h_xyz) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return AFPS_ERR_INVALID_ARG;
+    }
+    if ((int64_t)s->queue.size() >= s->cfg.max_queued) return AFPS_ERR_BUSY;
+    std::unique_ptr<Request> r(new (std::nothrow) Request());
+    if (!r) return AFPS_ERR_NO_MEMORY;
+    r->tag = tag;
+    r->N = N;
+    r->borrowed = h_xyz;
+    r->t_submit = s->now();
+    s->queue.push_back(std::move(r));
+    return AFPS_OK;
+}
+
 int afps_server_step(afps_server* s) {
     if (!s) return AFPS_ERR_INVALID_ARG;
     // stay at most max_steps_ahead steps ahead of the GPU
@@ -343,12 +363,14 @@ int afps_server_step(afps_server* s) {
     while (!s->queue.empty() && (int)s->active.size() < s->cfg.max_inflight) {
         Request& r = *s->queue.front();
         if (!admit_one(s, r)) break;
-        if (cudaMemcpyAsync(xyz + 3 * r.xyz_pt[0], s->pool_base + r.staged.off,
-                            (size_t)(12 * r.N), cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+        const void* src = r.borrowed ? static_cast<const void*>(r.borrowed)
+                                     : static_cast<const void*>(s->pool_base + r.staged.off);
+        if (cudaMemcpyAsync(xyz + 3 * r.xyz_pt[0], src, (size_t)(12 * r.N),
+                            cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
             cudaGetLastError();
             return AFPS_ERR_CUDA;
         }
-        copied.push_back(r.staged);
+        if (!r.borrowed) copied.push_back(r.staged);
         r.staged = Block{};
         s->active.push_back(std::move(s->queue.front()));
         s->queue.pop_front();

@@ -19,8 +19,11 @@ def poisson_arrivals(rate_hz: float, n: int, seed: int) -> np.ndarray:
 
 
 def poisson_run(server, frames, rate_hz: float, n_requests: int, seed: int = 0,
-                keep_results: bool = False, max_wall_s: float = 60.0):
+                keep_results: bool = False, max_wall_s: float = 60.0, pinned: bool = False):
+    """pinned=True: `frames` lie in page-locked memory and are submitted
+    without a copy (Server.submit_pinned); they outlive the run."""
     arrivals = poisson_arrivals(rate_hz, n_requests, seed)
+    submit = server.submit_pinned if pinned else server.submit
     t0 = server.clock_ms()
     done = {}
     i = 0
@@ -29,7 +32,7 @@ def poisson_run(server, frames, rate_hz: float, n_requests: int, seed: int = 0,
     while len(done) < n_requests:
         now = server.clock_ms() - t0
         while i < n_requests and arrivals[i] <= now:
-            rc = server.submit(frames[i % len(frames)], i)
+            rc = submit(frames[i % len(frames)], i)
             if rc != 0:
                 break  # queue full: retry on the next turn
             i += 1

@@ -120,3 +120,23 @@ def test_host_pool_recycles_blocks(sampler):
         ref = oracle.chain(frames[t], LEVELS, 32, 16)
         for l in range(len(LEVELS)):
             assert np.array_equal(done[t].levels[l], ref[l]), (t, l)
+
+
+def test_pinned_frames_without_copy(sampler):
+    """submit_pinned: page-locked frames are read in place at admission; a
+    Poisson stream over them matches the oracle, and pageable memory is
+    refused."""
+    torch = pytest.importorskip("torch")
+    frames = [synth.lidar_frame(s) for s in range(4)]
+    pinned = [torch.from_numpy(f).pin_memory().numpy() for f in frames]
+    srv = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=64 << 20)
+    try:
+        assert srv.submit_pinned(frames[0], 0) == B.AFPS_ERR_INVALID_ARG  # pageable
+        res = serving.poisson_run(srv, pinned, rate_hz=4000.0, n_requests=40, seed=2,
+                                  keep_results=True, pinned=True)
+    finally:
+        srv.close()
+    for t in (0, 1, 2, 3, 17):
+        ref = oracle.chain(frames[t % 4], LEVELS, 32, 16)
+        for l in range(len(LEVELS)):
+            assert np.array_equal(res["results"][t].levels[l], ref[l]), (t, l)
