@@ -82,7 +82,9 @@ typedef struct afps_config {
     uint32_t flags;         /* AFPS_FLAG_* */
     int64_t timeout_ns;     /* bound on each device-side wait; <= 0: 2 s */
     const char* tune_cache; /* autotuner cache file (read at create, written
-                               by afps_save_tuning), or NULL */
+                               by afps_save_tuning with a "# device" line
+                               naming the GPU; a file from another kind of
+                               GPU is ignored), or NULL */
 } afps_config;
 
 /*

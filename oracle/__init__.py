@@ -32,10 +32,13 @@ _lock = threading.Lock()
 _lib = None
 
 
-def compile_oracle(source: str = SOURCE, output: str = LIBRARY, werror: bool = True) -> str:
-    """Compile the oracle C source into a shared library; returns its path."""
+def compile_oracle(source: str = SOURCE, output: str = LIBRARY, werror: bool = True,
+                   extra_flags=()) -> str:
+    """Compile the oracle C source into a shared library; returns its path.
+    ``extra_flags`` are added to the compiler line (sanitizer builds)."""
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-std=c11", "-Wall"] + (["-Werror"] if werror else []) + ["-o", output, source, "-lm"]
+           "-std=c11", "-Wall"] + (["-Werror"] if werror else []) + list(extra_flags) + \
+          ["-o", output, source, "-lm"]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
     return output
 

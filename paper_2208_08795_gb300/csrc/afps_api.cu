@@ -17,6 +17,7 @@
 
 #include "../../include/afps.h"
 #include "afps_internal.h"
+#include "afps_trace.h"
 
 using afps::ItemDesc;
 using afps::LaunchArgs;
@@ -811,12 +812,33 @@ int host_graph_call(afps_ctx* ctx, const float* h_xyz, const int64_t* pt_off, in
     return AFPS_OK;
 }
 
+// The device a tuning file belongs to: name, SM count and compute capability.
+std::string device_signature(int device) {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::ostringstream os;
+    for (const char* c = prop.name; *c; ++c) os << (*c == ' ' ? '_' : *c);
+    os << " sms=" << prop.multiProcessorCount << " cc=" << prop.major << '.' << prop.minor;
+    return os.str();
+}
+
+// Tuning file: a "# device <signature>" line, then one line per class,
+// "key kind P W CS occ skip".  A file written on another kind of device is
+// ignored (its variants would be valid but not tuned for this one).
 int load_tuning(afps_ctx* ctx, const std::string& path) {
     std::ifstream f(path);
     if (!f) return 0;
     std::string line;
     int n = 0;
+    const std::string want = "# device " + device_signature(ctx->device);
     while (std::getline(f, line)) {
+        if (line.rfind("# device ", 0) == 0) {
+            if (line != want) return 0;
+            continue;
+        }
         std::istringstream is(line);
         std::string key;
         Variant v{};
@@ -959,12 +981,14 @@ void afps_destroy(afps_ctx* ctx) {
 
 int afps_sample(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int32_t M,
                 int32_t npdu_window, int64_t start_idx, int32_t* d_out, void* stream) {
+    AFPS_TRACE("afps_sample");
     return afps_sample_ex(ctx, d_xyz, N, C, M, npdu_window, start_idx, 0u, d_out, stream);
 }
 
 int afps_sample_ex(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int32_t M,
                    int32_t npdu_window, int64_t start_idx, uint32_t method, int32_t* d_out,
                    void* stream) {
+    AFPS_TRACE("afps_sample_ex");
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     if (method > AFPS_METHOD_ALL)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sample_ex: unknown method bits");
@@ -1012,6 +1036,7 @@ int afps_sample_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_o
                         const int32_t* h_C, const int32_t* h_M, const int32_t* h_win,
                         const int64_t* h_start, const int64_t* h_out_off, int32_t* d_out,
                         void* stream) {
+    AFPS_TRACE("afps_sample_batched");
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     DeviceGuard guard(ctx->device);
     return batched_device(ctx, d_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, d_out,
@@ -1023,6 +1048,7 @@ int afps_sample_batched_ex(afps_ctx* ctx, const float* d_xyz, const int64_t* h_p
                            const int32_t* h_win, const int64_t* h_start,
                            const uint32_t* h_method, const int64_t* h_out_off, int32_t* d_out,
                            void* stream) {
+    AFPS_TRACE("afps_sample_batched_ex");
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     if (!h_method) return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sample_batched_ex: NULL h_method");
     DeviceGuard guard(ctx->device);
@@ -1095,6 +1121,7 @@ int afps_sample_batched_host(afps_ctx* ctx, const float* h_xyz, const int64_t* h
                              int32_t B, const int32_t* h_C, const int32_t* h_M,
                              const int32_t* h_win, const int64_t* h_start,
                              const int64_t* h_out_off, int32_t* h_out, void* stream) {
+    AFPS_TRACE("afps_sample_batched_host");
     return host_call(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, h_out, stream,
                      true, "afps_sample_batched_host");
 }
@@ -1103,6 +1130,7 @@ int afps_sample_batched_host_async(afps_ctx* ctx, const float* h_xyz, const int6
                                    int32_t B, const int32_t* h_C, const int32_t* h_M,
                                    const int32_t* h_win, const int64_t* h_start,
                                    const int64_t* h_out_off, int32_t* h_out, void* stream) {
+    AFPS_TRACE("afps_sample_batched_host_async");
     return host_call(ctx, h_xyz, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, h_out, stream,
                      false, "afps_sample_batched_host_async");
 }
@@ -1111,6 +1139,7 @@ int afps_gather_levels(afps_ctx* ctx, int32_t B, const int64_t* h_in_pt_off,
                        const float* d_in_xyz, const int32_t* d_in_frame,
                        const int64_t* h_sel_off, const int32_t* d_sel, float* d_out_xyz,
                        int32_t* d_out_frame, int32_t* d_sel_frame, void* stream) {
+    AFPS_TRACE("afps_gather_levels");
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     if (B < 1 || !h_in_pt_off || !h_sel_off || !d_in_xyz || !d_sel || !d_out_xyz)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_gather_levels: NULL argument or B < 1");
@@ -1136,6 +1165,7 @@ int afps_gather_levels(afps_ctx* ctx, int32_t B, const int64_t* h_in_pt_off,
 
 int afps_sort_by_key(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
                      int32_t key, float* d_xyz_sorted, int32_t* d_perm, void* stream) {
+    AFPS_TRACE("afps_sort_by_key");
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     if (B < 1 || !h_pt_off || !d_xyz || !d_xyz_sorted || !d_perm || key < AFPS_KEY_X ||
         key > AFPS_KEY_AZIMUTH || h_pt_off[0] < 0)
@@ -1174,6 +1204,7 @@ int afps_sort_by_key(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const fl
 int afps_coverage_radius(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
                          const int64_t* h_sel_off, const int32_t* d_sel, double* d_radius,
                          void* stream) {
+    AFPS_TRACE("afps_coverage_radius");
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     if (B < 1 || B > 65535 || !h_pt_off || !h_sel_off || !d_xyz || !d_sel || !d_radius)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_coverage_radius: bad argument (1 <= B <= 65535)");
@@ -1209,6 +1240,7 @@ int afps_coverage_radius(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, cons
 int afps_ball_query(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
                     const int64_t* h_sel_off, const int32_t* d_sel, float radius, int32_t K,
                     int32_t sorted_axis, int32_t* d_group, void* stream) {
+    AFPS_TRACE("afps_ball_query");
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     if (B < 1 || B > 65535 || !h_pt_off || !h_sel_off || !d_xyz || !d_sel || !d_group ||
         !(radius > 0.f) || K < 1 || sorted_axis < -1 || sorted_axis > 2)
@@ -1246,6 +1278,7 @@ int afps_ball_query(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const flo
 int afps_knn(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_xyz,
              const int64_t* h_sel_off, const int32_t* d_sel, int32_t K, int32_t sorted_axis,
              int32_t* d_group, float* d_dist2, void* stream) {
+    AFPS_TRACE("afps_knn");
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     if (B < 1 || B > 65535 || !h_pt_off || !h_sel_off || !d_xyz || !d_sel || !d_group || K < 1 ||
         K > 64 || sorted_axis < -1 || sorted_axis > 2)
@@ -1279,6 +1312,7 @@ int afps_knn(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const float* d_x
 }
 
 int afps_sync(afps_ctx* ctx, void* stream) {
+    AFPS_TRACE("afps_sync");
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     DeviceGuard guard(ctx->device);
     AFPS_CUDA(ctx, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
@@ -1304,6 +1338,7 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
                           const int32_t* h_C, const int32_t* h_M, const int32_t* h_win,
                           const int64_t* h_start, const int64_t* h_out_off, int32_t* d_out,
                           void* stream) {
+    AFPS_TRACE("afps_autotune_batched");
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     if (!d_xyz || !d_out) return fail(ctx, AFPS_ERR_INVALID_ARG, "autotune: NULL device pointer");
     DeviceGuard guard(ctx->device);
@@ -1370,6 +1405,7 @@ int afps_save_tuning(afps_ctx* ctx, const char* path) {
     if (p.empty()) return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_save_tuning: no path");
     std::ofstream f(p);
     if (!f) return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_save_tuning: cannot open " + p);
+    f << "# device " << device_signature(ctx->device) << '\n';
     for (const auto& kv : ctx->tuned)
         f << kv.first << ' ' << kv.second.kind << ' ' << kv.second.P << ' ' << kv.second.W << ' '
           << kv.second.CS << ' ' << kv.second.occ << ' ' << kv.second.skip << '\n';

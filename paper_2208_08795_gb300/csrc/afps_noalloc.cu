@@ -22,6 +22,7 @@
 
 #include "../../include/afps.h"
 #include "afps_internal.h"
+#include "afps_trace.h"
 
 namespace {
 
@@ -127,6 +128,7 @@ extern "C" int afps_sample_batched_noalloc(const float* d_xyz, const int64_t* h_
                                            const int32_t* h_win, const int64_t* h_start,
                                            const int64_t* h_out_off, int32_t* d_out,
                                            void* stream) {
+    AFPS_TRACE("afps_sample_batched_noalloc");
     if (!d_xyz || !d_out || B < 1 || !h_pt_off || !h_C || !h_M || !h_win || !h_start ||
         !h_out_off)
         return AFPS_ERR_INVALID_ARG;

@@ -23,6 +23,7 @@
 
 #include "../../include/afps.h"
 #include "afps_internal.h"
+#include "afps_trace.h"
 
 namespace afps {
 // afps_api.cu: reserve the context's shared workspace for tables of `bytes`.
@@ -294,6 +295,7 @@ int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_confi
 }
 
 int afps_server_submit(afps_server* s, const float* h_xyz, int64_t N, uint64_t tag) {
+    AFPS_TRACE("afps_server_submit");
     if (!s || !h_xyz || N < s->levels[0] || N > 65536) return AFPS_ERR_INVALID_ARG;
     if (footprint(s, N) > s->cfg.hbm_budget_bytes) return AFPS_ERR_INVALID_ARG;
     if ((int64_t)s->queue.size() >= s->cfg.max_queued) return AFPS_ERR_BUSY;
@@ -321,6 +323,7 @@ int afps_server_submit(afps_server* s, const float* h_xyz, int64_t N, uint64_t t
 }
 
 int afps_server_submit_pinned(afps_server* s, const float* h_xyz, int64_t N, uint64_t tag) {
+    AFPS_TRACE("afps_server_submit_pinned");
     if (!s || !h_xyz || N < s->levels[0] || N > 65536) return AFPS_ERR_INVALID_ARG;
     if (footprint(s, N) > s->cfg.hbm_budget_bytes) return AFPS_ERR_INVALID_ARG;
     cudaPointerAttributes at{};
@@ -340,6 +343,7 @@ int afps_server_submit_pinned(afps_server* s, const float* h_xyz, int64_t N, uin
 }
 
 int afps_server_step(afps_server* s) {
+    AFPS_TRACE("afps_server_step");
     if (!s) return AFPS_ERR_INVALID_ARG;
     // stay at most max_steps_ahead steps ahead of the GPU
     while ((int)s->step_events.size() >= s->cfg.max_steps_ahead) {
@@ -454,6 +458,7 @@ int afps_server_step(afps_server* s) {
 }
 
 int afps_server_poll(afps_server* s, afps_server_result* out, int32_t max_results) {
+    AFPS_TRACE("afps_server_poll");
     if (!s || (!out && max_results > 0)) return AFPS_ERR_INVALID_ARG;
     // results handed out by the previous poll give their slots back now
     for (auto& r : s->handed) s->free_slots.push_back(r->slot);

@@ -495,6 +495,33 @@ def test_autotune_on_first_use(objects, tmp_path):
         s.close()
 
 
+def test_tuning_file_names_its_device(tmp_path):
+    """A saved tuning file names the GPU; a file naming another GPU is ignored,
+    one naming this GPU (or none) is used."""
+    build_mod.build()
+    key = "npdu:n64:c16:i1024"
+    forced = f"{key} 0 2 8 1 0 1\n"
+    path = tmp_path / "t.txt"
+    s = B.Sampler(0, tune_cache=str(path))
+    try:
+        default = s.describe_plan(64, 16, 16, 1024)
+        assert default != "warp P=2 W=8 skip"  # the untuned choice differs from the forced one
+        assert B.afps_save_tuning(s.ctx, None) == 0
+        header = path.read_text().splitlines()[0]
+        assert header.startswith("# device ") and "sms=" in header
+    finally:
+        s.close()
+    for text, expect_forced in ((header + "\n" + forced, True), (forced, True),
+                                ("# device Other_GPU sms=1 cc=1.0\n" + forced, False)):
+        path.write_text(text)
+        s = B.Sampler(0, tune_cache=str(path))
+        try:
+            got = s.describe_plan(64, 16, 16, 1024)
+            assert got == ("warp P=2 W=8 skip" if expect_forced else default), (text, got)
+        finally:
+            s.close()
+
+
 def test_cached_plan_with_new_buffers(objects):
     """Without graphs a repeated argument set reuses its plan: other device
     buffers and other points must still give each set's own result, also
