@@ -369,6 +369,11 @@ int afps_sample_batched_noalloc(const float* d_xyz, const int64_t* h_pt_off, int
  * -------------------------------------------------------------------------- */
 #define AFPS_SERVER_MAX_LEVELS 8
 #define AFPS_ERR_BUSY (-8) /* afps_server_submit: the host queue is full */
+/* afps_sync: a device-side index check failed (libraries built with
+ * AFPS_DEBUG_CHECKS only: every sampling kernel checks its sector sizes and
+ * indices, records a failure in the status word and clamps the index, so no
+ * access leaves its buffer; the regular build compiles the checks out). */
+#define AFPS_ERR_DEVICE_CHECK (-9)
 
 typedef struct afps_server afps_server;
 

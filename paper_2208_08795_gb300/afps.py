@@ -56,6 +56,7 @@ class AfpsError(RuntimeError):
 
 
 AFPS_ERR_BUSY = -8
+AFPS_ERR_DEVICE_CHECK = -9
 AFPS_KEY_X, AFPS_KEY_Y, AFPS_KEY_Z, AFPS_KEY_AZIMUTH = 0, 1, 2, 3
 AFPS_METHOD_FULL_FIRST_PASS = 1
 AFPS_METHOD_WINDOW_HAS_SAMPLE = 2

@@ -13,6 +13,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIBRARY = os.path.join(PKG, "libafps.so")
+# debug build: device-side index checks (AFPS_DEBUG_CHECKS), a library of its own
+BUILD_DIR_DEBUG = os.path.join(PKG, "_build_debug")
+LIBRARY_DEBUG = os.path.join(PKG, "libafps_debug.so")
 HEADER = os.path.join(ROOT, "include", "afps.h")
 SOURCES = ["afps_warp.cu", "afps_cta.cu", "afps_gather.cu", "afps_api.cu", "afps_noalloc.cu",
            "afps_server.cu", "afps_sort.cu", "afps_coverage.cu", "afps_group.cu",
@@ -41,18 +44,22 @@ def _stale(target: str, inputs) -> bool:
     return any(os.path.getmtime(i) > t for i in inputs)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libafps.so if any source changed; returns its path."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile and link libafps.so (debug=True: libafps_debug.so, with the
+    device-side index checks) if any source changed; returns its path."""
+    build_dir = BUILD_DIR_DEBUG if debug else BUILD_DIR
+    library = LIBRARY_DEBUG if debug else LIBRARY
+    flags = NVCC_FLAGS + (["-DAFPS_DEBUG_CHECKS"] if debug else [])
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     deps = _deps()
     objs, procs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + deps):
-            cmd = [nvcc] + NVCC_FLAGS + ["-c", s, "-o", o]
+            cmd = [nvcc] + flags + ["-c", s, "-o", o]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE,
@@ -66,15 +73,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(out, file=sys.stderr)
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    if force or procs or _stale(LIBRARY, objs):
-        tmp = LIBRARY + ".tmp"
+    if force or procs or _stale(library, objs):
+        tmp = library + ".tmp"
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-        os.replace(tmp, LIBRARY)
-    return LIBRARY
+        os.replace(tmp, library)
+    return library
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

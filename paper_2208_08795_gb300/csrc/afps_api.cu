@@ -1320,6 +1320,9 @@ int afps_sync(afps_ctx* ctx, void* stream) {
     AFPS_CUDA(ctx, cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (status != 0) {
         AFPS_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+        if (status == afps::DEV_CHECK_FAILED)
+            return fail(ctx, AFPS_ERR_DEVICE_CHECK,
+                        "a device-side index check failed (debug build); the index was clamped");
         return fail(ctx, AFPS_ERR_TIMEOUT,
                     status == afps::DEV_TIMEOUT_STAGE
                         ? "a stage-in bulk copy did not complete within the timeout"

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
 
     for (int item = group; item < a.n_items; item += ngroups) {
         const ItemDesc d = dev::load_item(a, item);
-        const int n = d.n;
+        const int n = dev::checked(d.n, 1, CS * T * P + 1, a.status);  // fits the CTA(s)
         const int chunk = CLUSTER ? (n + CS - 1) / CS : n;
         const int c0 = rank * chunk;
         const int cn = max(0, min(n - c0, chunk));
@@ -159,11 +159,11 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             Z2[h] = dev::pack2(zs[0], zs[1]);
         }
 
-        int p = d.first;  // sector offset of the current sample
+        int p = dev::checked(d.first, 0, n, a.status);  // sector offset of the current sample
         const float* gq = a.xyz + 3 * (d.src + p);
         float qx = gq[0], qy = gq[1], qz = gq[2];
         int32_t* out = a.out + d.dst;
-        const int c = d.c;
+        const int c = dev::checked(d.c, 1, n + 1, a.status);
         const int kl = d.kl;
         const int kr = d.kr;
         const bool full_first = (d.flags & ITEM_FULL_FIRST) != 0;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         if (tlo + u <= thi) {
-                            const int sj = p + (tlo + u) * q;
+                            const int sj = dev::checked(p + (tlo + u) * q, 0, n, a.status);
                             const float dd = dev::sqdist(px, py, pz, pts[3 * sj],
                                                          pts[3 * sj + 1], pts[3 * sj + 2]);
                             ok = ok && dd < 1e10f;
@@ -313,11 +313,12 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             const unsigned hi = (unsigned)(bkey >> 32), lo = (unsigned)bkey;
             const unsigned mm = __reduce_max_sync(dev::kFull, hi);
             const unsigned lo2 = __reduce_max_sync(dev::kFull, hi == mm ? lo : 0u);
-            p = (int)(0xffffffffu - lo2);
+            p = dev::checked((int)(0xffffffffu - lo2), 0, n, a.status);
             if (CLUSTER) {
                 // the winner's record sits at (owner rank, owner warp)
                 const int r = p / chunk;
-                const int e_star = r * W + (((p - r * chunk) % T) >> 5);
+                const int e_star =
+                    dev::checked(r * W + (((p - r * chunk) % T) >> 5), 0, E, a.status);
                 qx = R[e_star].x;
                 qy = R[e_star].y;
                 qz = R[e_star].z;

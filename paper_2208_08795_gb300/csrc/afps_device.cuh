@@ -153,6 +153,22 @@ __device__ __forceinline__ void record_status(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
 }
 
+// Debug build (AFPS_DEBUG_CHECKS): index v must lie in [lo, hi); otherwise
+// the failure is recorded and v is clamped into the range, so the access it
+// guards stays in bounds.  The regular build returns v unchanged.
+__device__ __forceinline__ int checked(int v, int lo, int hi, int* status) {
+#ifdef AFPS_DEBUG_CHECKS
+    if (v < lo || v >= hi) {
+        record_status(status, DEV_CHECK_FAILED);
+        return v < lo ? lo : hi - 1;
+    }
+#endif
+    (void)lo;
+    (void)hi;
+    (void)status;
+    return v;
+}
+
 // Squared distance with every product and sum rounded on its own (the
 // intrinsics are never contracted into fused multiply-adds).
 __device__ __forceinline__ float sqdist(float x, float y, float z, float qx, float qy,

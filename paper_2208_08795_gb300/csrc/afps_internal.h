@@ -74,6 +74,7 @@ enum DeviceStatus : int {
     DEV_TIMEOUT_STAGE = 1,     // a stage-in bulk copy did not complete in time
     DEV_TIMEOUT_DRAIN = 2,     // ... nor within the second, draining wait
     DEV_TIMEOUT_EXCHANGE = 3,  // a cluster record exchange did not complete in time
+    DEV_CHECK_FAILED = 4,      // a device-side check of the debug build failed
 };
 
 // Points a variant can hold per item.

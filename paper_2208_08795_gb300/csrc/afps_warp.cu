@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
 
     while (item < a.n_items) {
         const ItemDesc d = dev::load_item(a, item);
-        const int n = d.n;
+        const int n = dev::checked(d.n, 1, 32 * P + 1, a.status);  // fits the staging buffer
 
         // ---- stage-in (the previous item's readers are done: fence + sync)
         dev::fence_proxy_async_smem();
@@ -114,11 +114,11 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         }
 
         int32_t* out = a.out + d.dst;
-        const int c = d.c;
+        const int c = dev::checked(d.c, 1, n + 1, a.status);
         const int kl = d.kl;
         const int kr = d.kr;
         const bool full_first = (d.flags & ITEM_FULL_FIRST) != 0;
-        int p = d.first;
+        int p = dev::checked(d.first, 0, n, a.status);
         // sample t's index is kept by lane t % 32 and stored once per 32 samples
         int obuf = lane == 0 ? d.lo + p : 0;
         int t0 = 1;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         if (tlo + u <= thi) {
-                            const int sj = p + (tlo + u) * q;
+                            const int sj = dev::checked(p + (tlo + u) * q, 0, n, a.status);
                             const float dd = dev::sqdist(px, py, pz, pts[3 * sj],
                                                          pts[3 * sj + 1], pts[3 * sj + 2]);
                             ok = ok && dd < 1e10f;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
             const unsigned bits = __float_as_uint(best);
             const unsigned m = __reduce_max_sync(dev::kFull, bits);
             const unsigned cand = bits == m ? (unsigned)(lane + 32 * bi) : 0xffffffffu;
-            p = (int)__reduce_min_sync(dev::kFull, cand);
+            p = dev::checked((int)__reduce_min_sync(dev::kFull, cand), 0, n, a.status);
             obuf = lane == (t & 31) ? d.lo + p : obuf;
             if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
         }
