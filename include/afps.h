@@ -419,6 +419,14 @@ int afps_server_submit(afps_server* srv, const float* h_xyz, int64_t N, uint64_t
  * for memory that is not page-locked. */
 int afps_server_submit_pinned(afps_server* srv, const float* h_xyz, int64_t N, uint64_t tag);
 
+/* Withdraw the request with this tag (the oldest if several): a queued one
+ * is removed at once; an admitted one is left out of the following steps and
+ * its device memory and result slot are reclaimed once the steps already
+ * launched have completed.  A cancelled request is never returned by
+ * afps_server_poll.  AFPS_ERR_INVALID_ARG when no queued or admitted request
+ * has the tag (or its result is already being returned). */
+int afps_server_cancel(afps_server* srv, uint64_t tag);
+
 /* One continuous-batching step (see above).  Returns the number of requests
  * it advanced by one level (0 when idle), or a negative error. */
 int afps_server_step(afps_server* srv);

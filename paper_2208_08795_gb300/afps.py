@@ -41,7 +41,7 @@ EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
            "afps_server_stats", "afps_server_clock_ms", "afps_server_destroy",
            "afps_sort_by_key", "afps_sample_ex", "afps_sample_batched_ex",
            "afps_coverage_radius", "afps_ball_query", "afps_knn",
-           "afps_sample_batched_host_async", "afps_server_submit_pinned")
+           "afps_sample_batched_host_async", "afps_server_submit_pinned", "afps_server_cancel")
 
 
 class AfpsLibraryError(RuntimeError):
@@ -132,6 +132,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.afps_server_submit.restype = ctypes.c_int
     L.afps_server_submit_pinned.argtypes = [vp, vp, i64, ctypes.c_uint64]
     L.afps_server_submit_pinned.restype = ctypes.c_int
+    L.afps_server_cancel.argtypes = [vp, ctypes.c_uint64]
+    L.afps_server_cancel.restype = ctypes.c_int
     L.afps_server_step.argtypes = [vp]
     L.afps_server_step.restype = ctypes.c_int
     L.afps_server_poll.argtypes = [vp, ctypes.POINTER(afps_server_result), i32]
@@ -510,6 +512,10 @@ def afps_server_submit_pinned(srv, h_xyz, N, tag) -> int:
     return load().afps_server_submit_pinned(srv, h_xyz, N, tag)
 
 
+def afps_server_cancel(srv, tag) -> int:
+    return load().afps_server_cancel(srv, tag)
+
+
 def afps_server_step(srv) -> int:
     return load().afps_server_step(srv)
 
@@ -581,6 +587,10 @@ class Server:
         array must stay alive and unchanged until its result is polled."""
         assert xyz.dtype == np.float32 and xyz.flags.c_contiguous
         return afps_server_submit_pinned(self.srv, xyz.ctypes.data, xyz.shape[0], tag)
+
+    def cancel(self, tag: int) -> int:
+        """Withdraw a queued or admitted request (0, or AFPS_ERR_INVALID_ARG)."""
+        return afps_server_cancel(self.srv, tag)
 
     def step(self) -> int:
         rc = afps_server_step(self.srv)

@@ -82,7 +82,7 @@ class Arena {
     int64_t used_ = 0;
 };
 
-enum State { QUEUED, ACTIVE, COMPLETING, DONE };
+enum State { QUEUED, ACTIVE, COMPLETING, DONE, CANCELLED };
 
 struct Request {
     uint64_t tag = 0;
@@ -175,6 +175,12 @@ void reap(afps_server* s) {
             give_event(s, r->done_ev);
             r->done_ev = nullptr;
             s->done.push_back(std::move(r));
+        } else if (r && r->state == CANCELLED && cudaEventQuery(r->done_ev) == cudaSuccess) {
+            // no launched step uses its memory any more: drop it
+            s->arena->release(r->block);
+            give_event(s, r->done_ev);
+            s->free_slots.push_back(r->slot);
+            r.reset();
         }
     }
     s->active.erase(std::remove(s->active.begin(), s->active.end(), nullptr), s->active.end());
@@ -340,6 +346,35 @@ int afps_server_submit_pinned(afps_server* s, const float* h_xyz, int64_t N, uin
     r->t_submit = s->now();
     s->queue.push_back(std::move(r));
     return AFPS_OK;
+}
+
+int afps_server_cancel(afps_server* s, uint64_t tag) {
+    AFPS_TRACE("afps_server_cancel");
+    if (!s) return AFPS_ERR_INVALID_ARG;
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        if ((*it)->tag == tag) {  // not admitted: nothing on the device yet
+            s->pool->release((*it)->staged);
+            s->queue.erase(it);
+            return AFPS_OK;
+        }
+    }
+    for (auto& r : s->active) {
+        if (r && r->tag == tag && r->state == ACTIVE) {
+            // later steps leave it out; its memory is freed once every step
+            // launched so far (all before this event) has completed
+            cudaEvent_t e = take_event(s);
+            if (!e) return AFPS_ERR_CUDA;
+            if (cudaEventRecord(e, s->stream) != cudaSuccess) {
+                cudaGetLastError();
+                give_event(s, e);
+                return AFPS_ERR_CUDA;
+            }
+            r->state = CANCELLED;
+            r->done_ev = e;
+            return AFPS_OK;
+        }
+    }
+    return AFPS_ERR_INVALID_ARG;
 }
 
 int afps_server_step(afps_server* s) {

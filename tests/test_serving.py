@@ -140,3 +140,32 @@ def test_pinned_frames_without_copy(sampler):
         ref = oracle.chain(frames[t % 4], LEVELS, 32, 16)
         for l in range(len(LEVELS)):
             assert np.array_equal(res["results"][t].levels[l], ref[l]), (t, l)
+
+
+def test_cancel_queued_and_admitted(sampler):
+    """Withdrawing a queued and an admitted request: the others still match
+    the oracle, the withdrawn ones never come back, and all device memory
+    and result slots are returned."""
+    frames = [synth.lidar_frame(s) for s in range(8)]
+    srv = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=3_000_000)  # about three at once
+    try:
+        for t, f in enumerate(frames):
+            assert srv.submit(f, t) == 0
+        srv.step()  # admits the first few and advances them one level
+        assert srv.cancel(1) == 0  # admitted
+        assert srv.cancel(6) == 0  # still queued
+        assert srv.cancel(6) == B.AFPS_ERR_INVALID_ARG  # already withdrawn
+        assert srv.cancel(99) == B.AFPS_ERR_INVALID_ARG
+        done = drain(srv, len(frames) - 2)
+        for _ in range(4):
+            srv.step()
+            assert not srv.poll()
+        q, inflight, used = srv.stats()
+        assert (q, inflight, used) == (0, 0, 0)
+    finally:
+        srv.close()
+    assert sorted(done) == [t for t in range(8) if t not in (1, 6)]
+    for t in (0, 2, 7):
+        ref = oracle.chain(frames[t], LEVELS, 32, 16)
+        for l in range(len(LEVELS)):
+            assert np.array_equal(done[t].levels[l], ref[l]), (t, l)
