@@ -359,11 +359,12 @@ int afps_sample_batched_noalloc(const float* d_xyz, const int64_t* h_pt_off, int
  * emission (sector-major) order.
  *
  * Each afps_server_step admits queued requests while the device arena (the
- * HBM budget) and the slot count allow, then launches one batched sampling
- * call over the current level of every admitted request, one gather that
- * builds every next-level cloud on the device, and device-to-host copies of
- * finished results.  Requests at different levels share each launch; a
- * request admitted while others are on the GPU joins the next step.  Frames
+ * HBM budget) and the slot count allow, then, levels_per_step times (default:
+ * as many as there are levels), launches one batched sampling call over the
+ * current level of every admitted request and one gather that builds every
+ * next-level cloud on the device, and copies finished results to the host.
+ * Requests at different levels share each launch; a request admitted while
+ * others are on the GPU joins the next step.  Frames
  * and level clouds stay resident in the arena until their request finishes.
  * The host runs at most max_steps_ahead steps ahead of the GPU.
  * -------------------------------------------------------------------------- */
@@ -386,7 +387,8 @@ typedef struct afps_server_config {
     int32_t M;                 /* sectors per level (capped at the level's size) */
     int32_t npdu_window;       /* k >= 0 (0 = no NPDU) */
     int32_t max_steps_ahead;   /* <= 0: 2 */
-    int32_t pad;
+    int32_t levels_per_step;   /* levels a step advances each admitted request by;
+                                  <= 0: all (a request admitted by a step completes in it) */
     int64_t host_pool_bytes;   /* page-locked staging for queued frames; <= 0: 64 MiB */
 } afps_server_config;
 
@@ -427,8 +429,9 @@ int afps_server_submit_pinned(afps_server* srv, const float* h_xyz, int64_t N, u
  * has the tag (or its result is already being returned). */
 int afps_server_cancel(afps_server* srv, uint64_t tag);
 
-/* One continuous-batching step (see above).  Returns the number of requests
- * it advanced by one level (0 when idle), or a negative error. */
+/* One continuous-batching step (see above).  Returns the number of
+ * single-level advances it made (requests times levels; 0 when idle), or a
+ * negative error. */
 int afps_server_step(afps_server* srv);
 
 /* Move up to max_results finished requests into out; returns how many. */

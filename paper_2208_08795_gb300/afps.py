@@ -68,7 +68,7 @@ class afps_server_config(ctypes.Structure):
                 ("max_inflight", ctypes.c_int32), ("n_levels", ctypes.c_int32),
                 ("levels", ctypes.c_int32 * AFPS_SERVER_MAX_LEVELS), ("M", ctypes.c_int32),
                 ("npdu_window", ctypes.c_int32), ("max_steps_ahead", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("host_pool_bytes", ctypes.c_int64)]
+                ("levels_per_step", ctypes.c_int32), ("host_pool_bytes", ctypes.c_int64)]
 
 
 class afps_server_result(ctypes.Structure):
@@ -553,7 +553,7 @@ class Server:
 
     def __init__(self, sampler: "Sampler", levels, M: int, k: int, hbm_budget_bytes: int,
                  max_inflight: int = 256, max_queued: int = 4096, max_steps_ahead: int = 2,
-                 host_pool_bytes: int = 0, stream=None):
+                 host_pool_bytes: int = 0, levels_per_step: int = 0, stream=None):
         cfg = afps_server_config()
         cfg.hbm_budget_bytes = int(hbm_budget_bytes)
         cfg.max_queued = int(max_queued)
@@ -563,6 +563,7 @@ class Server:
             cfg.levels[i] = int(c)
         cfg.M, cfg.npdu_window, cfg.max_steps_ahead = int(M), int(k), int(max_steps_ahead)
         cfg.host_pool_bytes = int(host_pool_bytes)
+        cfg.levels_per_step = int(levels_per_step)
         self.sampler = sampler
         self.srv = afps_server_create(sampler.ctx, cfg, stream)
         self._buf = (afps_server_result * 256)()

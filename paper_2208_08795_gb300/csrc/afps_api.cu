@@ -29,7 +29,7 @@ namespace {
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
 constexpr size_t kMaxGraphs = 512;  // cached graphs per context (least recently used evicted)
 constexpr size_t kMaxPlans = 256;   // cached batch plans per context (cleared when full)
-constexpr int kStageSlots = 4;  // pinned upload buffers in flight
+constexpr int kStageSlots = 16;  // pinned upload buffers in flight
 
 // ---------------------------------------------------------------- buffers
 struct DevBuf {

@@ -420,76 +420,84 @@ int afps_server_step(afps_server* s) {
         s->pool_pending.emplace_back(ce, std::move(copied));
     }
 
-    // one batched sampling launch over every active request's current level
-    std::vector<Request*> run;
-    for (auto& r : s->active)
-        if (r->state == ACTIVE) run.push_back(r.get());
-    if (run.empty()) return 0;
-    const int32_t B = (int32_t)run.size();
-    std::vector<int64_t> pt_begin(B), n_pts(B), start(B, 0), out_begin(B);
-    std::vector<int32_t> C(B), M(B), K(B, s->cfg.npdu_window);
-    std::vector<afps::GatherDesc> g(B);
-    for (int32_t b = 0; b < B; ++b) {
-        Request& r = *run[b];
-        const int l = r.level;
-        const int64_t n = l == 0 ? r.N : s->levels[l - 1];
-        pt_begin[b] = r.xyz_pt[l];
-        n_pts[b] = n;
-        C[b] = s->levels[l];
-        M[b] = std::min(s->cfg.M, C[b]);
-        out_begin[b] = r.out_el[l];
-        afps::GatherDesc& d = g[b];
-        d.in_xyz = r.xyz_pt[l];
-        d.in_frame = r.fidx_el[l];  // -1 at level 0: the frame itself
-        d.sel = r.out_el[l];
-        d.out_xyz = r.xyz_pt[l + 1];
-        d.out_frame = l + 1 < s->cfg.n_levels ? r.fidx_el[l + 1] : -1;
-        int64_t res = r.res_el;
-        for (int q = 0; q < l; ++q) res += s->levels[q];
-        d.sel_frame = res;
-        d.n = (int32_t)n;
-        d.c = C[b];
-    }
-    int rc = afps::sample_scattered(s->ctx, xyz, B, pt_begin.data(), n_pts.data(), C.data(),
-                                    M.data(), K.data(), start.data(), ints, out_begin.data(),
-                                    s->stream);
-    if (rc != AFPS_OK) return rc;
-    rc = afps::gather_run(s->ctx, g.data(), B, xyz, ints, ints, xyz, ints, ints, s->stream);
-    if (rc != AFPS_OK) return rc;
-
-    // finished chains: copy their results to pinned memory
-    cudaEvent_t fin = nullptr;
-    for (Request* r : run) {
-        if (++r->level < s->cfg.n_levels) continue;
-        if (cudaMemcpyAsync(s->pinned + (int64_t)r->slot * s->total_samples, ints + r->res_el,
-                            (size_t)s->total_samples * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                            s->stream) != cudaSuccess) {
-            cudaGetLastError();
-            return AFPS_ERR_CUDA;
+    // level after level: one batched sampling launch over every active
+    // request's current level (mixed levels share it), then the gather
+    const int per_step = s->cfg.levels_per_step > 0 ? s->cfg.levels_per_step : s->cfg.n_levels;
+    int advanced = 0;
+    for (int sub = 0; sub < per_step; ++sub) {
+        // one batched sampling launch over every active request's current level
+        std::vector<Request*> run;
+        for (auto& r : s->active)
+            if (r->state == ACTIVE) run.push_back(r.get());
+        if (run.empty()) break;
+        const int32_t B = (int32_t)run.size();
+        std::vector<int64_t> pt_begin(B), n_pts(B), start(B, 0), out_begin(B);
+        std::vector<int32_t> C(B), M(B), K(B, s->cfg.npdu_window);
+        std::vector<afps::GatherDesc> g(B);
+        for (int32_t b = 0; b < B; ++b) {
+            Request& r = *run[b];
+            const int l = r.level;
+            const int64_t n = l == 0 ? r.N : s->levels[l - 1];
+            pt_begin[b] = r.xyz_pt[l];
+            n_pts[b] = n;
+            C[b] = s->levels[l];
+            M[b] = std::min(s->cfg.M, C[b]);
+            out_begin[b] = r.out_el[l];
+            afps::GatherDesc& d = g[b];
+            d.in_xyz = r.xyz_pt[l];
+            d.in_frame = r.fidx_el[l];  // -1 at level 0: the frame itself
+            d.sel = r.out_el[l];
+            d.out_xyz = r.xyz_pt[l + 1];
+            d.out_frame = l + 1 < s->cfg.n_levels ? r.fidx_el[l + 1] : -1;
+            int64_t res = r.res_el;
+            for (int q = 0; q < l; ++q) res += s->levels[q];
+            d.sel_frame = res;
+            d.n = (int32_t)n;
+            d.c = C[b];
         }
-        r->state = COMPLETING;
-        if (!fin) fin = take_event(s);
-    }
-    if (fin) {
-        if (cudaEventRecord(fin, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
-        // each finishing request keeps its own handle on the step's completion
-        bool first = true;
+        int rc = afps::sample_scattered(s->ctx, xyz, B, pt_begin.data(), n_pts.data(), C.data(),
+                                        M.data(), K.data(), start.data(), ints, out_begin.data(),
+                                        s->stream);
+        if (rc != AFPS_OK) return rc;
+        rc = afps::gather_run(s->ctx, g.data(), B, xyz, ints, ints, xyz, ints, ints, s->stream);
+        if (rc != AFPS_OK) return rc;
+
+        // finished chains: copy their results to pinned memory
+        cudaEvent_t fin = nullptr;
         for (Request* r : run) {
-            if (r->state != COMPLETING || r->done_ev) continue;
-            if (first) {
-                r->done_ev = fin;
-                first = false;
-            } else {
-                cudaEvent_t e = take_event(s);
-                if (!e || cudaEventRecord(e, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
-                r->done_ev = e;
+            if (++r->level < s->cfg.n_levels) continue;
+            if (cudaMemcpyAsync(s->pinned + (int64_t)r->slot * s->total_samples, ints + r->res_el,
+                                (size_t)s->total_samples * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                s->stream) != cudaSuccess) {
+                cudaGetLastError();
+                return AFPS_ERR_CUDA;
+            }
+            r->state = COMPLETING;
+            if (!fin) fin = take_event(s);
+        }
+        if (fin) {
+            if (cudaEventRecord(fin, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
+            // each finishing request keeps its own handle on the step's completion
+            bool first = true;
+            for (Request* r : run) {
+                if (r->state != COMPLETING || r->done_ev) continue;
+                if (first) {
+                    r->done_ev = fin;
+                    first = false;
+                } else {
+                    cudaEvent_t e = take_event(s);
+                    if (!e || cudaEventRecord(e, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
+                    r->done_ev = e;
+                }
             }
         }
+        advanced += (int)run.size();
     }
+    if (advanced == 0) return 0;
     cudaEvent_t se = take_event(s);
     if (!se || cudaEventRecord(se, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
     s->step_events.push_back(se);
-    return B;
+    return advanced;
 }
 
 int afps_server_poll(afps_server* s, afps_server_result* out, int32_t max_results) {

@@ -32,10 +32,12 @@ def drain(server, n):
     return done
 
 
-def test_mixed_stream_matches_oracle_and_alone(sampler):
+@pytest.mark.parametrize("levels_per_step", [0, 1, 2])
+def test_mixed_stream_matches_oracle_and_alone(sampler, levels_per_step):
     frames = [synth.lidar_frame(s) for s in range(10)]
     # a budget for about three requests at once: the rest waits for admission
-    srv = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=3_000_000)
+    srv = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=3_000_000,
+                   levels_per_step=levels_per_step)
     try:
         for t, f in enumerate(frames):
             assert srv.submit(f, t) == 0
@@ -147,7 +149,8 @@ def test_cancel_queued_and_admitted(sampler):
     the oracle, the withdrawn ones never come back, and all device memory
     and result slots are returned."""
     frames = [synth.lidar_frame(s) for s in range(8)]
-    srv = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=3_000_000)  # about three at once
+    srv = B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=3_000_000,  # about three at once
+                   levels_per_step=1)
     try:
         for t, f in enumerate(frames):
             assert srv.submit(f, t) == 0
