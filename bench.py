@@ -401,6 +401,39 @@ def large_clouds(sampler, flush, dev, steps: int):
     return {"workload": "slab clouds 8K/16K/32K, C=N/4", "runs": rows}
 
 
+# Table IV of the paper: Transmuter (gem5) seconds, for context only
+PAPER_TABLE_IV = {"fps_s": {2048: 0.0170, 4096: 0.0892, 8192: 0.3028, 16384: 0.6172, 32768: 1.2211},
+                  "npdu_afps_m32_s": {2048: 0.0005, 4096: 0.0007, 8192: 0.0011, 16384: 0.0022,
+                                      32768: 0.0044}}
+
+
+def table_iv(sampler, flush, dev, steps: int):
+    """The paper's size sweep (Table IV, and NPDU on FPS, Sec. IV-D) on one
+    GB300: single slab clouds of N in {2K .. 32K} points sorted by x, C = 512,
+    plain FPS, NPDU-FPS (M = 1, k = 8), AFPS (M = 32) and NPDU-AFPS (M = 32,
+    k = 16); isolated steps after an L2 flush, variants autotuned.  The
+    paper's own times (a simulated 64-core accelerator) are listed beside."""
+    import torch
+    from paper_2208_08795_gb300 import afps as A, synth
+    rows = []
+    for N in (2048, 4096, 8192, 16384, 32768):
+        x = torch.from_numpy(synth.slab_cloud(2, N)).to(dev)
+        row = {"N": N, "C": 512}
+        for name, M, k in (("fps", 1, 0), ("npdu_fps_k8", 1, 8), ("afps_m32", 32, 0),
+                           ("npdu_afps_m32_k16", 32, 16)):
+            ba = A.BatchArgs([0, N], 512, M, k, 0)
+            out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
+            ms, _ = time_batch(sampler, x, ba, out, steps, 3, flush)
+            row[name + "_ms"] = round(ms, 4)
+        for name in ("npdu_fps_k8", "afps_m32", "npdu_afps_m32_k16"):
+            row[name + "_speedup"] = round(row["fps_ms"] / row[name + "_ms"], 1)
+        row["paper_fps_ms"] = PAPER_TABLE_IV["fps_s"][N] * 1e3
+        row["paper_npdu_afps_m32_ms"] = PAPER_TABLE_IV["npdu_afps_m32_s"][N] * 1e3
+        rows.append(row)
+    return {"workload": "single slab clouds, C=512 (Table IV analogue); paper times are a "
+                        "simulated 64-core accelerator, context only", "rows": rows}
+
+
 def ragged_batch(sampler, flush, dev, steps: int):
     """256 object-scale clouds, N ~ U[2048, 32768], C = N/4, M = round(N/256)
     (sectors of about 256 points), NPDU k = 16: all (cloud, sector) items in
@@ -688,6 +721,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     serving_stats = serving_sweep(sampler) if args.serving else None
     extra_steps = max(5, min(args.steps, 20))
     large = large_clouds(sampler, flush, dev, extra_steps) if args.configs else None
+    tab4 = table_iv(sampler, flush, dev, extra_steps) if args.configs else None
     ragged = ragged_batch(sampler, flush, dev, extra_steps) if args.configs else None
     sorting = sort_section(sampler, flush, dev, extra_steps) if args.configs else None
     grouping = group_section(sampler, x, off, flush, dev, extra_steps) if args.configs else None
@@ -746,6 +780,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
                 "sync_call_ms": e2e_call_ms, "sync_call_matches_device_path": e2e_ok},
         "serving": serving_stats,
         "large_clouds": large,
+        "table_iv": tab4,
         "ragged_batch": ragged,
         "sort_by_key": sorting,
         "ball_query": grouping,

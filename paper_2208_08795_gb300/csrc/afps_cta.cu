@@ -103,6 +103,9 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
 
     uint32_t phase = 0;
     uint32_t xchg = 0;  // exchange counter: record buffer parity
+    // cluster stride phase: every CTA's 1e10-test verdict, two alternating buffers
+    __shared__ __align__(16) uint32_t cl_ok[CLUSTER ? 2 : 1][CLUSTER ? 16 : 1][4];
+    uint32_t npro = 0;  // stride phases run (buffer parity)
     const int group = CLUSTER ? (int)dev::cluster_id_x() : (int)blockIdx.x;
     const int ngroups = CLUSTER ? (int)dev::ncluster_x() : (int)gridDim.x;
 
@@ -171,7 +174,10 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
         int obuf = lane == 0 ? d.lo + p : 0;
 
         int t0 = 1;
-        if (NPDU && !CLUSTER && !full_first && p <= kl && kl <= kr) {
+        // (not in the 8-points-per-thread cluster kernel: at 1024 threads its
+        // 64 registers leave no room, and the tuner has its neighbours)
+        constexpr bool kStride = NPDU && !(CLUSTER && P == 8);
+        if (kStride && !full_first && p <= kl && kl <= kr) {  // the same for every CTA of a cluster
             // Stride phase of the literal NPDU reading (Sec. III-C; distances
             // start at 1e10): while points past the last window are untouched
             // they hold the maximum, so the lowest-index argmax is the first of
@@ -180,18 +186,22 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             // at once (with kl <= kr a point lies in at most two windows); the
             // argmax rounds they replace are decided in advance provided every
             // windowed distance is below 1e10, else the serial loop runs from
-            // the start.
+            // the start.  A cluster's CTAs each hold a chunk: the samples'
+            // coordinates come from memory and the 1e10 test is combined
+            // across the cluster.
             const int q = kr + 1;
             const int x = n - 1 - kr - p;
             const int ts = x <= 0 ? 1 : (int)((unsigned)(x + q - 1) / (unsigned)q) + 1;  // stride length
             const int tn = min(ts, c);                        // of them emitted
             const int tw = min(ts, c - 1);                    // whose window is applied
+            const float* G = CLUSTER ? a.xyz + 3 * d.src : pts;  // the sector's points
             bool ok = true;  // D is updated in place and reset if the test fails
 #pragma unroll
             for (int i = 0; i < 2 * PP; ++i) {
-                const int j = tid + T * i;
-                if (i < P && j < n) {
-                    const float px = pts[3 * j], py = pts[3 * j + 1], pz = pts[3 * j + 2];
+                const int jl = tid + T * i;
+                if (i < P && jl < cn) {
+                    const int j = c0 + jl;  // sector-local index
+                    const float px = pts[3 * jl], py = pts[3 * jl + 1], pz = pts[3 * jl + 2];
                     const int y = j - kr - p;
                     // unsigned divisions: both operands are >= 0 (p <= kl)
                     const int tlo = y <= 0 ? 0 : (int)((unsigned)(y + q - 1) / (unsigned)q);
@@ -200,28 +210,40 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
                     for (int u = 0; u < 2; ++u) {
                         if (tlo + u <= thi) {
                             const int sj = dev::checked(p + (tlo + u) * q, 0, n, a.status);
-                            const float dd = dev::sqdist(px, py, pz, pts[3 * sj],
-                                                         pts[3 * sj + 1], pts[3 * sj + 2]);
+                            const float dd = dev::sqdist(px, py, pz, G[3 * sj], G[3 * sj + 1],
+                                                         G[3 * sj + 2]);
                             ok = ok && dd < 1e10f;
                             D[i] = fminf(D[i], dd);
                         }
                     }
                 }
             }
-            if (__syncthreads_and(ok)) {
+            bool all = __syncthreads_and(ok) != 0;
+            if (CLUSTER) {
+                // each CTA's verdict to every peer (buffers alternate between
+                // stride phases), one cluster barrier, then every CTA reads all
+                const int par = npro & 1;
+                if (tid < CS)
+                    dev::st_cluster_v4(dev::mapa(dev::smem_u32(&cl_ok[par][rank][0]), (uint32_t)tid),
+                                       all ? 1u : 0u, 0u, 0u, 0u);
+                dev::cluster_sync();
+                for (int r = 0; r < CS; ++r) all = all && cl_ok[par][r][0] != 0u;
+                ++npro;
+            }
+            if (all) {
                 if (emitter) {
                     for (int r0 = 0; r0 + 32 <= tn; r0 += 32)
                         out[r0 + lane] = d.lo + p + (r0 + lane) * q;
                     obuf = d.lo + p + (((tn - 1) & ~31) + lane) * q;
                 }
                 p += (tn - 1) * q;
-                qx = pts[3 * p];
-                qy = pts[3 * p + 1];
-                qz = pts[3 * p + 2];
+                qx = G[3 * p];
+                qy = G[3 * p + 1];
+                qz = G[3 * p + 2];
                 t0 = tn;  // re-applying the last window is a no-op
             } else {
 #pragma unroll
-                for (int i = 0; i < 2 * PP; ++i) D[i] = (i < P && tid + T * i < n) ? 1e10f : 0.f;
+                for (int i = 0; i < 2 * PP; ++i) D[i] = (i < P && tid + T * i < cn) ? 1e10f : 0.f;
             }
         }
 

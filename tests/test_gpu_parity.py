@@ -212,6 +212,14 @@ def test_forced_variant(tmp_path, row):
         s.close()
 
 
+@pytest.mark.parametrize("N", [2048, 8192, 32768])
+@pytest.mark.parametrize("M,k", [(1, 0), (1, 8), (32, 0), (32, 16)])
+def test_table_iv_sizes(S, N, M, k):
+    """The benchmark's Table IV sweep: single slab clouds, C = 512."""
+    P = synth.slab_cloud(2, N)
+    assert_same(gpu_one(S, P, 512, M, k), oracle.afps(P, 512, M, k), f"N={N} M={M} k={k}")
+
+
 # --------------------------------------------------------------- NPDU stride phase
 # Under the literal NPDU reading (distances start at 1e10) the first samples of
 # a sector started at offset r <= floor(k/2) are r, r + q, r + 2q, ... with
@@ -222,7 +230,8 @@ def test_forced_variant(tmp_path, row):
 # of the stride's length, on a 32-sample row boundary, with starts inside and
 # outside the half window, the other window reading, and coordinates far
 # enough apart to reach 1e10.
-STRIDE_KERNELS = [(0, 2, 4, 1), (0, 8, 2, 1), (1, 2, 8, 1), (1, 8, 4, 1), (1, 16, 8, 1)]
+STRIDE_KERNELS = [(0, 2, 4, 1), (0, 8, 2, 1), (1, 2, 8, 1), (1, 8, 4, 1), (1, 16, 8, 1),
+                  (1, 4, 8, 4), (1, 16, 4, 2)]  # the last two: thread-block clusters
 
 
 def stride_len(n, k, r, method=0):
@@ -247,7 +256,7 @@ def stride_cases(n):
 def test_npdu_stride_phase(tmp_path, kern):
     kind, Pp, W, CS = kern
     build_mod.build()
-    cap = 32 * Pp if kind == 0 else 32 * W * Pp
+    cap = 32 * Pp if kind == 0 else 32 * W * Pp * CS
     sizes = [cap - 3] + ([288] if cap >= 288 else [])
     for n in sizes:
         M = 3
