@@ -210,23 +210,28 @@ def rotation(x, total_out: int, dev):
     return xr, outr
 
 
-def time_stream(sampler, xr, outr, ba, steps: int, warmup: int):
-    """Whole-job throughput: K steps issued back to back on one stream through
-    the C ABI (afps_sample_batched on a context without graphs: one direct
-    kernel launch per step; hundreds of distinct graphs, one per slot, were
-    measured to launch slower than that when queued), each on the next
-    resident slot of the rotation, timed by one pair of CUDA events around
-    the K steps.  Every slot is run once first (untimed); the timed steps
-    start at the least recently used slot, so every one of them reads cold
-    points.  Returns (ms per step, launches in the timed region, last slot
-    used, enqueue information)."""
+def time_stream(sampler, xr, outr, ba, steps: int, warmup: int, n_streams: int = 1):
+    """Whole-job throughput: K steps issued through the C ABI
+    (afps_sample_batched on a context without graphs: one direct kernel
+    launch per step; hundreds of distinct graphs, one per slot, were measured
+    to launch slower than that when queued), each on the next resident slot
+    of the rotation.  Step i goes to stream i mod S: the steps of one stream
+    run back to back, the S streams side by side (independent batches; a
+    step's kernel leaves most of the GPU idle, so they overlap).  One pair of
+    CUDA events on the launching stream brackets the K steps; every stream
+    waits for the first event and the second waits for every stream.  Every
+    slot is run once first (untimed); the timed steps start at the least
+    recently used slot, so every one of them reads cold points.  Returns (ms
+    per step, launches in the timed region, last slot used, enqueue
+    information)."""
     import torch
     from paper_2208_08795_gb300 import afps as A
     fn = A.load().afps_sample_batched
-    stream = torch.cuda.current_stream()
+    main = torch.cuda.current_stream()
+    streams = [main] + [torch.cuda.Stream() for _ in range(n_streams - 1)]
     R = xr.shape[0]
-    args = [(sampler.ctx, xr[i].data_ptr(), *ba.args(), outr[i].data_ptr(), stream.cuda_stream)
-            for i in range(R)]
+    args = [(sampler.ctx, xr[i % R].data_ptr(), *ba.args(), outr[i % R].data_ptr(),
+             streams[i % n_streams].cuda_stream) for i in range(R)]
 
     def call(i):
         if fn(*args[i % R]) != 0:
@@ -240,18 +245,24 @@ def time_stream(sampler, xr, outr, ba, steps: int, warmup: int):
         call(i)
     torch.cuda.synchronize()
     per_call = (time.perf_counter() - t0) / warmup
-    # Hold the stream (a fixed-length sleep kernel, outside the events) while
-    # the K steps are enqueued, so that the GPU runs them back to back and the
-    # host's per-call cost does not set the pace.
+    # Hold the streams (a fixed-length sleep kernel before the first event)
+    # while the K steps are enqueued, so that the GPU runs them without
+    # waiting for the host, whose per-call cost does not set the pace.
     hold_s = min(3.0 * per_call * steps + 1e-3, 0.05)
     torch.cuda._sleep(int(hold_s * 2.07e9))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n0 = sampler.launch_count
-    e0.record(stream)
+    e0.record(main)
+    for st in streams[1:]:
+        st.wait_event(e0)
     t0 = time.perf_counter()
     for i in range(warmup, warmup + steps):
         call(i)
-    e1.record(stream)
+    for st in streams[1:]:
+        ev = torch.cuda.Event()
+        ev.record(st)
+        main.wait_event(ev)
+    e1.record(main)
     enqueue_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     sampler.sync()
@@ -261,25 +272,26 @@ def time_stream(sampler, xr, outr, ba, steps: int, warmup: int):
             info)
 
 
-def time_e2e_stream(sampler, xyz, ba, steps: int, warmup: int, expect):
+def time_e2e_stream(sampler, xyz, ba, steps: int, warmup: int, expect, n_streams: int = 1):
     """End to end through the public API, pipelined: K calls of
     afps_sample_batched_host_async (a context without graphs: its kernels
     read the points from, and write the indices to, page-locked host memory
-    over the C2C link), then one synchronisation, timed on the host clock.
-    Step i reads input copy i mod R (R copies span twice the L2, so no step
-    finds its points cached) and writes its own output buffer; every output
-    is checked against `expect` afterwards.  Returns (ms per step, input
-    bytes per step, output bytes per step)."""
+    over the C2C link), call i on stream i mod S, then one synchronisation of
+    the device, timed on the host clock.  Step i reads input copy i mod R (R
+    copies span twice the L2, so no step finds its points cached) and writes
+    its own output buffer; every output is checked against `expect`
+    afterwards.  Returns (ms per step, input bytes per step, output bytes per
+    step)."""
     import torch
     from paper_2208_08795_gb300 import afps as A
     fn = A.load().afps_sample_batched_host_async
-    stream = torch.cuda.current_stream()
+    streams = [torch.cuda.current_stream()] + [torch.cuda.Stream() for _ in range(n_streams - 1)]
     slot = xyz.nbytes + ba.total_out * 4
     R = max(8, -(-2 * L2_BYTES // slot))
     hx = torch.from_numpy(xyz).unsqueeze(0).repeat(R, 1, 1).pin_memory()
     ho = torch.full((warmup + steps, ba.total_out), -1, dtype=torch.int32).pin_memory()
-    args = [(sampler.ctx, hx[i % R].data_ptr(), *ba.args(), ho[i].data_ptr(), stream.cuda_stream)
-            for i in range(warmup + steps)]
+    args = [(sampler.ctx, hx[i % R].data_ptr(), *ba.args(), ho[i].data_ptr(),
+             streams[i % n_streams].cuda_stream) for i in range(warmup + steps)]
 
     def call(i):
         if fn(*args[i]) != 0:
@@ -287,12 +299,13 @@ def time_e2e_stream(sampler, xyz, ba, steps: int, warmup: int, expect):
 
     for i in range(warmup):
         call(i)
-    sampler.sync()
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(warmup, warmup + steps):
         call(i)
-    sampler.sync()
+    torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / steps
+    sampler.sync()
     if not bool((ho[warmup:] == torch.from_numpy(expect).unsqueeze(0)).all()):
         raise RuntimeError("an end-to-end step differs from the device path")
     return ms, xyz.nbytes, ba.total_out * 4
@@ -639,9 +652,10 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
 
     rot = {}
 
-    def run(M, k, steps, warmup, latency=False):
-        """Throughput over the rotation (back to back), and with latency=True
-        also per-step latency of isolated steps after an L2 flush."""
+    def run(M, k, steps, warmup, latency=False, n_streams=args.streams):
+        """Throughput over the rotation (steps back to back on each of
+        n_streams streams), and with latency=True also per-step latency of
+        isolated steps after an L2 flush."""
         ba = A.BatchArgs(off, C_SAMPLES, M, k, 0)
         out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
         # untimed: the autotuner picks the kernel variant (and writes the result)
@@ -659,7 +673,8 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
             if direct.describe_plan(n_s, c_s, k, B_CLOUDS * M) != plans[f"M{M}_{'npdu' if k else 'full'}"]:
                 raise RuntimeError("the throughput context did not load the tuned variant")
             barrier()
-            ms, launches, last, rot["enqueue"] = time_stream(direct, xr, outr, ba, steps, warmup)
+            ms, launches, last, rot["enqueue"] = time_stream(direct, xr, outr, ba, steps, warmup,
+                                                             n_streams)
             barrier()
         finally:
             direct.close()
@@ -682,11 +697,17 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     value = B_CLOUDS * world / (ms_step / 1e3)
     head_out = out.cpu().numpy()
     head_enqueue = dict(rot["enqueue"])
+    # the same steps on one stream (each step waits for the one before)
+    _, _, ms1, _, _ = run(M_SECTORS, K_WINDOW, args.steps, args.warmup, n_streams=1)
+    ms_one = max_over_ranks(ms1, world, dev)
 
     # plain FPS on the same batch, same protocol
     _, _, ms_f, _, _ = run(1, 0, args.steps, args.warmup)
     ms_fps = max_over_ranks(ms_f, world, dev)
     fps_value = B_CLOUDS * world / (ms_fps / 1e3)
+    _, _, ms_f1, _, _ = run(1, 0, max(3, min(args.steps, 50)), max(3, args.warmup // 2),
+                            n_streams=1)
+    ms_fps_one = max_over_ranks(ms_f1, world, dev)
 
     # sweep of the paper's M values, NPDU off / on
     sweep = {}
@@ -706,7 +727,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     try:
         barrier()
         e2e_ms, h2d_bytes, d2h_bytes = time_e2e_stream(direct, xyz, ba, args.steps, args.warmup,
-                                                       head_out)
+                                                       head_out, args.streams)
         barrier()
     finally:
         direct.close()
@@ -728,10 +749,13 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     clk = clocks.stop()
     e2e_ok = bool(np.array_equal(h_out, head_out))
 
-    # roofline of the sampling kernel (one launch per step)
+    # roofline of the sampling kernel (one launch per step).  With S streams
+    # S launches run side by side: the GPU completes one every ms, and each
+    # launch lasts about S x ms on its own stream.  achieved = the bytes the
+    # launches of the timed region move together / the timed region.
     peak, peak_kind = measured_hbm_peak()
     hbm_bytes = 12 * int(off[-1]) + 4 * int(ba.total_out)
-    kernel_s = ms / 1e3  # average launch duration over the timed region (one launch per step)
+    kernel_s = ms / 1e3  # timed region / launches
     achieved = hbm_bytes / kernel_s / 1e9
     evals, compares = npdu_work(head_out, ba, K_WINDOW)
     sm_mhz = clk["sm_mhz"] or 2070.0
@@ -751,22 +775,32 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
                          f"({rot['mb']:.0f} MB with their outputs) are visited in turn, so each "
                          "timed step reads points untouched for more than 2 x L2 of traffic; "
                          "p50/p99 are isolated steps, each after a 256 MB L2 flush",
-                   "timing": "value and ms_per_step: K steps back to back between two CUDA "
-                             "events on the launching stream, enqueued while a sleep kernel "
-                             "(before the first event) holds the stream; p50/p99: per-step events",
+                   "streams": args.streams,
+                   "timing": f"value and ms_per_step: K steps, step i on stream i mod "
+                             f"{args.streams} (each stream's steps back to back, the streams "
+                             "side by side), between two CUDA events on the launching stream "
+                             "that every stream waits for / joins, enqueued while a sleep kernel "
+                             "(before the first event) holds the streams; ms_per_step = timed "
+                             "region / K; p50/p99: per-step events of isolated steps",
                    "parallelism": f"replicas x{world}",
                    "launch": "throughput: one direct kernel launch per step; latency: CUDA graph "
                              "replay; kernel variant chosen by the autotuner (untimed)"},
         "kernel_variants": plans,
         "sampled_points_per_s": value * C_SAMPLES,
         "fps_baseline": {"value": fps_value, "unit": UNIT, "ms_per_step": ms_fps,
-                         "speedup_npdu_afps": value / fps_value},
+                         "speedup_npdu_afps": value / fps_value, "streams": args.streams},
+        "one_stream": {"value": B_CLOUDS * world / (ms_one / 1e3), "ms_per_step": ms_one,
+                       "fps_value": B_CLOUDS * world / (ms_fps_one / 1e3),
+                       "fps_ms_per_step": ms_fps_one, "speedup_npdu_afps": ms_fps_one / ms_one},
         "sweep_clouds_per_s": sweep,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "algorithmic_bytes_per_launch": hbm_bytes,
+                     "how": f"algorithmic bytes per launch x launches / timed region "
+                            f"({args.streams} streams of back-to-back launches side by side; "
+                            f"each launch lasts about {args.streams} x ms_per_step on its stream)",
                      "kernel": plans.get(f"M{M_SECTORS}_npdu")},
         "roofline_alu": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
@@ -774,9 +808,10 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         "e2e": {"value": B_CLOUDS * world / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes),
                 "ms_per_step": e2e_ms, "matches_device_path": True,
-                "how": "K calls of afps_sample_batched_host_async on page-locked buffers "
-                       "(inputs rotating over copies larger than L2, one output per step), "
-                       "one synchronisation, host clock; every output checked",
+                "how": f"K calls of afps_sample_batched_host_async on page-locked buffers "
+                       f"(inputs rotating over copies larger than L2, one output per step), "
+                       f"call i on stream i mod {args.streams}, one synchronisation, host "
+                       f"clock; every output checked",
                 "sync_call_ms": e2e_call_ms, "sync_call_matches_device_path": e2e_ok},
         "serving": serving_stats,
         "large_clouds": large,
@@ -827,6 +862,8 @@ def main(argv=None) -> int:
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-seconds", type=float, default=5.0)
+    ap.add_argument("--streams", type=int, default=8,
+                    help="streams the throughput steps are spread over (1: one stream)")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the serving sweep")
     ap.add_argument("--no-configs", dest="configs", action="store_false",

@@ -39,9 +39,12 @@
  *   - Return value: AFPS_OK (0) or a negative AFPS_ERR_* code; the message of
  *     the last error is afps_last_error(ctx).  Nothing is written to any
  *     output on a validation error.
- *   - A context may be used from one host thread at a time.  Calls on one
- *     context are ordered on the device even across streams (the context's
- *     workspace is reused only after the previous call using it finished).
+ *   - A context may be used from one host thread at a time, with any number
+ *     of streams.  A call that uses the context's device workspace (the item
+ *     table of a ragged batch, the work-queue counters of a batch larger than
+ *     one wave of the grid) waits on the device for the previous call that
+ *     used it, whatever its stream; other calls on different streams may run
+ *     at the same time, which is how independent batches overlap.
  */
 #ifndef AFPS_H
 #define AFPS_H

@@ -563,9 +563,11 @@ int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* 
         queue = queue || (cp.v.kind == afps::KIND_WARP &&
                           (size_t)grid_for(cp.v, cp.count) * (size_t)cp.v.W < cp.count);
     }
-    if (table) {
+    if (table) {  // the upload waits for the workspace's last use
         int urc = upload(ctx, ctx->items, plan.items.data(), bytes, stream);
         if (urc != AFPS_OK) return urc;
+    } else if (queue) {  // the counters are reset on this stream: same wait
+        AFPS_CUDA(ctx, cudaStreamWaitEvent(stream, ctx->ev_done, 0));
     }
     const ItemDesc* d_items = static_cast<const ItemDesc*>(ctx->items.p);
     unsigned int* counters = static_cast<unsigned int*>(ctx->counters.p);

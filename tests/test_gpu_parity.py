@@ -612,6 +612,48 @@ def test_back_to_back_calls_on_one_output(objects):
         s.close()
 
 
+def test_calls_on_several_streams(objects):
+    """One context, four streams.  Calls that share none of the context's
+    workspace overlap on the device; calls that use it (the item table of a
+    ragged batch, the work-queue counters of a batch wider than one wave of
+    the grid) wait for its previous user on whatever stream.  Every output
+    must equal the same call made alone, and those the oracle's."""
+    build_mod.build()
+    s = B.Sampler(0)
+    try:
+        wide = [objects[i % 32] for i in range(1024)]  # 32768 sectors: the work queue
+        ragged = [objects[i][:2048 - 97 * i] for i in range(16)]  # an item table
+        cases = [(wide, 32, 16), (ragged, 8, 8), (objects, 32, 16), (ragged, 32, 0),
+                 (objects, 1, 0)]
+        calls = []
+        for clouds, M, k in cases:
+            xyz, off = synth.pack(clouds)
+            calls.append((torch.from_numpy(xyz).cuda(), B.BatchArgs(off, 256, M, k, 0)))
+        alone = []
+        for x, ba in calls:
+            alone.append(s.sample_batched(x, ba).cpu())
+            s.sync()
+        for j, (clouds, M, k) in enumerate(cases):
+            ba = calls[j][1]
+            for b in (0, len(clouds) - 1):
+                assert_same(alone[j][ba.out_off[b]:ba.out_off[b + 1]].numpy(),
+                            oracle.afps(clouds[b], 256, M, k), f"case {j} cloud {b}")
+        streams = [torch.cuda.Stream() for _ in range(4)]
+        plan = [(rep, j) for rep in range(6) for j in range(len(calls))]
+        outs = [torch.full((calls[j][1].total_out,), -1, dtype=torch.int32, device="cuda")
+                for _, j in plan]
+        torch.cuda.synchronize()
+        for (rep, j), o in zip(plan, outs):
+            x, ba = calls[j]
+            s.sample_batched(x, ba, out=o, stream=streams[(rep + j) % 4])
+        torch.cuda.synchronize()
+        s.sync()
+        for (rep, j), o in zip(plan, outs):
+            assert torch.equal(o.cpu(), alone[j]), f"rep {rep} case {j}"
+    finally:
+        s.close()
+
+
 # --------------------------------------------------------------- failure detection
 def test_bounded_wait_reports_timeout_and_context_survives():
     """Fault injection on the host side of the barrier: the copy is never
