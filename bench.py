@@ -8,13 +8,17 @@ one batched call (graph-replayed).  Beside it, in the same run: plain FPS
 off/on, the end-to-end time through host buffers, the roofline of the
 sampling kernel, and the CPU oracle on the host's cores.
 
-Timing.  Throughput (`value`, `ms_per_step`): K steps back to back on one
-stream between two CUDA events, each step on the next of R resident copies
-of the batch (R copies span twice the L2), so every timed step reads cold
-points without a flush; a fixed-length sleep kernel ahead of the first event
-holds the stream while the host enqueues the K steps, so the GPU runs them
-back to back (the host path is what `e2e` measures).  Latency (`p50_ms`, `p99_ms`): isolated steps, each
-after a 256 MB write that flushes the L2, with its own pair of events.
+Timing.  Throughput (`value`, `ms_per_step`): K steps between two CUDA
+events, step i on stream i mod S (S = 8 by default: the steps of a stream
+run back to back, the streams side by side, as independent batches would),
+each step on the next of R resident copies of the batch (R copies span twice
+the L2), so every timed step reads cold points without a flush; a
+fixed-length sleep kernel ahead of the first event holds the streams while
+the host enqueues the K steps, so the host's call rate does not set the pace
+(the host path is what `e2e` measures).  `one_stream` repeats it on a single
+stream.  Latency (`p50_ms`, `p99_ms`): isolated steps, each after a 256 MB
+write that flushes the L2, with its own pair of events.  The CPU oracle runs
+one worker process per host core.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -147,23 +151,75 @@ def measured_hbm_peak():
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_batch(clouds, C, M, k, threads):
+_ORACLE_WORK = None
+
+
+def _oracle_init(clouds, C, M, k):
+    global _ORACLE_WORK
+    _ORACLE_WORK = (clouds, C, M, k)
+
+
+def _oracle_chunk(lo: int, hi: int, reps: int):
+    """Clouds [lo, hi) of the batch through the oracle, `reps` times; returns
+    the last pass's indices."""
     import oracle
-    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        return list(ex.map(lambda P: oracle.afps(P, C, M, k, 0), clouds))
+    clouds, C, M, k = _ORACLE_WORK
+    out = None
+    for _ in range(reps):
+        out = [oracle.afps(clouds[i], C, M, k, 0) for i in range(lo, hi)]
+    return out
 
 
-def time_oracle(clouds, C, M, k, budget_s: float, threads: int):
-    """The oracle as it stands, threads over clouds (ctypes releases the GIL),
-    repeated over whole batches until about budget_s of CPU time."""
-    outs = oracle_batch(clouds, C, M, k, threads)  # also warms the library
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        oracle_batch(clouds, C, M, k, threads)
-        reps += 1
+class OraclePool:
+    """The oracle, as it stands, over one batch on `procs` host cores: worker
+    processes (started with spawn, so safe after CUDA use) that each hold the
+    batch and run a contiguous chunk of its clouds.  Processes rather than
+    threads: the oracle's Python wrapper holds the GIL for about a sixth of a
+    call, which capped 16 threads at 1.3x one."""
+
+    def __init__(self, clouds, C, M, k, procs: int):
+        self.n, self.procs = len(clouds), max(1, min(procs, len(clouds)))
+        self.pool = None
+        if self.procs == 1:
+            _oracle_init(clouds, C, M, k)
+        else:
+            import multiprocessing as mp
+            self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_oracle_init,
+                                                     initargs=(clouds, C, M, k))
+
+    def run(self, reps: int = 1):
+        """The batch `reps` times; returns the last pass's indices per cloud."""
+        if self.pool is None:
+            return _oracle_chunk(0, self.n, reps)
+        bounds = [(self.n * i // self.procs, self.n * (i + 1) // self.procs, reps)
+                  for i in range(self.procs)]
+        out = []
+        for part in self.pool.starmap(_oracle_chunk, bounds, chunksize=1):
+            out.extend(part)
+        return out
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+
+def time_oracle(clouds, C, M, k, budget_s: float, procs: int):
+    """The oracle as it stands on `procs` cores: whole batches, repeated for
+    about budget_s.  Returns (clouds/s, batches, indices per cloud)."""
+    pool = OraclePool(clouds, C, M, k, procs)
+    try:
+        outs = pool.run(1)  # starts the workers and warms the library
+        t0 = time.perf_counter()
+        pool.run(10)
+        once = (time.perf_counter() - t0) / 10
+        reps = max(1, min(100000, int(budget_s / max(once, 1e-6))))
+        t0 = time.perf_counter()
+        pool.run(reps)
         el = time.perf_counter() - t0
-        if el >= budget_s or reps >= 1000:
-            break
+    finally:
+        pool.close()
     return reps * len(clouds) / el, reps, outs
 
 
@@ -592,30 +648,42 @@ def serving_sweep(sampler, seconds_per_rate: float = 0.25):
 
 # ------------------------------------------------------------------ arms
 def run_reference(args, rank: int, world: int) -> int:
-    """The oracle, as it stands, on the host cores: the reference arm."""
+    """The oracle, as it stands, on the host cores: the reference arm.  One
+    step = `batches` whole batches (about 50 ms of work, so that handing the
+    work to the processes costs little), timed on the host clock."""
     if rank != 0:
         return 0
     clouds, _, _ = make_batch(batch_seed(0))
-    threads = cpu_threads()
-    for _ in range(args.warmup):
-        oracle_batch(clouds, C_SAMPLES, M_SECTORS, K_WINDOW, threads)
-    ts = []
-    for _ in range(args.steps):
+    procs = cpu_threads()
+    pool = OraclePool(clouds, C_SAMPLES, M_SECTORS, K_WINDOW, procs)
+    try:
+        pool.run(1)
         t0 = time.perf_counter()
-        oracle_batch(clouds, C_SAMPLES, M_SECTORS, K_WINDOW, threads)
-        ts.append((time.perf_counter() - t0) * 1e3)
+        pool.run(10)
+        batches = max(1, int(0.05 / max((time.perf_counter() - t0) / 10, 1e-6)))
+        for _ in range(args.warmup):
+            pool.run(batches)
+        ts = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            pool.run(batches)
+            ts.append((time.perf_counter() - t0) * 1e3)
+    finally:
+        pool.close()
     ms = float(np.mean(ts))
-    value = B_CLOUDS / (ms / 1e3)
+    value = B_CLOUDS * batches / (ms / 1e3)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "p99_ms": pct(ts, 99),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "clouds": B_CLOUDS, "N": N_POINTS, "C": C_SAMPLES,
-                   "M": M_SECTORS, "k": K_WINDOW, "parallelism": "host threads"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{args.steps} whole batches of {B_CLOUDS} clouds, "
-                                   f"threads over clouds"},
+                   "M": M_SECTORS, "k": K_WINDOW, "parallelism": f"{procs} host processes",
+                   "batches_per_step": batches},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": f"{args.steps} steps of {batches} whole batches of "
+                                   f"{B_CLOUDS} clouds, one process per core, each a "
+                                   f"contiguous chunk of the batch's clouds"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line, default=_json_default))
@@ -830,9 +898,15 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         threads = cpu_threads()
         rate, reps, ref = time_oracle(clouds, C_SAMPLES, M_SECTORS, K_WINDOW,
                                       args.cpu_seconds, threads)
+        rate1, reps1, _ = time_oracle(clouds, C_SAMPLES, M_SECTORS, K_WINDOW,
+                                      args.cpu_seconds / 4, 1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"{reps} whole batches of {B_CLOUDS} clouds "
-                                          f"(about {args.cpu_seconds:.0f} s), threads over clouds"}
+                                          f"(about {args.cpu_seconds:.0f} s), one process per "
+                                          f"core, each a contiguous chunk of the clouds",
+                                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                                  "sample": f"{reps1} whole batches of "
+                                                            f"{B_CLOUDS} clouds on one thread"}}
         same = sum(int(np.array_equal(head_out[ba.out_off[b]:ba.out_off[b + 1]], ref[b]))
                    for b in range(B_CLOUDS))
         line["parity"] = f"{same}/{B_CLOUDS} clouds bit-exact vs the FP32 oracle"
