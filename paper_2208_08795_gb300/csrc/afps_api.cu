@@ -475,6 +475,7 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
                 cp.single.flags = w.flags;
                 cp.single.start_r = m0.chk.start_r;
                 cp.single.wide = (int64_t)M[b0] * n_pts[b0] > (int64_t)UINT32_MAX ? 1 : 0;
+                cp.single.m_magic = afps::div_magic(M[b0]);
                 cp.n_max = m0.chk.n_max;
                 cp.c_max = m0.chk.c_max;
                 cp.count = g.second.size() * (size_t)M[b0];
@@ -1020,6 +1021,7 @@ int afps_sample_ex(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int3
     }
     a.single.start_r = chk.start_r;
     a.single.wide = (int64_t)M * N > (int64_t)UINT32_MAX ? 1 : 0;
+    a.single.m_magic = afps::div_magic(M);
     a.n_items = M;
     a.out = d_out;
     a.counter = nullptr;

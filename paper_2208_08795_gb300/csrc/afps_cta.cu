@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             // across the cluster.
             const int q = kr + 1;
             const int x = n - 1 - kr - p;
-            const int ts = x <= 0 ? 1 : (int)((unsigned)(x + q - 1) / (unsigned)q) + 1;  // stride length
+            const dev::SmallDiv divq((uint32_t)q);
+            const int ts = x <= 0 ? 1 : (int)divq((uint32_t)(x + q - 1)) + 1;  // stride length
             const int tn = min(ts, c);                        // of them emitted
             const int tw = min(ts, c - 1);                    // whose window is applied
             const float* G = CLUSTER ? a.xyz + 3 * d.src : pts;  // the sector's points
@@ -204,8 +205,8 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
                     const float px = pts[3 * jl], py = pts[3 * jl + 1], pz = pts[3 * jl + 2];
                     const int y = j - kr - p;
                     // unsigned divisions: both operands are >= 0 (p <= kl)
-                    const int tlo = y <= 0 ? 0 : (int)((unsigned)(y + q - 1) / (unsigned)q);
-                    const int thi = min(tw - 1, (int)((unsigned)(j + kl - p) / (unsigned)q));
+                    const int tlo = y <= 0 ? 0 : (int)divq((uint32_t)(y + q - 1));
+                    const int thi = min(tw - 1, (int)divq((uint32_t)(j + kl - p)));
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         if (tlo + u <= thi) {
@@ -338,9 +339,11 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             p = dev::checked((int)(0xffffffffu - lo2), 0, n, a.status);
             if (CLUSTER) {
                 // the winner's record sits at (owner rank, owner warp)
-                const int r = p / chunk;
-                const int e_star =
-                    dev::checked(r * W + (((p - r * chunk) % T) >> 5), 0, E, a.status);
+                const int r = (int)dev::SmallDiv((uint32_t)chunk)((uint32_t)p);
+                const int u = p - r * chunk;  // chunk-local index: thread u % T
+                const int e_star = dev::checked(
+                    r * W + ((u - (int)dev::SmallDiv((uint32_t)T)((uint32_t)u) * T) >> 5), 0, E,
+                    a.status);
                 qx = R[e_star].x;
                 qy = R[e_star].y;
                 qz = R[e_star].z;

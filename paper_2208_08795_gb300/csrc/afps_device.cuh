@@ -76,6 +76,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// As mbar_try_wait, with the thread suspended for up to hint_ns while the
+// phase is incomplete (fewer polling instructions while a copy is in flight).
+__device__ __forceinline__ bool mbar_try_wait_for(uint32_t bar, uint32_t parity,
+                                                  uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for phase `parity` of the barrier to complete, giving up after
 // timeout_ns.  Returns false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
@@ -83,7 +98,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_for(bar, parity, 20000u)) return true;
         if (globaltimer() - t0 > timeout_ns) return false;
     }
 }
@@ -213,6 +228,22 @@ __device__ __forceinline__ void sqdist2(unsigned long long x, unsigned long long
     d1 = __fadd_rn(__fadd_rn(x1, y1), z1);
 }
 
+// Unsigned division of x < 2^24 by a divisor d >= 1 used many times: the
+// product of x and the rounded reciprocal is within (x/d) 2^-23 < 1 of x/d
+// for d >= 2 (exact for d = 1), so its truncation is the quotient or one off
+// either way, which two integer checks correct.
+struct SmallDiv {
+    uint32_t d;
+    float r;
+    __device__ __forceinline__ explicit SmallDiv(uint32_t dd) : d(dd), r(1.0f / (float)dd) {}
+    __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
+        uint32_t t = __float2uint_rz(__uint2float_rn(x) * r);
+        t -= t * d > x ? 1u : 0u;
+        t += (t + 1u) * d <= x ? 1u : 0u;
+        return t;
+    }
+};
+
 // Item `i` of a launch: from the device table, or computed from the
 // parameters of a run of equal clouds stored back to back (cloud i / M,
 // sector i % M) with the sector rule floor(s*N/M), floor(s*C/M).  Computing
@@ -221,7 +252,12 @@ __device__ __forceinline__ ItemDesc load_item(const LaunchArgs& a, int i) {
     if (a.items) return a.items[i];
     const SingleCloud& s = a.single;
     const uint32_t M = (uint32_t)s.M;
-    const uint32_t b = (uint32_t)i / M;
+    const uint64_t mm = s.m_magic;
+    // x / M for x < 2^32 by one multiply-high (div_magic), or a division when M < 2
+    auto divM = [M, mm](uint32_t x) -> uint32_t {
+        return mm ? (uint32_t)__umul64hi((uint64_t)x, mm) : x / M;
+    };
+    const uint32_t b = divM((uint32_t)i);
     const uint32_t sec = (uint32_t)i - b * M;
     int64_t lo, hi, o0, o1;
     if (s.wide) {  // M * N does not fit in 32 bits
@@ -229,11 +265,11 @@ __device__ __forceinline__ ItemDesc load_item(const LaunchArgs& a, int i) {
         hi = (int64_t)(sec + 1) * s.N / s.M;
         o0 = (int64_t)sec * s.C / s.M;
         o1 = (int64_t)(sec + 1) * s.C / s.M;
-    } else {  // 32-bit unsigned divisions: a few instructions instead of a call
-        lo = sec * (uint32_t)s.N / M;
-        hi = (sec + 1) * (uint32_t)s.N / M;
-        o0 = sec * (uint32_t)s.C / M;
-        o1 = (sec + 1) * (uint32_t)s.C / M;
+    } else {  // numerators below M * N < 2^32
+        lo = divM(sec * (uint32_t)s.N);
+        hi = divM((sec + 1) * (uint32_t)s.N);
+        o0 = divM(sec * (uint32_t)s.C);
+        o1 = divM((sec + 1) * (uint32_t)s.C);
     }
     ItemDesc d;
     d.src = s.pt_off + (int64_t)b * s.N + lo;

@@ -37,7 +37,17 @@ struct SingleCloud {
     int32_t kl, kr, flags;  // as in ItemDesc
     int32_t start_r;        // offset of start_idx inside its own sector
     int32_t wide;           // M * N >= 2^32: sector bounds in 64-bit arithmetic
+    uint64_t m_magic;       // div_magic(M): x / M = high 64 bits of x * m_magic (x < 2^32)
 };
+
+// Multiplier for unsigned division of 32-bit numerators by d >= 2:
+// floor((2^64 - 1) / d) + 1 = ceil(2^64 / d) exceeds 2^64 / d by less than
+// one, so x * m / 2^64 exceeds x / d by less than x / 2^64 < 2^-32 <= 1/d,
+// which never reaches the next integer: the high word is floor(x / d).
+// 0 for d < 2 (the caller divides instead).
+inline uint64_t div_magic(int32_t d) {
+    return d >= 2 ? ~0ull / (uint64_t)d + 1ull : 0ull;
+}
 
 enum Kind : int32_t { KIND_WARP = 0, KIND_CTA = 1 };
 

@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
             // the start).  With kl <= kr a point lies in at most two windows.
             const int q = kr + 1;
             const int x = n - 1 - kr - p;
-            const int ts = x <= 0 ? 1 : (int)((unsigned)(x + q - 1) / (unsigned)q) + 1;  // stride length
+            const dev::SmallDiv divq((uint32_t)q);
+            const int ts = x <= 0 ? 1 : (int)divq((uint32_t)(x + q - 1)) + 1;  // stride length
             const int tn = min(ts, c);                        // of them emitted
             const int tw = min(ts, c - 1);                    // whose window is applied
             bool ok = true;  // D is updated in place and reset if the test fails
@@ -145,8 +146,8 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
                     const float px = pts[3 * j], py = pts[3 * j + 1], pz = pts[3 * j + 2];
                     const int y = j - kr - p;
                     // unsigned divisions: both operands are >= 0 (p <= kl)
-                    const int tlo = y <= 0 ? 0 : (int)((unsigned)(y + q - 1) / (unsigned)q);
-                    const int thi = min(tw - 1, (int)((unsigned)(j + kl - p) / (unsigned)q));
+                    const int tlo = y <= 0 ? 0 : (int)divq((uint32_t)(y + q - 1));
+                    const int thi = min(tw - 1, (int)divq((uint32_t)(j + kl - p)));
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         if (tlo + u <= thi) {
