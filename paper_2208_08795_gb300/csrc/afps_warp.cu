@@ -15,8 +15,9 @@
 //              steps: max of the distance bits (distances are >= +0, so the
 //              unsigned bit order is the float order), then min of the index
 //              among the lanes holding that maximum (lowest index on ties).
-//   emit       sample indices are buffered one per lane and stored as one
-//              coalesced 128-byte row every 32 iterations.
+//   emit       every lane learns each sample from the reduction; lane 0
+//              stores it (the stride phase's samples go out as coalesced
+//              rows).
 // Work items come from a device counter (dynamic queue) or by static
 // striding.  No CTA-wide synchronisation: warps of a CTA are independent.
 #include "afps_device.cuh"
@@ -119,8 +120,10 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         const int kr = d.kr;
         const bool full_first = (d.flags & ITEM_FULL_FIRST) != 0;
         int p = dev::checked(d.first, 0, n, a.status);
-        // sample t's index is kept by lane t % 32 and stored once per 32 samples
-        int obuf = lane == 0 ? d.lo + p : 0;
+        // every lane knows each sample; lane 0 stores it (one instruction per
+        // sample, where a coalesced row store per 32 samples needs a select
+        // per sample to buffer them)
+        if (lane == 0) out[0] = d.lo + p;
         int t0 = 1;
         if (NPDU && !full_first && p <= kl && kl <= kr) {
             // Stride phase of the literal NPDU reading (distances start at
@@ -161,8 +164,7 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
                 }
             }
             if (__all_sync(dev::kFull, ok)) {
-                for (int r0 = 0; r0 + 32 <= tn; r0 += 32) out[r0 + lane] = d.lo + p + (r0 + lane) * q;
-                obuf = d.lo + p + (((tn - 1) & ~31) + lane) * q;
+                for (int t = 1 + lane; t < tn; t += 32) out[t] = d.lo + p + t * q;
                 p += (tn - 1) * q;
                 t0 = tn;  // re-applying the last window is a no-op
             } else {
@@ -170,15 +172,16 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
                 for (int i = 0; i < 2 * PP; ++i) D[i] = (i < P && lane + 32 * i < n) ? 1e10f : 0.f;
             }
         }
-        for (int t = t0; t < c; ++t) {
+        // One argmax round: the update by the last sample p of the points in
+        // [wl, wh] (its NPDU window, or the whole sector), fused with each
+        // lane's argmax over its rows, then the warp argmax as two redux.sync
+        // steps (max of the distance bits, min of the index among the lanes
+        // holding it); stores sample t.
+        auto round = [&](int t, int wl, int wh) {
             const float qx = pts[3 * p], qy = pts[3 * p + 1], qz = pts[3 * p + 2];
             const unsigned long long qx2 = dev::pack2(qx, qx), qy2 = dev::pack2(qy, qy),
                                      qz2 = dev::pack2(qz, qz);
-            // window [wl, wh] as one unsigned range test; the whole sector at
-            // the first update under the full-first-pass reading
-            const bool whole = full_first && t == 1;
-            const int wl = whole ? 0 : p - kl, wh = whole ? n - 1 : p + kr;
-            const unsigned wlo = (unsigned)wl;
+            const unsigned wlo = (unsigned)wl;  // [wl, wh] as one unsigned range test
             const unsigned wspan = (unsigned)(wh - wl);
             float best = -1.f;
             int bi = 0;
@@ -188,8 +191,10 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
                 if (32 * i0 < n) {  // warp-uniform: the row pair holds real points
                     // NPDU: every row pair is computed and the window applied as
                     // a mask, or (npdu_skip) pairs the window misses are skipped
-                    // by a warp-uniform test; never a divergent branch.
-                    const bool hit = !NPDU || !a.npdu_skip || (32 * i0 + 63 >= wl && 32 * i0 <= wh);
+                    // by a warp-uniform test; never a divergent branch.  With
+                    // one pair the window always reaches it.
+                    const bool hit = !NPDU || PP == 1 || !a.npdu_skip ||
+                                     (32 * i0 + 63 >= wl && 32 * i0 <= wh);
                     if (hit) {
                         float d0, d1;
                         dev::sqdist2(X2[h], Y2[h], Z2[h], qx2, qy2, qz2, d0, d1);
@@ -218,10 +223,11 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
             const unsigned m = __reduce_max_sync(dev::kFull, bits);
             const unsigned cand = bits == m ? (unsigned)(lane + 32 * bi) : 0xffffffffu;
             p = dev::checked((int)__reduce_min_sync(dev::kFull, cand), 0, n, a.status);
-            obuf = lane == (t & 31) ? d.lo + p : obuf;
-            if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
-        }
-        if (lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
+            if (lane == 0) out[t] = d.lo + p;
+        };
+        int t = t0;
+        if (full_first && t < c) round(t++, 0, n - 1);  // full-first-pass reading: the first update is the whole sector
+        for (; t < c; ++t) round(t, p - kl, p + kr);
 
         if (a.counter) {
             unsigned v = 0;
