@@ -435,7 +435,9 @@ def kernel_source_hash() -> str:
 # DRAM traffic of the headline kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum per launch), valid only for the kernel sources it was
 # taken on (their hash); otherwise reported as null.
-NCU_TRAFFIC = {"source_hash": "5cffad6ddb745fc8", "bytes_per_launch": 815872}
+NCU_TRAFFIC = {"source_hash": "cf43849d32ede0b7", "bytes_per_launch": 820224}
+# warp instructions of one headline launch (ncu smsp__inst_executed.sum), same rule
+NCU_INST = {"source_hash": "cf43849d32ede0b7", "warp_inst_per_launch": 991232}
 
 
 # ------------------------------------------------------------------ other configs
@@ -831,6 +833,19 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     alu_ach = (9 * evals + compares) / kernel_s / 1e12
     traffic = (NCU_TRAFFIC["bytes_per_launch"]
                if NCU_TRAFFIC["source_hash"] == kernel_source_hash() else None)
+    # issue: executed warp instructions (an ncu count of one launch of these
+    # kernel sources) x launches / timed region, against every scheduler
+    # issuing one per cycle -- how busy the SMs are, not algorithmic work
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    inst = (NCU_INST["warp_inst_per_launch"]
+            if NCU_INST["source_hash"] == kernel_source_hash() else None)
+    issue_peak = n_sm * 4 * sm_mhz * 1e6
+    issue = None if inst is None else {
+        "bound": "issue", "achieved": inst / kernel_s, "peak": issue_peak,
+        "unit": "warp instructions/s", "frac": inst / kernel_s / issue_peak,
+        "warp_inst_per_launch": inst,
+        "how": f"ncu smsp__inst_executed.sum of one launch x launches / timed region; peak = "
+               f"{n_sm} SMs x 4 schedulers x the median SM clock under load"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -870,6 +885,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
                             f"({args.streams} streams of back-to-back launches side by side; "
                             f"each launch lasts about {args.streams} x ms_per_step on its stream)",
                      "kernel": plans.get(f"M{M_SECTORS}_npdu")},
+        "roofline_issue": issue,
         "roofline_alu": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
                          "fp32_ops_per_launch": 9 * evals + compares},
