@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
 }
 
 using SectorKernel = void (*)(LaunchArgs);
-SectorKernel warp_kernel_for(int P, bool npdu);
+SectorKernel warp_kernel_for(int P, bool npdu, bool rows);
 
 static SectorKernel cta_kernel_for(int P, bool npdu, bool cluster) {
 #define AFPS_CTA_CASE(PP)                                                             \
@@ -395,15 +395,17 @@ size_t variant_smem(const Variant& v) {
 
 bool variant_supported(const Variant& v) {
     if (v.kind == KIND_WARP)
-        return warp_kernel_for(v.P, false) != nullptr && v.W >= 1 && v.W <= 8 && v.CS == 1;
+        return warp_kernel_for(v.P, false, false) != nullptr && v.W >= 1 && v.W <= 8 && v.CS == 1;
     if (v.kind != KIND_CTA) return false;
     if (!cta_kernel_for(v.P, false, false)) return false;
     if (v.W < 1 || v.W > (v.P >= 16 ? 8 : 32) || v.CS < 1 || v.CS > 16) return false;
     return variant_smem(v) <= 227 * 1024;
 }
 
-static SectorKernel kernel_for(const Variant& v, bool npdu) {
-    if (v.kind == KIND_WARP) return warp_kernel_for(v.P, npdu);
+// rows: the launch writes its indices to host memory (warp kernels then
+// store them as rows of 32)
+static SectorKernel kernel_for(const Variant& v, bool npdu, bool rows = false) {
+    if (v.kind == KIND_WARP) return warp_kernel_for(v.P, npdu, rows);
     return cta_kernel_for(v.P, npdu, v.CS > 1);
 }
 
@@ -439,7 +441,7 @@ static cudaError_t prepare(SectorKernel fn, const Variant& v, size_t smem) {
 cudaError_t launch_sector(const Variant& v, bool npdu, const LaunchArgs& a, int grid,
                           cudaStream_t stream) {
     if (!variant_supported(v) || grid < 1) return cudaErrorInvalidValue;
-    SectorKernel fn = kernel_for(v, npdu);
+    SectorKernel fn = kernel_for(v, npdu, a.host_resident != 0);
     const size_t smem = variant_smem(v);
     cudaError_t e = prepare(fn, v, smem);
     if (e != cudaSuccess) return e;

@@ -17,14 +17,15 @@
 //              among the lanes holding that maximum (lowest index on ties).
 //   emit       every lane learns each sample from the reduction; lane 0
 //              stores it (the stride phase's samples go out as coalesced
-//              rows).
+//              rows); indices in host memory go out as rows of 32.
 // Work items come from a device counter (dynamic queue) or by static
 // striding.  No CTA-wide synchronisation: warps of a CTA are independent.
 #include "afps_device.cuh"
 
 namespace afps {
 
-template <int P, bool NPDU>
+// ROWS: the indices go to host memory (over the C2C link), as rows of 32.
+template <int P, bool NPDU, bool ROWS>
 __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int kBuf = 12 * 32 * P + 16;
@@ -120,10 +121,14 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         const int kr = d.kr;
         const bool full_first = (d.flags & ITEM_FULL_FIRST) != 0;
         int p = dev::checked(d.first, 0, n, a.status);
-        // every lane knows each sample; lane 0 stores it (one instruction per
-        // sample, where a coalesced row store per 32 samples needs a select
-        // per sample to buffer them)
-        if (lane == 0) out[0] = d.lo + p;
+        // Every lane knows each sample.  Indices in device memory: lane 0
+        // stores each one (one instruction per sample; buffering them for
+        // row stores costs a select per sample).  Indices in host memory,
+        // written over the C2C link, where each store is a transfer: lane t
+        // % 32 keeps sample t and the warp stores full rows of 32.
+        constexpr bool rows_out = ROWS;
+        int obuf = lane == 0 ? d.lo + p : 0;
+        if (lane == 0 && !rows_out) out[0] = d.lo + p;
         int t0 = 1;
         if (NPDU && !full_first && p <= kl && kl <= kr) {
             // Stride phase of the literal NPDU reading (distances start at
@@ -164,7 +169,12 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
                 }
             }
             if (__all_sync(dev::kFull, ok)) {
-                for (int t = 1 + lane; t < tn; t += 32) out[t] = d.lo + p + t * q;
+                if (rows_out) {
+                    for (int r0 = 0; r0 + 32 <= tn; r0 += 32) out[r0 + lane] = d.lo + p + (r0 + lane) * q;
+                    obuf = d.lo + p + (((tn - 1) & ~31) + lane) * q;
+                } else {
+                    for (int t = 1 + lane; t < tn; t += 32) out[t] = d.lo + p + t * q;
+                }
                 p += (tn - 1) * q;
                 t0 = tn;  // re-applying the last window is a no-op
             } else {
@@ -223,11 +233,17 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
             const unsigned m = __reduce_max_sync(dev::kFull, bits);
             const unsigned cand = bits == m ? (unsigned)(lane + 32 * bi) : 0xffffffffu;
             p = dev::checked((int)__reduce_min_sync(dev::kFull, cand), 0, n, a.status);
-            if (lane == 0) out[t] = d.lo + p;
+            if (rows_out) {
+                obuf = lane == (t & 31) ? d.lo + p : obuf;
+                if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
+            } else if (lane == 0) {
+                out[t] = d.lo + p;
+            }
         };
         int t = t0;
         if (full_first && t < c) round(t++, 0, n - 1);  // full-first-pass reading: the first update is the whole sector
         for (; t < c; ++t) round(t, p - kl, p + kr);
+        if (rows_out && lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
 
         if (a.counter) {
             unsigned v = 0;
@@ -241,10 +257,11 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
 
 using SectorKernel = void (*)(LaunchArgs);
 
-SectorKernel warp_kernel_for(int P, bool npdu) {
-#define AFPS_WARP_CASE(PP) \
-    case PP:               \
-        return npdu ? afps_warp_kernel<PP, true> : afps_warp_kernel<PP, false>;
+SectorKernel warp_kernel_for(int P, bool npdu, bool rows) {
+#define AFPS_WARP_CASE(PP)                                                              \
+    case PP:                                                                            \
+        if (rows) return npdu ? afps_warp_kernel<PP, true, true> : afps_warp_kernel<PP, false, true>; \
+        return npdu ? afps_warp_kernel<PP, true, false> : afps_warp_kernel<PP, false, false>;
     switch (P) {
         AFPS_WARP_CASE(1)
         AFPS_WARP_CASE(2)
