@@ -435,9 +435,9 @@ def kernel_source_hash() -> str:
 # DRAM traffic of the headline kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum per launch), valid only for the kernel sources it was
 # taken on (their hash); otherwise reported as null.
-NCU_TRAFFIC = {"source_hash": "986c4e1684c18792", "bytes_per_launch": 819968}
+NCU_TRAFFIC = {"source_hash": "86501c29aea197c6", "bytes_per_launch": 820224}
 # warp instructions of one headline launch (ncu smsp__inst_executed.sum), same rule
-NCU_INST = {"source_hash": "986c4e1684c18792", "warp_inst_per_launch": 991232}
+NCU_INST = {"source_hash": "86501c29aea197c6", "warp_inst_per_launch": 925696}
 
 
 # ------------------------------------------------------------------ other configs

@@ -193,12 +193,12 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
                                      qz2 = dev::pack2(qz, qz);
             const unsigned wlo = (unsigned)wl;  // [wl, wh] as one unsigned range test
             const unsigned wspan = (unsigned)(wh - wl);
-            float best = -1.f;
+            float best = 0.f;
             int bi = 0;
 #pragma unroll
             for (int h = 0; h < PP; ++h) {
                 const int i0 = 2 * h;
-                if (32 * i0 < n) {  // warp-uniform: the row pair holds real points
+                if (h == 0 || 32 * i0 < n) {  // warp-uniform: the row pair holds real points (n >= 1)
                     // NPDU: every row pair is computed and the window applied as
                     // a mask, or (npdu_skip) pairs the window misses are skipped
                     // by a warp-uniform test; never a divergent branch.  With
@@ -219,11 +219,16 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
                             D[i0 + 1] = d1;
                         }
                     }
-                    bool gt = D[i0] > best;  // strict: lowest row wins ties
-                    best = gt ? D[i0] : best;
-                    bi = gt ? i0 : bi;
+                    if (h == 0) {  // row 0 starts the lane's scan
+                        best = D[0];
+                        bi = 0;
+                    } else {
+                        const bool gt = D[i0] > best;  // strict: lowest row wins ties
+                        best = gt ? D[i0] : best;
+                        bi = gt ? i0 : bi;
+                    }
                     if (i0 + 1 < P) {
-                        gt = D[i0 + 1] > best;
+                        const bool gt = D[i0 + 1] > best;
                         best = gt ? D[i0 + 1] : best;
                         bi = gt ? i0 + 1 : bi;
                     }
