@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             const int wlo = whole ? -c0 : p - kl - c0, whi = whole ? n - 1 - c0 : p + kr - c0;
             const unsigned long long qx2 = dev::pack2(qx, qx), qy2 = dev::pack2(qy, qy),
                                      qz2 = dev::pack2(qz, qz);
-            float best = -1.f;
+            float best = 0.f;
             int bi = 0;
 #pragma unroll
             for (int h = 0; h < PP; ++h) {
@@ -280,11 +280,16 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
                             D[i0 + 1] = d1;
                         }
                     }
-                    bool gt = D[i0] > best;
-                    best = gt ? D[i0] : best;
-                    bi = gt ? i0 : bi;
+                    if (h == 0) {  // row 0 starts the thread's scan
+                        best = D[0];
+                        bi = 0;
+                    } else {
+                        const bool gt = D[i0] > best;  // strict: lowest row wins ties
+                        best = gt ? D[i0] : best;
+                        bi = gt ? i0 : bi;
+                    }
                     if (i0 + 1 < P) {
-                        gt = D[i0 + 1] > best;
+                        const bool gt = D[i0 + 1] > best;
                         best = gt ? D[i0 + 1] : best;
                         bi = gt ? i0 + 1 : bi;
                     }
