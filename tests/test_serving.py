@@ -172,3 +172,33 @@ def test_cancel_queued_and_admitted(sampler):
         ref = oracle.chain(frames[t], LEVELS, 32, 16)
         for l in range(len(LEVELS)):
             assert np.array_equal(done[t].levels[l], ref[l]), (t, l)
+
+
+def test_router_over_two_replicas(sampler):
+    """Two serving runtimes behind the least-outstanding router (one per GPU
+    in a deployment; both on the one GPU here, each with its own context and
+    stream): every result equals the oracle's chained sampling, both
+    replicas serve, and all times are on the first replica's clock."""
+    from paper_2208_08795_gb300 import routing
+    s2 = B.Sampler(0)
+    reps = [B.Server(sampler, LEVELS, 32, 16, hbm_budget_bytes=64 << 20),
+            B.Server(s2, LEVELS, 32, 16, hbm_budget_bytes=64 << 20)]
+    try:
+        router = routing.ReplicaRouter(reps)
+        frames = [synth.lidar_frame(100 + s) for s in range(6)]
+        out = serving.poisson_run(router, frames, rate_hz=4000.0, n_requests=24, seed=3,
+                                  keep_results=True)
+        res = out["results"]
+        assert sorted(res) == list(range(24))
+        refs = [oracle.chain(f, LEVELS, 32, 16) for f in frames]
+        for t, r in res.items():
+            assert r.status == 0
+            for l in range(len(LEVELS)):
+                assert np.array_equal(r.levels[l], refs[t % len(frames)][l]), (t, l)
+            assert r.submit_ms <= r.admit_ms <= r.done_ms <= router.clock_ms() + 1.0
+        assert all(n > 0 for n in router.routed)
+        assert router.points == [0, 0] and not router.owner
+    finally:
+        for r in reps:
+            r.close()
+        s2.close()
