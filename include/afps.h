@@ -77,6 +77,14 @@ extern "C" {
  * wait runs out (after timeout_ns) and afps_sync returns AFPS_ERR_TIMEOUT.
  * Outputs of such calls are meaningless; the context stays usable. */
 #define AFPS_FLAG_TEST_STALL_COPY 0x100u
+/* Fault injection for tests of failure detection: every growth of the
+ * context's device workspace (item tables, work-queue counters, staging and
+ * scratch buffers) fails as it would on an exhausted device, so a call that
+ * needs more workspace than the context already holds returns
+ * AFPS_ERR_NO_MEMORY before it launches anything (its outputs untouched) and
+ * the context stays usable.  (A failed device allocation returns
+ * AFPS_ERR_NO_MEMORY with or without this flag.) */
+#define AFPS_FLAG_TEST_FAIL_ALLOC 0x200u
 
 typedef struct afps_ctx afps_ctx;
 

@@ -31,6 +31,7 @@ AFPS_MAX_SECTOR_POINTS = 131072
 AFPS_FLAG_GRAPH = 1
 AFPS_FLAG_AUTOTUNE = 2
 AFPS_FLAG_TEST_STALL_COPY = 0x100
+AFPS_FLAG_TEST_FAIL_ALLOC = 0x200
 
 # every symbol include/afps.h declares
 EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
@@ -60,6 +61,7 @@ AFPS_ERR_DEVICE_CHECK = -9
 AFPS_KEY_X, AFPS_KEY_Y, AFPS_KEY_Z, AFPS_KEY_AZIMUTH = 0, 1, 2, 3
 AFPS_METHOD_FULL_FIRST_PASS = 1
 AFPS_METHOD_WINDOW_HAS_SAMPLE = 2
+AFPS_METHOD_ALL = 3
 AFPS_SERVER_MAX_LEVELS = 8
 
 

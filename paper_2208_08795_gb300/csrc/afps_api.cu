@@ -138,7 +138,16 @@ int fail(afps_ctx* ctx, int code, const std::string& msg) {
 int cuda_fail(afps_ctx* ctx, cudaError_t e, const char* what) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
     cudaGetLastError();  // clear a sticky launch error so the context stays usable
-    return fail(ctx, AFPS_ERR_CUDA, m);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? AFPS_ERR_NO_MEMORY : AFPS_ERR_CUDA, m);
+}
+
+// Growth of a workspace buffer of the context (device or page-locked).
+// AFPS_FLAG_TEST_FAIL_ALLOC makes every growth fail as on an exhausted
+// device (fault injection).
+template <class Buf>
+cudaError_t grow(afps_ctx* ctx, Buf& b, size_t want) {
+    if (want > b.bytes && (ctx->flags & AFPS_FLAG_TEST_FAIL_ALLOC)) return cudaErrorMemoryAllocation;
+    return b.reserve(want);
 }
 
 #define AFPS_CUDA(ctx, call)                                   \
@@ -524,8 +533,8 @@ int upload(afps_ctx* ctx, DevBuf& dst, const void* src, size_t bytes, cudaStream
     const int s = ctx->stage_next;
     ctx->stage_next = (s + 1) % kStageSlots;
     AFPS_CUDA(ctx, cudaEventSynchronize(ctx->stage_ev[s]));
-    AFPS_CUDA(ctx, ctx->stage[s].reserve(bytes));
-    AFPS_CUDA(ctx, dst.reserve(bytes));
+    AFPS_CUDA(ctx, grow(ctx, ctx->stage[s], bytes));
+    AFPS_CUDA(ctx, grow(ctx, dst, bytes));
     memcpy(ctx->stage[s].p, src, bytes);
     AFPS_CUDA(ctx, cudaStreamWaitEvent(stream, ctx->ev_done, 0));
     AFPS_CUDA(ctx, cudaMemcpyAsync(dst.p, ctx->stage[s].p, bytes, cudaMemcpyHostToDevice, stream));
@@ -556,7 +565,7 @@ int build_plan_consecutive(afps_ctx* ctx, const int64_t* pt_off, int32_t B, cons
 int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* d_out,
              cudaStream_t stream, bool host_resident = false) {
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);
-    AFPS_CUDA(ctx, ctx->counters.reserve(plan.classes.size() * sizeof(unsigned int)));
+    AFPS_CUDA(ctx, grow(ctx, ctx->counters, plan.classes.size() * sizeof(unsigned int)));
     bool table = false;  // some class reads the item table
     bool queue = false;  // some class uses a work-queue counter
     for (const ClassPlan& cp : plan.classes) {
@@ -626,8 +635,8 @@ int make_graph(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t
                GraphEntry& g, const float* h_xyz = nullptr, size_t xyz_bytes = 0,
                int32_t* h_out = nullptr, size_t out_bytes = 0, bool host_resident = false) {
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);
-    AFPS_CUDA(ctx, g.items.reserve(bytes));
-    AFPS_CUDA(ctx, g.counters.reserve(plan.classes.size() * sizeof(unsigned int)));
+    AFPS_CUDA(ctx, grow(ctx, g.items, bytes));
+    AFPS_CUDA(ctx, grow(ctx, g.counters, plan.classes.size() * sizeof(unsigned int)));
     if (bytes)  // classes of equal-cloud runs need no table
         AFPS_CUDA(ctx, cudaMemcpy(g.items.p, plan.items.data(), bytes, cudaMemcpyHostToDevice));
     const ItemDesc* d_items = static_cast<const ItemDesc*>(g.items.p);
@@ -794,7 +803,7 @@ int host_graph_call(afps_ctx* ctx, const float* h_xyz, const int64_t* pt_off, in
             rc = make_graph(ctx, plan, static_cast<const float*>(dx), static_cast<int32_t*>(dout),
                             g, nullptr, 0, nullptr, 0, true);
         } else {
-            if (g.xyz.reserve(xyz_bytes) != cudaSuccess || g.out.reserve(out_bytes) != cudaSuccess) {
+            if (grow(ctx, g.xyz, xyz_bytes) != cudaSuccess || grow(ctx, g.out, out_bytes) != cudaSuccess) {
                 cudaGetLastError();
                 drop_graph(g);
                 return fail(ctx, AFPS_ERR_NO_MEMORY, "afps_sample_batched_host: device staging");
@@ -895,8 +904,8 @@ int reserve_workspace(afps_ctx* ctx, size_t bytes) {
     if (!ctx) return AFPS_ERR_INVALID_ARG;
     DeviceGuard guard(ctx->device);
     AFPS_CUDA(ctx, cudaDeviceSynchronize());  // nothing may still read the old buffers
-    AFPS_CUDA(ctx, ctx->items.reserve(bytes));
-    for (int s = 0; s < kStageSlots; ++s) AFPS_CUDA(ctx, ctx->stage[s].reserve(bytes));
+    AFPS_CUDA(ctx, grow(ctx, ctx->items, bytes));
+    for (int s = 0; s < kStageSlots; ++s) AFPS_CUDA(ctx, grow(ctx, ctx->stage[s], bytes));
     return AFPS_OK;
 }
 
@@ -1100,8 +1109,8 @@ int host_call(afps_ctx* ctx, const float* h_xyz, const int64_t* h_pt_off, int32_
             return AFPS_OK;
         }
     }
-    AFPS_CUDA(ctx, ctx->xyz_stage.reserve(xyz_bytes));
-    AFPS_CUDA(ctx, ctx->out_stage.reserve(out_bytes));
+    AFPS_CUDA(ctx, grow(ctx, ctx->xyz_stage, xyz_bytes));
+    AFPS_CUDA(ctx, grow(ctx, ctx->out_stage, out_bytes));
     AFPS_CUDA(ctx, cudaStreamWaitEvent(st, ctx->ev_done, 0));
     AFPS_CUDA(ctx, cudaMemcpyAsync(ctx->xyz_stage.p, h_xyz, xyz_bytes, cudaMemcpyHostToDevice, st));
     int rc = batched_device(ctx, static_cast<const float*>(ctx->xyz_stage.p), h_pt_off, B, h_C,
@@ -1189,7 +1198,7 @@ int afps_sort_by_key(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const fl
     const int64_t total = h_pt_off[B];
     // scratch: keys and indices, twice (ping-pong); earlier users are ordered
     // before the reallocation by cudaFree's device synchronisation
-    AFPS_CUDA(ctx, ctx->sort_scratch.reserve((size_t)total * 16 + 16));
+    AFPS_CUDA(ctx, grow(ctx, ctx->sort_scratch, (size_t)total * 16 + 16));
     int rc = upload(ctx, ctx->items, descs.data(), descs.size() * sizeof(afps::SortDesc), st);
     if (rc != AFPS_OK) return rc;
     unsigned char* base = static_cast<unsigned char*>(ctx->sort_scratch.p);
@@ -1229,7 +1238,7 @@ int afps_coverage_radius(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, cons
     }
     DeviceGuard guard(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    AFPS_CUDA(ctx, ctx->cov_scratch.reserve(sizeof(unsigned long long) * (size_t)B));
+    AFPS_CUDA(ctx, grow(ctx, ctx->cov_scratch, sizeof(unsigned long long) * (size_t)B));
     int rc = upload(ctx, ctx->items, descs.data(), descs.size() * sizeof(afps::CoverageDesc), st);
     if (rc != AFPS_OK) return rc;
     cudaError_t e = afps::launch_coverage(

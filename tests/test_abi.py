@@ -60,3 +60,19 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     with pytest.raises(B.AfpsLibraryError):
         B.load(str(tmp_path / "nope.so"))
     monkeypatch.setattr(B, "_lib", None)
+
+
+def test_python_constants_match_the_header():
+    """Every error code, flag, method and key the header defines has the
+    same value in the binding."""
+    import re
+    here = os.path.dirname(os.path.abspath(__file__))
+    text = open(os.path.join(here, "..", "include", "afps.h")).read()
+    defs = dict(re.findall(r"#define (AFPS_[A-Z0-9_]+) \(?(-?(?:0x)?[0-9a-fA-F]+)u?\)?", text))
+    checked = 0
+    for name, val in defs.items():
+        if name.startswith(("AFPS_ERR_", "AFPS_FLAG_", "AFPS_METHOD_", "AFPS_KEY_")):
+            assert hasattr(B, name), name
+            assert getattr(B, name) == int(val, 0), name
+            checked += 1
+    assert checked >= 12

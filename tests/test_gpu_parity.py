@@ -679,6 +679,42 @@ def test_bounded_wait_reports_timeout_and_context_survives():
         s2.close()
 
 
+def test_allocation_failure_is_reported_and_context_survives(objects):
+    """Fault injection on the host: every growth of the context's workspace
+    fails as on an exhausted device.  Batched calls (which need a work-queue
+    counter) return AFPS_ERR_NO_MEMORY before launching anything, their
+    outputs untouched; a server cannot reserve its tables; the context, the
+    GPU and a fresh context still work."""
+    build_mod.build()
+    xyz, off = synth.pack(objects[:4])
+    x = torch.from_numpy(xyz).cuda()
+    s = B.Sampler(0, flags=B.AFPS_FLAG_TEST_FAIL_ALLOC)
+    try:
+        for (M, k) in ((1, 0), (32, 16)):
+            ba = B.BatchArgs(off, 512, M, k, 0)
+            out = torch.full((ba.total_out,), -1, dtype=torch.int32, device="cuda")
+            with pytest.raises(B.AfpsError) as ei:
+                s.sample_batched(x, ba, out=out)
+            assert ei.value.code == B.AFPS_ERR_NO_MEMORY
+            s.sync()  # nothing was launched: no device-side error either
+            assert bool((out == -1).all())
+        with pytest.raises(B.AfpsError) as ei:
+            B.Server(s, [1024, 256], 32, 16, hbm_budget_bytes=1 << 20)
+        assert ei.value.code == B.AFPS_ERR_NO_MEMORY
+        # a single-cloud call needs no workspace and still runs on this context
+        P = objects[0]
+        assert_same(gpu_one(s, P, 512, 4, 0), oracle.afps(P, 512, 4, 0), "no-workspace call")
+    finally:
+        s.close()
+    s2 = B.Sampler(0)
+    try:
+        got, _ = gpu_batch(s2, objects[:4], 512, 32, 16)
+        for b in range(4):
+            assert_same(got[b], oracle.afps(objects[b], 512, 32, 16), f"fresh context, cloud {b}")
+    finally:
+        s2.close()
+
+
 # --------------------------------------------------------------- chained levels
 def test_chained_levels_lidar(S):
     frame = synth.lidar_frame(5)
