@@ -733,3 +733,47 @@ def test_chained_levels_lidar(S):
         assert_same(sfr.cpu().numpy(), ref[L], f"level {L}")
         assert np.all(np.diff(nfr.cpu().numpy()) > 0)
         cloud, fidx = nxt, nfr
+
+
+# --------------------------------------------------------------- random sweep
+def test_random_configurations_batched(S):
+    """A seeded random sweep through the batched entry point: ragged clouds
+    (sorted, unsorted, with repeated points) with their own C, M, window,
+    reading and start in one call, each equal to the oracle."""
+    g = np.random.Generator(np.random.PCG64(31))
+    for rep in range(4):
+        clouds, Cs, Ms, ks, starts, methods = [], [], [], [], [], []
+        while len(clouds) < 24:
+            N = int(g.integers(1, 3000))
+            M = int(g.integers(1, min(N, 64) + 1))
+            C = int(g.integers(M, min(N, 600) + 1))
+            lo = [(s * N) // M for s in range(M + 1)]
+            off = [(s * C) // M for s in range(M + 1)]
+            if any(off[s + 1] - off[s] > lo[s + 1] - lo[s] for s in range(M)):
+                continue
+            k = int(g.choice([0, 0, 2, 3, 8, 16, 33]))
+            kind = len(clouds) % 3
+            seed = 5000 + 100 * rep + len(clouds)
+            if kind == 0:
+                P = synth.uniform_cloud(seed, N)
+            elif kind == 1:
+                P = synth.uniform_cloud(seed, N, axis=None)
+            else:
+                P = np.ascontiguousarray(np.resize(synth.uniform_cloud(seed, max(1, N // 3)),
+                                                   (N, 3)).astype(np.float32))
+            clouds.append(P)
+            Cs.append(C)
+            Ms.append(M)
+            ks.append(k)
+            starts.append(int(g.integers(0, N)))
+            methods.append(int(g.integers(0, 4)) if k > 0 else 0)
+        xyz, off = synth.pack(clouds)
+        ba = B.BatchArgs(off, Cs, Ms, ks, starts, method=methods)
+        out = S.sample_batched(torch.from_numpy(xyz).cuda(), ba)
+        S.sync()
+        o = out.cpu().numpy()
+        for b, P in enumerate(clouds):
+            ref = oracle.afps(P, Cs[b], Ms[b], ks[b], starts[b], method=methods[b])
+            assert_same(o[ba.out_off[b]:ba.out_off[b + 1]], ref,
+                        f"rep {rep} cloud {b}: N={P.shape[0]} C={Cs[b]} M={Ms[b]} k={ks[b]} "
+                        f"start={starts[b]} method={methods[b]}")
