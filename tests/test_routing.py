@@ -159,7 +159,9 @@ def test_poisson_run_drives_the_router():
         ref = oracle.chain(fr[t % len(fr)], LEVELS, M, K)
         assert all(np.array_equal(r.levels[l], ref[l]) for l in range(len(LEVELS)))
     assert out["p99_ms"] >= out["p50_ms"] >= 0.0
-    assert all(n > 0 for n in router.routed)
+    # (which replicas serve depends on how the arrivals overlap: an idle
+    # router sends every frame to replica 0; the order is checked above)
+    assert sum(router.routed) == 20 and not router.owner
 
 
 # ------------------------------------------------- replicas in other processes
