@@ -186,17 +186,29 @@ def test_router_over_two_replicas(sampler):
     try:
         router = routing.ReplicaRouter(reps)
         frames = [synth.lidar_frame(100 + s) for s in range(6)]
+        refs = [oracle.chain(f, LEVELS, 32, 16) for f in frames]
+        # a burst: the frames are outstanding together, so both replicas get some
+        for t, f in enumerate(frames):
+            assert router.submit(f, 100 + t) == 0
+        burst = {}
+        while len(burst) < len(frames):
+            router.step()
+            burst.update({r.tag: r for r in router.poll()})
+        assert {r.replica for r in burst.values()} == {0, 1}
+        for t, r in burst.items():
+            for l in range(len(LEVELS)):
+                assert np.array_equal(r.levels[l], refs[t - 100][l]), (t, l)
+        # a Poisson stream through the router
         out = serving.poisson_run(router, frames, rate_hz=4000.0, n_requests=24, seed=3,
                                   keep_results=True)
         res = out["results"]
         assert sorted(res) == list(range(24))
-        refs = [oracle.chain(f, LEVELS, 32, 16) for f in frames]
         for t, r in res.items():
             assert r.status == 0
             for l in range(len(LEVELS)):
                 assert np.array_equal(r.levels[l], refs[t % len(frames)][l]), (t, l)
             assert r.submit_ms <= r.admit_ms <= r.done_ms <= router.clock_ms() + 1.0
-        assert all(n > 0 for n in router.routed)
+        assert sum(router.routed) == 30
         assert router.points == [0, 0] and not router.owner
     finally:
         for r in reps:
