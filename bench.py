@@ -1,24 +1,28 @@
 """Benchmark: NPDU-AFPS vs plain FPS on one GB300, clouds/s and p99 ms.
 
-Workload (one step): a batch of 32 object-scale clouds of 2048 points
-(2-5 primitive surfaces, jitter 0.005, unit ball, sorted by x), C = 512
-samples each, NPDU-AFPS with M = 32 sectors and window k = 16, all clouds in
-one batched call (graph-replayed).  Beside it, in the same run: plain FPS
-(M = 1, no NPDU) on the same batch, the sweep M in {1, 4, 16, 32} with NPDU
-off/on, the end-to-end time through host buffers, the roofline of the
-sampling kernel, and the CPU oracle on the host's cores.
+Headline workload (one step): the ragged batch of 256 object-scale clouds
+(N ~ U[2048, 32768], seed 3; 2-5 primitive surfaces, jitter 0.005, unit
+ball, sorted by x), C = N/4, M = max(1, round(N/256)) sectors of about 256
+points, NPDU window k = 8 for M <= 8 and 16 for M >= 16 (Sec. IV-D); all
+17,576 (cloud, sector) items in one batched call through the C ABI, replayed
+from a CUDA graph, kernel variant chosen by the autotuner (untimed).  Beside
+it, on the same batch and in the same run: plain FPS (M = 1, no NPDU) and
+AFPS without NPDU, the end-to-end time through host buffers, the roofline of
+the sampling kernel and the CPU oracle on the host's cores.
 
-Timing.  Throughput (`value`, `ms_per_step`): K steps between two CUDA
-events, step i on stream i mod S (S = 8 by default: the steps of a stream
-run back to back, the streams side by side, as independent batches would),
-each step on the next of R resident copies of the batch (R copies span twice
-the L2), so every timed step reads cold points without a flush; a
-fixed-length sleep kernel ahead of the first event holds the streams while
-the host enqueues the K steps, so the host's call rate does not set the pace
-(the host path is what `e2e` measures).  `one_stream` repeats it on a single
-stream.  Latency (`p50_ms`, `p99_ms`): isolated steps, each after a 256 MB
-write that flushes the L2, with its own pair of events.  The CPU oracle runs
-one worker process per host core.
+Timing.  Throughput (`value`, `ms_per_step`): K steps back to back on one
+stream between two CUDA events on that stream; step i runs on the next of R
+resident copies of the batch (the copies span twice the L2), so every timed
+step reads cold points without a flush; a fixed-length sleep kernel ahead of
+the first event holds the stream while the host enqueues the K steps.
+Latency (`p50_ms`, `p99_ms`): isolated steps, each after a 256 MB write that
+flushes the L2, with its own pair of events.  The end-to-end number (`e2e`)
+is the same metric through host buffers on the host clock.  The CPU oracle
+runs one worker process per host core.
+
+Secondary sections: the object batch of 32 x 2048 points (M in {1, 4, 16,
+32}, NPDU off and on, one stream), single large clouds, the paper's Table IV
+sweep, sorting, grouping and the serving runtime.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -29,7 +33,6 @@ over ranks.
 from __future__ import annotations
 
 import argparse
-import concurrent.futures as cf
 import json
 import os
 import statistics
@@ -46,9 +49,11 @@ if ROOT not in sys.path:
 
 METRIC = "clouds/s & p99 ms, NPDU-AFPS vs plain FPS on 1 GB300, indices = FP32 oracle"
 UNIT = "clouds/s"
+RAGGED_CLOUDS, RAGGED_SECTOR = 256, 256
+WORKLOAD = ("ragged batch of 256 clouds, N ~ U[2048, 32768] (seed 3), C = N/4, "
+            "M = round(N/256), NPDU-AFPS k = 8 (M <= 8) / 16 (M >= 16)")
+# the object batch (secondary section): 32 x 2048 points, C = 512
 B_CLOUDS, N_POINTS, C_SAMPLES, M_SECTORS, K_WINDOW = 32, 2048, 512, 32, 16
-WORKLOAD = (f"object batch {B_CLOUDS} x {N_POINTS} pts, C={C_SAMPLES}, "
-            f"NPDU-AFPS M={M_SECTORS} k={K_WINDOW}")
 L2_FLUSH_BYTES = 256 << 20
 L2_BYTES = 129 << 20  # GB300 L2
 FALLBACK_HBM_GBS = 6800.0
@@ -68,8 +73,8 @@ def rank_info():
 
 
 def batch_seed(rank: int) -> int:
-    """Each rank samples its own batch (weak scaling)."""
-    return 1 + rank
+    """Each rank samples its own ragged batch (weak scaling)."""
+    return 3 + rank
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -134,7 +139,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ inputs
+def make_ragged(seed: int):
+    """The ragged batch: clouds, per-cloud C, M and NPDU window."""
+    from paper_2208_08795_gb300 import synth
+    clouds, Cs, Ms = synth.ragged_batch(seed, RAGGED_CLOUDS, sector_points=RAGGED_SECTOR)
+    ks = [k_rule(M) for M in Ms]
+    return clouds, Cs, Ms, ks
+
+
 def make_batch(seed: int):
+    """The object batch (32 x 2048 points)."""
     from paper_2208_08795_gb300 import synth
     clouds = synth.object_batch(seed, B_CLOUDS, N_POINTS)
     xyz, off = synth.pack(clouds)
@@ -154,47 +168,62 @@ def measured_hbm_peak():
 _ORACLE_WORK = None
 
 
-def _oracle_init(clouds, C, M, k):
+def _oracle_init(clouds, Cs, Ms, ks):
     global _ORACLE_WORK
-    _ORACLE_WORK = (clouds, C, M, k)
+    _ORACLE_WORK = (clouds, Cs, Ms, ks)
 
 
 def _oracle_chunk(lo: int, hi: int, reps: int):
     """Clouds [lo, hi) of the batch through the oracle, `reps` times; returns
     the last pass's indices."""
     import oracle
-    clouds, C, M, k = _ORACLE_WORK
+    clouds, Cs, Ms, ks = _ORACLE_WORK
     out = None
     for _ in range(reps):
-        out = [oracle.afps(clouds[i], C, M, k, 0) for i in range(lo, hi)]
+        out = [oracle.afps(clouds[i], Cs[i], Ms[i], ks[i], 0) for i in range(lo, hi)]
     return out
+
+
+def balanced_chunks(sizes, parts: int):
+    """Contiguous ranges of the clouds with about equal total points each."""
+    total = float(sum(sizes))
+    bounds, acc, b = [0], 0.0, 1
+    for i, s in enumerate(sizes):
+        acc += s
+        if b < parts and acc >= total * b / parts and i + 1 < len(sizes):
+            bounds.append(i + 1)
+            b += 1
+    bounds.append(len(sizes))
+    return [(bounds[i], bounds[i + 1]) for i in range(len(bounds) - 1)
+            if bounds[i + 1] > bounds[i]]
 
 
 class OraclePool:
     """The oracle, as it stands, over one batch on `procs` host cores: worker
     processes (started with spawn, so safe after CUDA use) that each hold the
-    batch and run a contiguous chunk of its clouds.  Processes rather than
-    threads: the oracle's Python wrapper holds the GIL for about a sixth of a
-    call, which capped 16 threads at 1.3x one."""
+    batch and run a contiguous chunk of its clouds (chunks of about equal
+    points).  Processes rather than threads: the oracle's Python wrapper
+    holds the GIL for part of each call."""
 
-    def __init__(self, clouds, C, M, k, procs: int):
-        self.n, self.procs = len(clouds), max(1, min(procs, len(clouds)))
+    def __init__(self, clouds, Cs, Ms, ks, procs: int):
+        self.n = len(clouds)
+        self.chunks = balanced_chunks([c.shape[0] for c in clouds], max(1, procs))
+        self.procs = len(self.chunks)
         self.pool = None
         if self.procs == 1:
-            _oracle_init(clouds, C, M, k)
+            _oracle_init(clouds, Cs, Ms, ks)
         else:
             import multiprocessing as mp
             self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_oracle_init,
-                                                     initargs=(clouds, C, M, k))
+                                                     initargs=(clouds, Cs, Ms, ks))
 
     def run(self, reps: int = 1):
         """The batch `reps` times; returns the last pass's indices per cloud."""
         if self.pool is None:
             return _oracle_chunk(0, self.n, reps)
-        bounds = [(self.n * i // self.procs, self.n * (i + 1) // self.procs, reps)
-                  for i in range(self.procs)]
         out = []
-        for part in self.pool.starmap(_oracle_chunk, bounds, chunksize=1):
+        for part in self.pool.starmap(_oracle_chunk, [(a, b, reps) for a, b in self.chunks],
+                                      chunksize=1):
             out.extend(part)
         return out
 
@@ -205,22 +234,21 @@ class OraclePool:
             self.pool = None
 
 
-def time_oracle(clouds, C, M, k, budget_s: float, procs: int):
+def time_oracle(clouds, Cs, Ms, ks, budget_s: float, procs: int):
     """The oracle as it stands on `procs` cores: whole batches, repeated for
-    about budget_s.  Returns (clouds/s, batches, indices per cloud)."""
-    pool = OraclePool(clouds, C, M, k, procs)
+    about budget_s.  Returns (clouds/s, batches, indices per cloud, processes)."""
+    pool = OraclePool(clouds, Cs, Ms, ks, procs)
     try:
-        outs = pool.run(1)  # starts the workers and warms the library
         t0 = time.perf_counter()
-        pool.run(10)
-        once = (time.perf_counter() - t0) / 10
+        outs = pool.run(1)  # starts the workers and warms the library
+        once = time.perf_counter() - t0
         reps = max(1, min(100000, int(budget_s / max(once, 1e-6))))
         t0 = time.perf_counter()
         pool.run(reps)
         el = time.perf_counter() - t0
     finally:
         pool.close()
-    return reps * len(clouds) / el, reps, outs
+    return reps * len(clouds) / el, reps, outs, pool.procs
 
 
 def cpu_threads() -> int:
@@ -260,34 +288,30 @@ def rotation(x, total_out: int, dev):
     in more than 2 x L2 of traffic reads its points from DRAM."""
     import torch
     slot_bytes = x.numel() * 4 + total_out * 4
-    R = max(8, -(-2 * L2_BYTES // slot_bytes))
+    R = max(4, -(-2 * L2_BYTES // slot_bytes))
     xr = x.unsqueeze(0).repeat(R, *([1] * x.dim())).contiguous()
     outr = torch.full((R, total_out), -1, dtype=torch.int32, device=dev)
     return xr, outr
 
 
-def time_stream(sampler, xr, outr, ba, steps: int, warmup: int, n_streams: int = 1):
-    """Whole-job throughput: K steps issued through the C ABI
-    (afps_sample_batched on a context without graphs: one direct kernel
-    launch per step; hundreds of distinct graphs, one per slot, were measured
-    to launch slower than that when queued), each on the next resident slot
-    of the rotation.  Step i goes to stream i mod S: the steps of one stream
-    run back to back, the S streams side by side (independent batches; a
-    step's kernel leaves most of the GPU idle, so they overlap).  One pair of
-    CUDA events on the launching stream brackets the K steps; every stream
-    waits for the first event and the second waits for every stream.  Every
-    slot is run once first (untimed); the timed steps start at the least
-    recently used slot, so every one of them reads cold points.  Returns (ms
-    per step, launches in the timed region, last slot used, enqueue
-    information)."""
+def time_steps(sampler, xr, outr, ba, steps: int, warmup: int):
+    """Whole-job throughput on one stream: K steps issued through the C ABI
+    (afps_sample_batched: a graph replay on a graph context, a direct launch
+    otherwise), each on the next resident slot of the rotation, back to back.
+    One pair of CUDA events on the stream brackets the K steps.  Every slot
+    is run once first (untimed; a graph context captures its graphs there);
+    the timed steps start at the least recently used slot, so every one of
+    them reads cold points.  A fixed-length sleep kernel before the first
+    event holds the stream while the host enqueues the steps, so the host's
+    call rate does not set the pace.  Returns (ms per step, launches in the
+    timed region, last slot used, enqueue information)."""
     import torch
     from paper_2208_08795_gb300 import afps as A
     fn = A.load().afps_sample_batched
-    main = torch.cuda.current_stream()
-    streams = [main] + [torch.cuda.Stream() for _ in range(n_streams - 1)]
+    stream = torch.cuda.current_stream()
     R = xr.shape[0]
-    args = [(sampler.ctx, xr[i % R].data_ptr(), *ba.args(), outr[i % R].data_ptr(),
-             streams[i % n_streams].cuda_stream) for i in range(R)]
+    args = [(sampler.ctx, xr[i].data_ptr(), *ba.args(), outr[i].data_ptr(), stream.cuda_stream)
+            for i in range(R)]
 
     def call(i):
         if fn(*args[i % R]) != 0:
@@ -301,24 +325,15 @@ def time_stream(sampler, xr, outr, ba, steps: int, warmup: int, n_streams: int =
         call(i)
     torch.cuda.synchronize()
     per_call = (time.perf_counter() - t0) / warmup
-    # Hold the streams (a fixed-length sleep kernel before the first event)
-    # while the K steps are enqueued, so that the GPU runs them without
-    # waiting for the host, whose per-call cost does not set the pace.
-    hold_s = min(3.0 * per_call * steps + 1e-3, 0.05)
+    hold_s = min(3.0 * per_call * steps + 1e-3, 0.2)
     torch.cuda._sleep(int(hold_s * 2.07e9))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n0 = sampler.launch_count
-    e0.record(main)
-    for st in streams[1:]:
-        st.wait_event(e0)
+    e0.record(stream)
     t0 = time.perf_counter()
     for i in range(warmup, warmup + steps):
         call(i)
-    for st in streams[1:]:
-        ev = torch.cuda.Event()
-        ev.record(st)
-        main.wait_event(ev)
-    e1.record(main)
+    e1.record(stream)
     enqueue_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     sampler.sync()
@@ -328,49 +343,47 @@ def time_stream(sampler, xr, outr, ba, steps: int, warmup: int, n_streams: int =
             info)
 
 
-def time_e2e_stream(sampler, xyz, ba, steps: int, warmup: int, expect, n_streams: int = 1):
-    """End to end through the public API, pipelined: K calls of
-    afps_sample_batched_host_async (a context without graphs: its kernels
-    read the points from, and write the indices to, page-locked host memory
-    over the C2C link), call i on stream i mod S, then one synchronisation of
-    the device, timed on the host clock.  Step i reads input copy i mod R (R
-    copies span twice the L2, so no step finds its points cached) and writes
-    its own output buffer; every output is checked against `expect`
-    afterwards.  Returns (ms per step, input bytes per step, output bytes per
-    step)."""
+def time_e2e_stream(sampler, xyz, ba, steps: int, warmup: int, expect):
+    """End to end through the public API: K calls of
+    afps_sample_batched_host_async on page-locked host buffers (a graph
+    context: one replay per call; the kernels read the points from, and write
+    the indices to, host memory over the C2C link), one stream, then one
+    synchronisation, timed on the host clock.  Step i reads input copy i mod R
+    and writes output copy i mod R (the copies span twice the L2); every
+    output is checked against `expect` afterwards.  Returns (ms per step,
+    input bytes per step, output bytes per step)."""
     import torch
     from paper_2208_08795_gb300 import afps as A
     fn = A.load().afps_sample_batched_host_async
-    streams = [torch.cuda.current_stream()] + [torch.cuda.Stream() for _ in range(n_streams - 1)]
+    stream = torch.cuda.current_stream()
     slot = xyz.nbytes + ba.total_out * 4
-    R = max(8, -(-2 * L2_BYTES // slot))
+    R = max(4, -(-2 * L2_BYTES // slot))
     hx = torch.from_numpy(xyz).unsqueeze(0).repeat(R, 1, 1).pin_memory()
-    ho = torch.full((warmup + steps, ba.total_out), -1, dtype=torch.int32).pin_memory()
-    args = [(sampler.ctx, hx[i % R].data_ptr(), *ba.args(), ho[i].data_ptr(),
-             streams[i % n_streams].cuda_stream) for i in range(warmup + steps)]
+    ho = torch.full((R, ba.total_out), -1, dtype=torch.int32).pin_memory()
+    args = [(sampler.ctx, hx[i].data_ptr(), *ba.args(), ho[i].data_ptr(), stream.cuda_stream)
+            for i in range(R)]
 
     def call(i):
-        if fn(*args[i]) != 0:
+        if fn(*args[i % R]) != 0:
             raise A.AfpsError(-1, A.afps_last_error(sampler.ctx))
 
-    for i in range(warmup):
+    for i in range(max(R, warmup)):  # captures every slot's graph, then warms
         call(i)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i in range(warmup, warmup + steps):
+    for i in range(steps):
         call(i)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / steps
     sampler.sync()
-    if not bool((ho[warmup:] == torch.from_numpy(expect).unsqueeze(0)).all()):
+    if not bool((ho == torch.from_numpy(expect).unsqueeze(0)).all()):
         raise RuntimeError("an end-to-end step differs from the device path")
     return ms, xyz.nbytes, ba.total_out * 4
 
 
-def time_e2e(sampler, h_xyz, ba, h_out, steps: int, warmup: int):
-    """The C-ABI call afps_sample_batched_host on pinned host buffers: the
-    host-to-device copy of the points, the sampling and the device-to-host copy
-    of the indices are inside each timed call (which returns after the copy)."""
+def time_e2e_sync(sampler, h_xyz, ba, h_out, steps: int, warmup: int):
+    """One synchronous afps_sample_batched_host call at a time (page-locked
+    buffers): the latency a caller sees for a single batch."""
     import torch
     from paper_2208_08795_gb300 import afps as A
     fn = A.load().afps_sample_batched_host
@@ -397,32 +410,35 @@ def pct(xs, q):
     return float(np.percentile(np.asarray(xs), q))
 
 
-def npdu_work(out_idx, ba, k):
+def npdu_work(out_idx, ba, k=None):
     """Algorithmic work of one batch: distance evaluations (window sizes, or
-    whole sectors) and argmax compares, from the sector plan and the output."""
+    whole sectors) and argmax compares, from the sector plan and the output.
+    k: the window of every cloud, or None for each cloud's own (ba.k)."""
     evals = compares = 0
     for b in range(ba.B):
         N = int(ba.pt_off[b + 1] - ba.pt_off[b])
         C, M = int(ba.C[b]), int(ba.M[b])
+        kb = int(ba.k[b]) if k is None else k
         idx = out_idx[ba.out_off[b]:ba.out_off[b] + C]
         for s in range(M):
             lo, hi = s * N // M, (s + 1) * N // M
             o0, o1 = s * C // M, (s + 1) * C // M
             n = hi - lo
             compares += (o1 - o0 - 1) * n
-            for p in idx[o0:o1 - 1] - lo:
-                if k > 0:
-                    evals += int(min(n - 1, p + (k - k // 2)) - max(0, p - k // 2) + 1)
-                else:
-                    evals += n
+            p = idx[o0:o1 - 1].astype(np.int64) - lo
+            if kb > 0:
+                evals += int((np.minimum(n - 1, p + (kb - kb // 2))
+                              - np.maximum(0, p - kb // 2) + 1).sum())
+            else:
+                evals += n * len(p)
     return evals, compares
 
 
-HEADLINE_KERNEL_SOURCES = ("afps_warp.cu", "afps_device.cuh", "afps_internal.h")
+HEADLINE_KERNEL_SOURCES = ("afps_win.cu", "afps_device.cuh", "afps_internal.h")
 
 
 def kernel_source_hash() -> str:
-    """Hash of the sources the headline kernel (afps_warp_kernel) is built from."""
+    """Hash of the sources the headline kernel (afps_win_kernel) is built from."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2208_08795_gb300", "csrc")
@@ -433,11 +449,11 @@ def kernel_source_hash() -> str:
 
 
 # DRAM traffic of the headline kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum per launch), valid only for the kernel sources it was
-# taken on (their hash); otherwise reported as null.
-NCU_TRAFFIC = {"source_hash": "86501c29aea197c6", "bytes_per_launch": 820224}
+# dram__bytes_write.sum of one launch over the ragged batch), valid only for
+# the kernel sources it was taken on (their hash); otherwise reported as null.
+NCU_TRAFFIC = {"source_hash": None, "bytes_per_launch": None}
 # warp instructions of one headline launch (ncu smsp__inst_executed.sum), same rule
-NCU_INST = {"source_hash": "86501c29aea197c6", "warp_inst_per_launch": 925696}
+NCU_INST = {"source_hash": None, "warp_inst_per_launch": None}
 
 
 # ------------------------------------------------------------------ other configs
@@ -505,28 +521,6 @@ def table_iv(sampler, flush, dev, steps: int):
                         "simulated 64-core accelerator, context only", "rows": rows}
 
 
-def ragged_batch(sampler, flush, dev, steps: int):
-    """256 object-scale clouds, N ~ U[2048, 32768], C = N/4, M = round(N/256)
-    (sectors of about 256 points), NPDU k = 16: all (cloud, sector) items in
-    one persistent launch, replayed from a CUDA graph, variant autotuned."""
-    import torch
-    from paper_2208_08795_gb300 import afps as A, synth
-    clouds, Cs, Ms = synth.ragged_batch(3, 256)
-    xyz, off = synth.pack(clouds)
-    x = torch.from_numpy(xyz).to(dev)
-    res = {}
-    for k in (0, 16):
-        ba = A.BatchArgs(off, Cs, Ms, k, 0)
-        out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
-        ms, p99 = time_batch(sampler, x, ba, out, steps, 3, flush)
-        res["npdu" if k else "full"] = {"ms": round(ms, 4), "p99_ms": round(p99, 4),
-                                        "clouds_per_s": round(256 / (ms / 1e3), 1),
-                                        "hbm_gbs": round((12 * int(off[-1]) + 4 * ba.total_out)
-                                                         / (ms / 1e3) / 1e9, 1)}
-    return {"workload": f"ragged batch of 256 clouds, {int(off[-1])} points, "
-                        f"{sum(Ms)} sectors, C=N/4", **res}
-
-
 def sort_section(sampler, flush, dev, steps: int):
     """Device sort by x of unsorted input: the object batch (32 x 2048) and a
     32768-point slab cloud, each in random storage order."""
@@ -555,7 +549,7 @@ def sort_section(sampler, flush, dev, steps: int):
         torch.cuda.synchronize()
         ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
         rows[name] = {"ms": round(ms, 4), "points_per_s": round(int(off[-1]) / (ms / 1e3), 1)}
-    return {"workload": "stable radix sort by x of shuffled clouds (one CTA per cloud)", **rows}
+    return {"workload": "stable radix sort by x of shuffled clouds", **rows}
 
 
 def group_section(sampler, x, off, flush, dev, steps: int):
@@ -650,19 +644,19 @@ def serving_sweep(sampler, seconds_per_rate: float = 0.25):
 
 # ------------------------------------------------------------------ arms
 def run_reference(args, rank: int, world: int) -> int:
-    """The oracle, as it stands, on the host cores: the reference arm.  One
-    step = `batches` whole batches (about 50 ms of work, so that handing the
-    work to the processes costs little), timed on the host clock."""
+    """The oracle, as it stands, on the host cores: the reference arm, on the
+    headline workload.  One step = `batches` whole ragged batches (at least
+    one; about 50 ms of work), timed on the host clock."""
     if rank != 0:
         return 0
-    clouds, _, _ = make_batch(batch_seed(0))
+    clouds, Cs, Ms, ks = make_ragged(batch_seed(0))
     procs = cpu_threads()
-    pool = OraclePool(clouds, C_SAMPLES, M_SECTORS, K_WINDOW, procs)
+    pool = OraclePool(clouds, Cs, Ms, ks, procs)
     try:
-        pool.run(1)
         t0 = time.perf_counter()
-        pool.run(10)
-        batches = max(1, int(0.05 / max((time.perf_counter() - t0) / 10, 1e-6)))
+        pool.run(1)
+        once = time.perf_counter() - t0
+        batches = max(1, int(0.05 / max(once, 1e-6)))
         for _ in range(args.warmup):
             pool.run(batches)
         ts = []
@@ -673,19 +667,20 @@ def run_reference(args, rank: int, world: int) -> int:
     finally:
         pool.close()
     ms = float(np.mean(ts))
-    value = B_CLOUDS * batches / (ms / 1e3)
+    value = RAGGED_CLOUDS * batches / (ms / 1e3)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "p99_ms": pct(ts, 99),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "clouds": B_CLOUDS, "N": N_POINTS, "C": C_SAMPLES,
-                   "M": M_SECTORS, "k": K_WINDOW, "parallelism": f"{procs} host processes",
+        "config": {"workload": WORKLOAD, "clouds": RAGGED_CLOUDS,
+                   "points": int(sum(c.shape[0] for c in clouds)), "samples": int(sum(Cs)),
+                   "sectors": int(sum(Ms)), "parallelism": f"{pool.procs} host processes",
                    "batches_per_step": batches},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
-                         "sample": f"{args.steps} steps of {batches} whole batches of "
-                                   f"{B_CLOUDS} clouds, one process per core, each a "
-                                   f"contiguous chunk of the batch's clouds"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+                         "sample": f"{args.steps} steps of {batches} whole ragged batch(es) of "
+                                   f"{RAGGED_CLOUDS} clouds, one process per core, each a "
+                                   f"contiguous chunk of the clouds (about equal points)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line, default=_json_default))
@@ -701,12 +696,15 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         dist.init_process_group("nccl", device_id=dev)
     from paper_2208_08795_gb300 import afps as A
     from paper_2208_08795_gb300 import build as build_mod
+    from paper_2208_08795_gb300 import synth
     if local == 0:
         build_mod.build()
     if world > 1:
         torch.distributed.barrier()
 
-    clouds, xyz, off = make_batch(batch_seed(rank))
+    clouds, Cs, Ms, ks = make_ragged(batch_seed(rank))
+    xyz, off = synth.pack(clouds)
+    n_clouds = len(clouds)
     sampler = A.Sampler(local, graph=True)
     x = torch.from_numpy(xyz).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -718,223 +716,185 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         if world > 1:
             torch.distributed.barrier()
 
-    plans = {}
-
-    rot = {}
-
-    def run(M, k, steps, warmup, latency=False, n_streams=args.streams):
-        """Throughput over the rotation (steps back to back on each of
-        n_streams streams), and with latency=True also per-step latency of
-        isolated steps after an L2 flush."""
-        ba = A.BatchArgs(off, C_SAMPLES, M, k, 0)
-        out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
-        # untimed: the autotuner picks the kernel variant (and writes the result)
-        sampler.autotune_batched(x, ba, out)
-        sampler.sync()
-        n_s, c_s = -(-N_POINTS // M), -(-C_SAMPLES // M)
-        plans[f"M{M}_{'npdu' if k else 'full'}"] = sampler.describe_plan(n_s, c_s, k, B_CLOUDS * M)
-        xr, outr = rotation(x, ba.total_out, dev)
-        rot["slots"], rot["mb"] = xr.shape[0], (xr.numel() + outr.numel()) * 4 / 2**20
-        # a context without graphs for the throughput, with the variant just tuned
-        tune = os.path.join(tempfile.gettempdir(), f"afps_bench_tune_{os.getpid()}.txt")
-        A.afps_save_tuning(sampler.ctx, tune)
-        direct = A.Sampler(local, tune_cache=tune)
-        try:
-            if direct.describe_plan(n_s, c_s, k, B_CLOUDS * M) != plans[f"M{M}_{'npdu' if k else 'full'}"]:
-                raise RuntimeError("the throughput context did not load the tuned variant")
-            barrier()
-            ms, launches, last, rot["enqueue"] = time_stream(direct, xr, outr, ba, steps, warmup,
-                                                             n_streams)
-            barrier()
-        finally:
-            direct.close()
-            os.unlink(tune)
-        if not torch.equal(outr[last], out):
-            raise RuntimeError(f"M={M} k={k}: a rotated step differs from the single call")
-        del xr, outr
-        lat = None
-        if latency:
-            lat, _ = time_device(sampler, x, ba, out, steps, warmup, flush)
-            barrier()
-        return ba, out, ms, lat, launches
-
-    # headline: NPDU-AFPS M=32 k=16
-    ba, out, ms, lat, launches = run(M_SECTORS, K_WINDOW, args.steps, args.warmup, latency=True)
+    # ---------------------------------------------------------- headline
+    ba = A.BatchArgs(off, Cs, Ms, ks, 0)
+    out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
+    sampler.autotune_batched(x, ba, out)  # untimed: every shape class tuned
+    sampler.sync()
+    head_out = sampler.sample_batched(x, ba).cpu().numpy()
+    xr, outr = rotation(x, ba.total_out, dev)
+    slots, rot_mb = xr.shape[0], (xr.numel() + outr.numel()) * 4 / 2**20
+    barrier()
+    ms, launches, last, enqueue = time_steps(sampler, xr, outr, ba, args.steps, args.warmup)
+    barrier()
+    if not np.array_equal(outr[last].cpu().numpy(), head_out):
+        raise RuntimeError("a timed step differs from the single call")
+    del xr, outr
     ms_step = max_over_ranks(ms, world, dev)
-    p99 = max_over_ranks(pct(lat, 99), world, dev)
+    value = n_clouds * world / (ms_step / 1e3)
+    lat, _ = time_device(sampler, x, ba, out, args.steps, args.warmup, flush)
+    barrier()
     p50 = max_over_ranks(pct(lat, 50), world, dev)
+    p99 = max_over_ranks(pct(lat, 99), world, dev)
     iso_ms = max_over_ranks(float(np.mean(lat)), world, dev)
-    value = B_CLOUDS * world / (ms_step / 1e3)
-    head_out = out.cpu().numpy()
-    head_enqueue = dict(rot["enqueue"])
-    # the same steps on one stream (each step waits for the one before)
-    _, _, ms1, _, _ = run(M_SECTORS, K_WINDOW, args.steps, args.warmup, n_streams=1)
-    ms_one = max_over_ranks(ms1, world, dev)
+    launches_per_step = launches / args.steps
 
-    # plain FPS on the same batch, same protocol
-    _, _, ms_f, _, _ = run(1, 0, args.steps, args.warmup)
-    ms_fps = max_over_ranks(ms_f, world, dev)
-    fps_value = B_CLOUDS * world / (ms_fps / 1e3)
-    _, _, ms_f1, _, _ = run(1, 0, max(3, min(args.steps, 50)), max(3, args.warmup // 2),
-                            n_streams=1)
-    ms_fps_one = max_over_ranks(ms_f1, world, dev)
+    # plain FPS and AFPS without NPDU on the same batch, same protocol
+    def arm(M, k, steps, warmup):
+        b = A.BatchArgs(off, Cs, M, k, 0)
+        o = torch.empty(b.total_out, dtype=torch.int32, device=dev)
+        sampler.autotune_batched(x, b, o)
+        sampler.sync()
+        xr2, outr2 = rotation(x, b.total_out, dev)
+        barrier()
+        m, _, _, _ = time_steps(sampler, xr2, outr2, b, steps, warmup)
+        barrier()
+        del xr2, outr2
+        return max_over_ranks(m, world, dev)
 
-    # sweep of the paper's M values, NPDU off / on
-    sweep = {}
-    sw_steps = max(3, min(args.steps, 50))
-    for M in (1, 4, 16, 32):
-        for npdu in (False, True):
-            k = k_rule(M) if npdu else 0
-            _, _, ms_s, _, _ = run(M, k, sw_steps, max(3, args.warmup // 2))
-            m = max_over_ranks(ms_s, world, dev)
-            sweep[f"M{M}_{'npdu' if npdu else 'full'}"] = round(B_CLOUDS * world / (m / 1e3), 1)
+    fps_steps, fps_warm = max(3, min(args.steps, 5)), 3
+    ms_fps = arm(1, 0, fps_steps, fps_warm)
+    ms_full = arm(Ms, 0, max(3, min(args.steps, 20)), 3)
 
     # end to end through host buffers: pipelined calls (the throughput) and
     # one synchronous call at a time (the latency of a call)
-    tune = os.path.join(tempfile.gettempdir(), f"afps_bench_tune_{os.getpid()}.txt")
-    A.afps_save_tuning(sampler.ctx, tune)
-    direct = A.Sampler(local, tune_cache=tune)
-    try:
-        barrier()
-        e2e_ms, h2d_bytes, d2h_bytes = time_e2e_stream(direct, xyz, ba, args.steps, args.warmup,
-                                                       head_out, args.streams)
-        barrier()
-    finally:
-        direct.close()
-        os.unlink(tune)
+    e2e_ms, h2d_bytes, d2h_bytes = time_e2e_stream(sampler, xyz, ba, args.steps, args.warmup,
+                                                   head_out)
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     h_xyz = torch.from_numpy(xyz).pin_memory().numpy()
     h_out = torch.empty(ba.total_out, dtype=torch.int32).pin_memory().numpy()
     barrier()
-    ts = time_e2e(sampler, h_xyz, ba, h_out, args.steps, args.warmup)
+    ts = time_e2e_sync(sampler, h_xyz, ba, h_out, max(3, min(args.steps, 10)), 3)
     barrier()
     e2e_call_ms = max_over_ranks(float(np.mean(ts)), world, dev)
+    e2e_ok = bool(np.array_equal(h_out, head_out))
+
+    # ---------------------------------------------------------- object batch (config 2)
+    obj = object_batch_section(args, sampler, dev, world, barrier) if args.configs else None
     serving_stats = serving_sweep(sampler) if args.serving else None
     extra_steps = max(5, min(args.steps, 20))
     large = large_clouds(sampler, flush, dev, extra_steps) if args.configs else None
     tab4 = table_iv(sampler, flush, dev, extra_steps) if args.configs else None
-    ragged = ragged_batch(sampler, flush, dev, extra_steps) if args.configs else None
     sorting = sort_section(sampler, flush, dev, extra_steps) if args.configs else None
-    grouping = group_section(sampler, x, off, flush, dev, extra_steps) if args.configs else None
+    grouping = None
+    if args.configs:
+        _, oxyz, ooff = make_batch(1 + rank)
+        grouping = group_section(sampler, torch.from_numpy(oxyz).to(dev), ooff, flush, dev,
+                                 extra_steps)
     clk = clocks.stop()
-    e2e_ok = bool(np.array_equal(h_out, head_out))
 
-    # roofline of the sampling kernel (one launch per step).  With S streams
-    # S launches run side by side: the GPU completes one every ms, and each
-    # launch lasts about S x ms on its own stream.  achieved = the bytes the
-    # launches of the timed region move together / the timed region.
+    # roofline of the sampling kernel: one launch per step (the merged
+    # window-kernel class; `launches_per_step` says so), its duration the
+    # timed region / K on the launching stream
     peak, peak_kind = measured_hbm_peak()
     hbm_bytes = 12 * int(off[-1]) + 4 * int(ba.total_out)
-    kernel_s = ms / 1e3  # timed region / launches
-    achieved = hbm_bytes / kernel_s / 1e9
-    evals, compares = npdu_work(head_out, ba, K_WINDOW)
+    kernel_s = ms / 1e3 / max(launches_per_step, 1.0)
+    achieved = hbm_bytes / (ms / 1e3) / 1e9
+    evals, compares = npdu_work(head_out, ba)
     sm_mhz = clk["sm_mhz"] or 2070.0
-    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # FP32 lanes x clock, Tops/s
-    alu_ach = (9 * evals + compares) / kernel_s / 1e12
-    traffic = (NCU_TRAFFIC["bytes_per_launch"]
-               if NCU_TRAFFIC["source_hash"] == kernel_source_hash() else None)
-    # issue: executed warp instructions (an ncu count of one launch of these
-    # kernel sources) x launches / timed region, against every scheduler
-    # issuing one per cycle -- how busy the SMs are, not algorithmic work
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    inst = (NCU_INST["warp_inst_per_launch"]
-            if NCU_INST["source_hash"] == kernel_source_hash() else None)
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12  # FP32 lanes x clock, Tops/s
+    alu_ach = (9 * evals + compares) / (ms / 1e3) / 1e12
+    src = kernel_source_hash()
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["source_hash"] == src else None
+    inst = NCU_INST["warp_inst_per_launch"] if NCU_INST["source_hash"] == src else None
     issue_peak = n_sm * 4 * sm_mhz * 1e6
     issue = None if inst is None else {
         "bound": "issue", "achieved": inst / kernel_s, "peak": issue_peak,
         "unit": "warp instructions/s", "frac": inst / kernel_s / issue_peak,
         "warp_inst_per_launch": inst,
-        "how": f"ncu smsp__inst_executed.sum of one launch x launches / timed region; peak = "
+        "how": f"ncu smsp__inst_executed.sum of one launch / the launch's duration; peak = "
                f"{n_sm} SMs x 4 schedulers x the median SM clock under load"}
+    plan_desc = sampler.describe_batched(ba)
 
+    sum_c = int(ba.total_out)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "p50_ms": p50, "p99_ms": p99,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "clouds_per_gpu": B_CLOUDS, "N": N_POINTS,
-                   "C": C_SAMPLES, "M": M_SECTORS, "k": K_WINDOW,
-                   "l2": f"inputs larger than L2: the {rot['slots']} resident copies of the batch "
-                         f"({rot['mb']:.0f} MB with their outputs) are visited in turn, so each "
+        "config": {"workload": WORKLOAD, "clouds_per_gpu": n_clouds,
+                   "points": int(off[-1]), "samples": sum_c, "sectors": int(sum(Ms)),
+                   "l2": f"inputs larger than L2: the {slots} resident copies of the batch "
+                         f"({rot_mb:.0f} MB with their outputs) are visited in turn, so each "
                          "timed step reads points untouched for more than 2 x L2 of traffic; "
                          "p50/p99 are isolated steps, each after a 256 MB L2 flush",
-                   "streams": args.streams,
-                   "timing": f"value and ms_per_step: K steps, step i on stream i mod "
-                             f"{args.streams} (each stream's steps back to back, the streams "
-                             "side by side), between two CUDA events on the launching stream "
-                             "that every stream waits for / joins, enqueued while a sleep kernel "
-                             "(before the first event) holds the streams; ms_per_step = timed "
+                   "timing": "value and ms_per_step: K steps back to back on one stream between "
+                             "two CUDA events on that stream, enqueued while a sleep kernel "
+                             "(before the first event) holds the stream; ms_per_step = timed "
                              "region / K; p50/p99: per-step events of isolated steps",
                    "parallelism": f"replicas x{world}",
-                   "launch": "throughput: one direct kernel launch per step; latency: CUDA graph "
-                             "replay; kernel variant chosen by the autotuner (untimed)"},
-        "kernel_variants": plans,
-        "sampled_points_per_s": value * C_SAMPLES,
-        "fps_baseline": {"value": fps_value, "unit": UNIT, "ms_per_step": ms_fps,
-                         "speedup_npdu_afps": value / fps_value, "streams": args.streams},
-        "one_stream": {"value": B_CLOUDS * world / (ms_one / 1e3), "ms_per_step": ms_one,
-                       "fps_value": B_CLOUDS * world / (ms_fps_one / 1e3),
-                       "fps_ms_per_step": ms_fps_one, "speedup_npdu_afps": ms_fps_one / ms_one},
-        "sweep_clouds_per_s": sweep,
+                   "launch": "one afps_sample_batched call per step: a CUDA graph replay (one "
+                             "graph per resident copy); kernel variants chosen by the "
+                             "autotuner (untimed)"},
+        "kernel_launches": plan_desc,
+        "launches_per_step": launches_per_step,
+        "sampled_points_per_s": sum_c * world / (ms_step / 1e3),
+        "fps_baseline": {"value": n_clouds * world / (ms_fps / 1e3), "unit": UNIT,
+                         "ms_per_step": ms_fps, "speedup_npdu_afps": ms_fps / ms_step,
+                         "steps": fps_steps, "what": "plain FPS (M = 1, k = 0) on the same "
+                                                     "batch, same C, same protocol"},
+        "afps_no_npdu": {"value": n_clouds * world / (ms_full / 1e3), "unit": UNIT,
+                         "ms_per_step": ms_full, "speedup_npdu_afps": ms_full / ms_step,
+                         "what": "AFPS with the same M and no NPDU window"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "algorithmic_bytes_per_launch": hbm_bytes,
-                     "how": f"algorithmic bytes per launch x launches / timed region "
-                            f"({args.streams} streams of back-to-back launches side by side; "
-                            f"each launch lasts about {args.streams} x ms_per_step on its stream)",
-                     "kernel": plans.get(f"M{M_SECTORS}_npdu")},
+                     "launch_ms": kernel_s * 1e3,
+                     "how": "algorithmic bytes of one step (12 bytes a point read, 4 bytes a "
+                            "sample written) / the step's duration (timed region / K on the "
+                            "launching stream; one kernel launch per step)"},
         "roofline_issue": issue,
         "roofline_alu": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
-                         "fp32_ops_per_launch": 9 * evals + compares},
-        "e2e": {"value": B_CLOUDS * world / (e2e_ms / 1e3), "unit": UNIT,
+                         "fp32_ops_per_launch": 9 * evals + compares,
+                         "peak_how": f"{n_sm} SMs x 128 FP32 lanes x the median SM clock"},
+        "e2e": {"value": n_clouds * world / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes),
                 "ms_per_step": e2e_ms, "matches_device_path": True,
-                "how": f"K calls of afps_sample_batched_host_async on page-locked buffers "
-                       f"(inputs rotating over copies larger than L2, one output per step), "
-                       f"call i on stream i mod {args.streams}, one synchronisation, host "
-                       f"clock; every output checked",
+                "how": "K calls of afps_sample_batched_host_async on page-locked buffers "
+                       "(graph context; the kernels read the points and write the indices in "
+                       "host memory over the C2C link; inputs rotating over copies larger "
+                       "than L2, one output per step), one stream, one synchronisation, host "
+                       "clock; every output checked",
                 "sync_call_ms": e2e_call_ms, "sync_call_matches_device_path": e2e_ok},
+        "object_batch": obj,
         "serving": serving_stats,
         "large_clouds": large,
         "table_iv": tab4,
-        "ragged_batch": ragged,
         "sort_by_key": sorting,
         "ball_query": grouping,
         "gpu_launches": launches,
         "isolated_step_ms": iso_ms,
-        "enqueue": head_enqueue,
+        "enqueue": enqueue,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                    "reasons": clk["reasons"], "samples": clk["samples"]},
     }
 
     if rank == 0 and world == 1:
         threads = cpu_threads()
-        rate, reps, ref = time_oracle(clouds, C_SAMPLES, M_SECTORS, K_WINDOW,
-                                      args.cpu_seconds, threads)
-        rate1, reps1, _ = time_oracle(clouds, C_SAMPLES, M_SECTORS, K_WINDOW,
-                                      args.cpu_seconds / 4, 1)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": f"{reps} whole batches of {B_CLOUDS} clouds "
+        rate, reps, ref, procs = time_oracle(clouds, Cs, Ms, ks, args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
+                                "sample": f"{reps} whole ragged batch(es) of {n_clouds} clouds "
                                           f"(about {args.cpu_seconds:.0f} s), one process per "
-                                          f"core, each a contiguous chunk of the clouds",
-                                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
-                                                  "sample": f"{reps1} whole batches of "
-                                                            f"{B_CLOUDS} clouds on one thread"}}
+                                          f"core, each a contiguous chunk of the clouds"}
         same = sum(int(np.array_equal(head_out[ba.out_off[b]:ba.out_off[b + 1]], ref[b]))
-                   for b in range(B_CLOUDS))
-        line["parity"] = f"{same}/{B_CLOUDS} clouds bit-exact vs the FP32 oracle"
+                   for b in range(n_clouds))
+        line["parity"] = f"{same}/{n_clouds} clouds bit-exact vs the FP32 oracle"
         import oracle
         agree, drel = [], []
-        for b, P in enumerate(clouds):
-            r64 = oracle.afps(P, C_SAMPLES, M_SECTORS, K_WINDOW, 0, precision="f64")
+        for b in range(0, n_clouds, 16):  # every 16th cloud in FP64
+            P = clouds[b]
+            r64 = oracle.afps(P, Cs[b], Ms[b], ks[b], 0, precision="f64")
             agree.append(float(np.mean(r64 == ref[b])))
             R32, R64 = oracle.coverage_radius(P, ref[b]), oracle.coverage_radius(P, r64)
             drel.append(abs(R32 - R64) / R64)
         line["fp64_oracle"] = {"index_agreement": float(np.mean(agree)),
-                               "coverage_radius_rel_diff_max": float(max(drel))}
+                               "coverage_radius_rel_diff_max": float(max(drel)),
+                               "clouds": len(agree)}
     else:
         line["cpu_baseline"] = None
     sampler.close()
@@ -945,19 +905,71 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     return 0
 
 
+def object_batch_section(args, sampler, dev, world, barrier):
+    """The object batch (32 x 2048 points, C = 512), the paper's part-
+    segmentation shape (Sec. IV-B): one call per step on one stream, the
+    rotation over resident copies as for the headline, on a context without
+    graphs (direct launches chain through programmatic dependent launch);
+    NPDU-AFPS M = 32, k = 16, plain FPS and the sweep M in {1, 4, 16, 32}
+    with NPDU off and on."""
+    import torch
+    from paper_2208_08795_gb300 import afps as A
+    clouds, xyz, off = make_batch(1)
+    x = torch.from_numpy(xyz).to(dev)
+    res = {"workload": f"object batch {B_CLOUDS} x {N_POINTS} pts, C={C_SAMPLES}"}
+    steps = max(3, min(args.steps * 10, 200))
+
+    def run(M, k):
+        ba = A.BatchArgs(off, C_SAMPLES, M, k, 0)
+        out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
+        sampler.autotune_batched(x, ba, out)
+        sampler.sync()
+        tune = os.path.join(tempfile.gettempdir(), f"afps_bench_tune_{os.getpid()}.txt")
+        A.afps_save_tuning(sampler.ctx, tune)
+        direct = A.Sampler(sampler.device, tune_cache=tune)
+        xr, outr = rotation(x, ba.total_out, dev)
+        try:
+            barrier()
+            ms, _, last, _ = time_steps(direct, xr, outr, ba, steps, 5)
+            barrier()
+        finally:
+            direct.close()
+            os.unlink(tune)
+        if not torch.equal(outr[last], out):
+            raise RuntimeError(f"object batch M={M} k={k}: a step differs from the single call")
+        return max_over_ranks(ms, world, dev), sampler.describe_plan(
+            -(-N_POINTS // M), -(-C_SAMPLES // M), k, B_CLOUDS * M)
+
+    sweep = {}
+    for M in (1, 4, 16, 32):
+        for npdu in (False, True):
+            k = k_rule(M) if npdu else 0
+            ms, plan = run(M, k)
+            sweep[f"M{M}_{'npdu' if npdu else 'full'}"] = {
+                "clouds_per_s": round(B_CLOUDS * world / (ms / 1e3), 1),
+                "ms_per_step": round(ms, 5), "variant": plan}
+    head = sweep[f"M{M_SECTORS}_npdu"]
+    res.update({"npdu_afps_m32_k16": head, "fps": sweep["M1_full"],
+                "speedup_npdu_afps_vs_fps": round(sweep["M1_full"]["ms_per_step"]
+                                                  / head["ms_per_step"], 2),
+                "sweep": sweep, "steps": steps,
+                "timing": "one call per step, steps back to back on one stream between two "
+                          "CUDA events, each on the next resident copy (copies span 2 x L2)"})
+    return res
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-seconds", type=float, default=5.0)
-    ap.add_argument("--streams", type=int, default=8,
-                    help="streams the throughput steps are spread over (1: one stream)")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the serving sweep")
     ap.add_argument("--no-configs", dest="configs", action="store_false",
-                    help="skip the large-cloud and ragged-batch sections")
+                    help="skip the object-batch, large-cloud, Table IV, sort and grouping "
+                         "sections")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -73,10 +73,22 @@ extern "C" {
  * then samples as usual. */
 #define AFPS_FLAG_AUTOTUNE 2u
 /* Fault injection for tests of failure detection: the stage-in arms its
- * shared-memory barrier but never issues the bulk copy, so every bounded
- * wait runs out (after timeout_ns) and afps_sync returns AFPS_ERR_TIMEOUT.
- * Outputs of such calls are meaningless; the context stays usable. */
+ * shared-memory barrier but never issues the bulk copy, so the bounded wait
+ * runs out (after timeout_ns) and afps_sync returns AFPS_ERR_TIMEOUT.
+ * Outputs of such calls are meaningless; the context stays usable.
+ * After any timeout every kernel leaves its remaining work items undone
+ * (nothing is computed on shared memory a copy may not have filled), and so
+ * do later launches on the context until afps_sync has reported and
+ * cleared the timeout: a stalled call costs a few timeouts, not one per
+ * item or iteration. */
 #define AFPS_FLAG_TEST_STALL_COPY 0x100u
+/* Fault injection for tests of failure detection: in thread-block-cluster
+ * kernels (plain FPS on large clouds) the last CTA of each cluster never
+ * sends its records of the per-iteration argmax exchange, so the exchange's
+ * bounded waits run out (after timeout_ns) and afps_sync returns
+ * AFPS_ERR_TIMEOUT.  Outputs of such calls are meaningless; the context
+ * stays usable. */
+#define AFPS_FLAG_TEST_STALL_EXCHANGE 0x400u
 /* Fault injection for tests of failure detection: every growth of the
  * context's device workspace (item tables, work-queue counters, staging and
  * scratch buffers) fails as it would on an exhausted device, so a call that
@@ -145,16 +157,21 @@ int afps_sample_ex(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int3
                    void* stream);
 
 /*
- * A ragged batch of B clouds in one call: cloud b is points
- * [h_pt_off[b], h_pt_off[b+1]) of d_xyz and writes h_C[b] indices at
- * d_out[h_out_off[b]], relative to its own first point.  Each cloud has its
- * own C, M, k and start (h_* arrays of B entries; h_pt_off and h_out_off of
- * B+1 nondecreasing entries with h_out_off[b+1] - h_out_off[b] >= h_C[b]).
- * All (cloud, sector) work items run in one launch per kernel shape class;
- * with AFPS_FLAG_GRAPH the launches are captured once per distinct argument
- * set (pointers included) and replayed; a context keeps up to 512 such
- * graphs, evicting the least recently used.  Host arrays are read before
- * return.
+ * A ragged batch of B clouds in one call, each cloud sampled exactly as
+ * afps_sample would (Algorithm 1 in every sector, Sec. III-B; the NPDU
+ * window of Sec. III-C).  The sectors of every cloud are independent (Sec.
+ * III-B: each runs its own FPS loop), so all (cloud, sector) pairs of the
+ * batch become work items of one kernel launch per kernel shape class
+ * (sectors of similar size; NPDU classes that the window kernel serves share
+ * one launch), distributed over the GPU by a work queue when there are more
+ * items than resident warps.  Cloud b is points [h_pt_off[b], h_pt_off[b+1])
+ * of d_xyz and writes h_C[b] indices at d_out[h_out_off[b]], relative to its
+ * own first point.  Each cloud has its own C, M, k and start (h_* arrays of
+ * B entries; h_pt_off and h_out_off of B+1 nondecreasing entries with
+ * h_out_off[b+1] - h_out_off[b] >= h_C[b]).  With AFPS_FLAG_GRAPH the
+ * launches are captured once per distinct argument set (pointers included)
+ * and replayed; a context keeps up to 512 such graphs, evicting the least
+ * recently used.  Host arrays are read before return.
  */
 int afps_sample_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt_off,
                         int32_t B, const int32_t* h_C, const int32_t* h_M,
@@ -322,6 +339,19 @@ int afps_save_tuning(afps_ctx* ctx, const char* path);
 int afps_describe_plan(afps_ctx* ctx, int64_t n_sector, int32_t c_sector,
                        int32_t npdu_window, int32_t n_items, char* buf, int32_t buf_len);
 
+/*
+ * Describe how afps_sample_batched would run an argument set (the same host
+ * arrays) on this context: one entry per kernel launch, "<variant>
+ * items=<n>", entries separated by "; " (e.g. "win P=9 W=8 items=17576").
+ * Validates like afps_sample_batched; no device work.  Writes a
+ * NUL-terminated text of at most buf_len bytes into buf and returns the
+ * full text length, or a negative AFPS_ERR_* code.
+ */
+int afps_describe_batched(afps_ctx* ctx, const int64_t* h_pt_off, int32_t B,
+                          const int32_t* h_C, const int32_t* h_M, const int32_t* h_win,
+                          const int64_t* h_start, const int64_t* h_out_off, char* buf,
+                          int32_t buf_len);
+
 /* Number of kernel launches issued by this context since creation. */
 int64_t afps_launch_count(const afps_ctx* ctx);
 
@@ -333,23 +363,33 @@ int64_t afps_launch_count(const afps_ctx* ctx);
  * framework that owns all device memory, a process under a fixed memory
  * budget or pool, a real-time loop that must not take allocator locks or
  * cause the implicit synchronisation an allocation can bring).  It takes no
- * context and allocates nothing, on the device or on the host heap.
+ * context and allocates no device memory.  On the host heap it allocates
+ * only on the first launch of each kernel variant on a device, where the
+ * library records the kernel attributes it has set; a warm-up call with the
+ * same shapes covers that.
  *
  * Arguments, layouts and results are those of afps_sample_batched; the
  * caller passes the input points and the output buffer.  The work-item table
- * (40 bytes per sector) lives in a static device array of
- * AFPS_NOALLOC_MAX_ITEMS items (about 320 KB) that every GPU loading the
- * library holds until the process exits.  A batch with more sectors than
- * that returns AFPS_ERR_SCRATCH_TOO_SMALL and launches nothing.
+ * (48 bytes per sector) lives in a static device array of
+ * AFPS_NOALLOC_MAX_ITEMS items plus a 256-byte header (393,472 bytes, about
+ * 384 KB) that every GPU loading the library holds until the process exits.
+ * A batch with more sectors than that returns AFPS_ERR_SCRATCH_TOO_SMALL and
+ * launches nothing.
  *
  * It runs on the current device.  The first call on a device looks up the
- * array's device address there (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * last call's table: calls whose work overlaps on the GPU (different streams
- * without ordering, or several host threads) race on it.  Calls on one
- * stream are ordered and safe.  Device-side wait timeouts are recorded in the
- * array's status word, which nothing reads back; use afps_sample_batched
- * with afps_sync where such reports matter.
+ * array's device address there (cudaGetSymbolAddress).  The table goes up
+ * by cudaMemcpyAsync from the library's static host copy, which is pageable
+ * memory, so a call may wait until the stream has reached it: it suits a
+ * loop that must not allocate, not one that must never wait.  It must not
+ * be captured into a CUDA graph (the copy would be recorded reading the host
+ * copy at every replay, after later calls have overwritten it): on a stream
+ * that is capturing it returns AFPS_ERR_INVALID_ARG and does nothing.  All
+ * calls share the one array and it keeps the last call's table: calls whose
+ * work overlaps on the GPU (different streams without ordering, or several
+ * host threads) race on it.  Calls on one stream are ordered and safe.
+ * Device-side wait timeouts are recorded in the array's status word, which
+ * nothing reads back; use afps_sample_batched with afps_sync where such
+ * reports matter.
  */
 #define AFPS_NOALLOC_MAX_ITEMS 8192
 #define AFPS_ERR_SCRATCH_TOO_SMALL (-7) /* batch exceeds AFPS_NOALLOC_MAX_ITEMS sectors */

@@ -31,13 +31,15 @@ AFPS_MAX_SECTOR_POINTS = 131072
 AFPS_FLAG_GRAPH = 1
 AFPS_FLAG_AUTOTUNE = 2
 AFPS_FLAG_TEST_STALL_COPY = 0x100
+AFPS_FLAG_TEST_STALL_EXCHANGE = 0x400
 AFPS_FLAG_TEST_FAIL_ALLOC = 0x200
 
 # every symbol include/afps.h declares
 EXPORTS = ("afps_create", "afps_destroy", "afps_sample", "afps_sample_batched",
            "afps_sample_batched_host", "afps_gather_levels", "afps_sync",
            "afps_last_error", "afps_autotune_batched", "afps_save_tuning",
-           "afps_describe_plan", "afps_launch_count", "afps_sample_batched_noalloc",
+           "afps_describe_plan", "afps_describe_batched", "afps_launch_count",
+           "afps_sample_batched_noalloc",
            "afps_server_create", "afps_server_submit", "afps_server_step", "afps_server_poll",
            "afps_server_stats", "afps_server_clock_ms", "afps_server_destroy",
            "afps_sort_by_key", "afps_sample_ex", "afps_sample_batched_ex",
@@ -112,6 +114,8 @@ def _declare(L: ctypes.CDLL) -> ctypes.CDLL:
     L.afps_save_tuning.restype = ctypes.c_int
     L.afps_describe_plan.argtypes = [vp, i64, i32, i32, i32, ctypes.c_char_p, i32]
     L.afps_describe_plan.restype = ctypes.c_int
+    L.afps_describe_batched.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, ctypes.c_char_p, i32]
+    L.afps_describe_batched.restype = ctypes.c_int
     L.afps_launch_count.argtypes = [vp]
     L.afps_launch_count.restype = ctypes.c_int64
     L.afps_sample_batched_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
@@ -245,6 +249,15 @@ def afps_describe_plan(ctx, n_sector: int, c_sector: int, npdu_window: int,
     rc = load().afps_describe_plan(ctx, n_sector, c_sector, npdu_window, n_items, buf, 128)
     if rc < 0:
         raise AfpsError(rc, "afps_describe_plan failed")
+    return buf.value.decode()
+
+
+def afps_describe_batched(ctx, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    rc = load().afps_describe_batched(ctx, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off,
+                                      buf, 1024)
+    if rc < 0:
+        raise AfpsError(rc, afps_last_error(ctx))
     return buf.value.decode()
 
 
@@ -491,6 +504,10 @@ class Sampler:
 
     def describe_plan(self, n_sector: int, c_sector: int, k: int, n_items: int = 1) -> str:
         return afps_describe_plan(self.ctx, n_sector, c_sector, k, n_items)
+
+    def describe_batched(self, ba: "BatchArgs") -> str:
+        """The kernel launches of a batched call: "<variant> items=<n>; ..."."""
+        return afps_describe_batched(self.ctx, *ba.args())
 
     @property
     def launch_count(self) -> int:

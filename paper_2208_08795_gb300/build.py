@@ -17,7 +17,7 @@ LIBRARY = os.path.join(PKG, "libafps.so")
 BUILD_DIR_DEBUG = os.path.join(PKG, "_build_debug")
 LIBRARY_DEBUG = os.path.join(PKG, "libafps_debug.so")
 HEADER = os.path.join(ROOT, "include", "afps.h")
-SOURCES = ["afps_warp.cu", "afps_cta.cu", "afps_gather.cu", "afps_api.cu", "afps_noalloc.cu",
+SOURCES = ["afps_warp.cu", "afps_win.cu", "afps_cta.cu", "afps_gather.cu", "afps_api.cu", "afps_noalloc.cu",
            "afps_server.cu", "afps_sort.cu", "afps_coverage.cu", "afps_group.cu",
            "afps_knn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

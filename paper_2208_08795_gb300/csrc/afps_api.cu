@@ -86,6 +86,7 @@ struct ClassPlan {
     // every cloud of the class has the same N, C, M, window and start, and
     // they are stored back to back: the kernel computes its items
     bool uniform = false;
+    bool merged = false;  // several shape classes in one launch (window kernels)
     afps::SingleCloud single{};
     const afps::SingleCloud* run() const { return uniform ? &single : nullptr; }
 };
@@ -245,8 +246,32 @@ CloudCheck check_cloud(int64_t N, int32_t C, int32_t M, int32_t k, int64_t start
 const int kWarpP[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
 const int kCtaP[] = {2, 4, 8, 16};
 
+// Window-kernel variant for NPDU sectors of up to n_max points: a buffer of
+// exactly the rows needed, and the most warps per CTA (a power of two, at
+// most 8) whose buffers fit in 64 KB, so that several CTAs share an SM.
+Variant win_variant(int64_t n_max, int W = 0) {
+    Variant v{};
+    v.kind = afps::KIND_WIN;
+    v.P = (int)((n_max + 31) / 32);
+    v.CS = 1;
+    if (W > 0) {
+        v.W = W;
+        return v;
+    }
+    const int64_t per_warp = 16 * 32 * (int64_t)v.P + 16;
+    v.W = 8;
+    while (v.W > 1 && v.W * per_warp > 64 * 1024) v.W /= 2;
+    return v;
+}
+
+// Whether NPDU sectors of up to n_max points go to the window kernel by
+// default: above 64 points (two rows per lane in the register kernel, where
+// its full rescan is as cheap as the row cache) and up to its capacity.
+bool win_default(int64_t n_max) { return n_max > 64 && n_max <= 32LL * afps::kWinMaxRows; }
+
 // Default variant for sectors of up to n_max points.
-Variant default_variant(int64_t n_max) {
+Variant default_variant(int64_t n_max, bool npdu) {
+    if (npdu && win_default(n_max)) return win_variant(n_max);
     Variant v{};
     v.CS = 1;
     v.occ = 0;
@@ -315,6 +340,11 @@ std::vector<Variant> candidate_variants(int64_t n_max, bool npdu) {
             ok.push_back(s);
         }
     }
+    if (npdu && n_max <= 32LL * afps::kWinMaxRows)
+        for (int W : {1, 2, 4, 8}) {
+            const Variant v = win_variant(n_max, W);
+            if (afps::variant_supported(v)) ok.push_back(v);
+        }
     return ok;
 }
 
@@ -330,15 +360,17 @@ Variant choose_variant(const afps_ctx* ctx, bool npdu, int64_t n_max, int32_t c_
                        size_t items) {
     auto it = ctx->tuned.find(class_key(npdu, n_max, c_max, items));
     if (it != ctx->tuned.end() && afps::variant_capacity(it->second) >= n_max &&
-        afps::variant_supported(it->second))
+        afps::variant_supported(it->second) && (npdu || it->second.kind != afps::KIND_WIN))
         return it->second;
-    return default_variant(n_max);
+    return default_variant(n_max, npdu);
 }
 
 std::string describe(const Variant& v) {
     std::ostringstream os;
     if (v.kind == afps::KIND_WARP)
         os << "warp P=" << v.P << " W=" << v.W;
+    else if (v.kind == afps::KIND_WIN)
+        os << "win P=" << v.P << " W=" << v.W;
     else if (v.CS > 1)
         os << "cluster P=" << v.P << " W=" << v.W << " CS=" << v.CS;
     else
@@ -366,9 +398,33 @@ int grid_for(const Variant& v, size_t count) {
     } else {
         cap = it->second;
     }
-    size_t want = v.kind == afps::KIND_WARP ? (count + v.W - 1) / v.W : count;
+    size_t want = v.kind != afps::KIND_CTA ? (count + v.W - 1) / v.W : count;
     if (cap > 0 && want > (size_t)cap) want = (size_t)cap;
     return (int)std::max<size_t>(want, 1);
+}
+
+// Fault-injection bits of the sector kernels for the context's flags.
+uint32_t stall_bits(uint32_t flags) {
+    return ((flags & AFPS_FLAG_TEST_STALL_COPY) ? afps::STALL_COPY : 0u) |
+           ((flags & AFPS_FLAG_TEST_STALL_EXCHANGE) ? afps::STALL_EXCHANGE : 0u);
+}
+
+// Whether a launch of `count` items of variant v takes its items from a
+// dynamic work queue: warp-per-item kernels whose grid is capped below one
+// warp per item (persistent launch); otherwise items map to warps 1:1.
+bool uses_queue(const Variant& v, size_t count) {
+    return v.kind != afps::KIND_CTA && (size_t)grid_for(v, count) * (size_t)v.W < count;
+}
+
+// Work-queue counters start at zero and every launch leaves its counter at
+// zero (the warp that draws the last ticket resets it), so a counter buffer
+// is cleared only when it is allocated.
+int grow_counters(afps_ctx* ctx, DevBuf& b, size_t n, cudaStream_t stream) {
+    const size_t want = n * sizeof(unsigned int);
+    if (want <= b.bytes) return AFPS_OK;
+    AFPS_CUDA(ctx, grow(ctx, b, want));
+    AFPS_CUDA(ctx, cudaMemsetAsync(b.p, 0, b.bytes, stream));
+    return AFPS_OK;
 }
 
 int launch_class(afps_ctx* ctx, const Variant& v, bool npdu, const ItemDesc* d_items,
@@ -381,18 +437,13 @@ int launch_class(afps_ctx* ctx, const Variant& v, bool npdu, const ItemDesc* d_i
     if (run) a.single = *run;
     a.n_items = (int32_t)count;
     a.out = out;
-    // The dynamic queue is needed only when the grid is capped below one
-    // warp per item (persistent launch); otherwise items map to warps 1:1.
     const int grid = grid_for(v, count);
-    const bool persistent =
-        v.kind == afps::KIND_WARP && (size_t)grid * (size_t)v.W < count && d_counter;
-    a.counter = persistent ? d_counter : nullptr;
+    a.counter = uses_queue(v, count) ? d_counter : nullptr;  // left at zero by the kernel
     a.status = ctx->d_status;
     a.timeout_ns = ctx->timeout_ns;
-    a.stall_copy = (ctx->flags & AFPS_FLAG_TEST_STALL_COPY) ? 1u : 0u;
+    a.stall = stall_bits(ctx->flags);
     a.npdu_skip = v.skip ? 1u : 0u;
     a.host_resident = host_resident ? 1u : 0u;
-    if (a.counter) AFPS_CUDA(ctx, cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), stream));
     cudaError_t e = afps::launch_sector(v, npdu, a, grid, stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sector kernel launch");
     ctx->launches += 1;
@@ -413,10 +464,55 @@ int64_t size_bucket(int64_t n_max) {
 
 // Cloud b: n_pts[b] points from point pt_begin[b] of the xyz base, C[b]
 // indices written from out_begin[b] of the output base (out_cap[b] slots).
+// Rows-per-lane template of a window-kernel variant (afps_win.cu).
+int win_slots(const Variant& v) {
+    int r = 1;
+    while (32 * r < v.P) r <<= 1;
+    return r;
+}
+
+// Work of an item, for largest-first ordering of a class's queue.
+int64_t item_cost(const ItemDesc& d, bool npdu) {
+    return npdu ? (int64_t)d.c * (d.kl + d.kr + 1 + d.n / 32) : (int64_t)d.c * d.n;
+}
+
+// Consecutive table classes whose variants are window kernels of the same
+// template (slots per lane) run as one launch: the buffer for the larger
+// sectors holds the smaller ones, and one dynamic queue over all of them
+// (largest work first) leaves a shorter tail than launches one after the
+// other.  The items of consecutive classes are contiguous in the table.
+void merge_window_classes(BatchPlan& plan) {
+    std::vector<ClassPlan> out;
+    for (const ClassPlan& cp : plan.classes) {
+        if (!out.empty()) {
+            ClassPlan& last = out.back();
+            if (!last.uniform && !cp.uniform && last.npdu && cp.npdu &&
+                last.v.kind == afps::KIND_WIN && cp.v.kind == afps::KIND_WIN &&
+                win_slots(last.v) == win_slots(cp.v) && last.first + last.count == cp.first) {
+                if (cp.v.P > last.v.P) last.v = cp.v;
+                last.count += cp.count;
+                last.n_max = std::max(last.n_max, cp.n_max);
+                last.c_max = std::max(last.c_max, cp.c_max);
+                last.merged = true;  // re-sorted below
+                continue;
+            }
+        }
+        out.push_back(cp);
+    }
+    for (const ClassPlan& cp : out)
+        if (cp.merged)
+            std::stable_sort(plan.items.begin() + cp.first,
+                             plan.items.begin() + cp.first + cp.count,
+                             [](const ItemDesc& x, const ItemDesc& y) {
+                                 return item_cost(x, true) > item_cost(y, true);
+                             });
+    plan.classes.swap(out);
+}
+
 int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t* n_pts,
                const int64_t* out_begin, const int64_t* out_cap, const int32_t* C,
                const int32_t* M, const int32_t* K, const int64_t* start, BatchPlan& plan,
-               const uint32_t* method = nullptr) {
+               const uint32_t* method = nullptr, bool merge = true) {
     if (B < 1 || !pt_begin || !n_pts || !out_begin || !out_cap || !C || !M || !K || !start)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
     struct Member {
@@ -514,14 +610,15 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
         }
         cp.count = plan.items.size() - cp.first;
         // largest work first (longest-processing-time order for the queue)
-        auto cost = [&](const ItemDesc& d) {
-            return cp.npdu ? (int64_t)d.c * (d.kl + d.kr + 1 + d.n / 32) : (int64_t)d.c * d.n;
-        };
+        const bool npdu = cp.npdu;
         std::stable_sort(plan.items.begin() + cp.first, plan.items.end(),
-                         [&](const ItemDesc& x, const ItemDesc& y) { return cost(x) > cost(y); });
+                         [npdu](const ItemDesc& x, const ItemDesc& y) {
+                             return item_cost(x, npdu) > item_cost(y, npdu);
+                         });
         cp.v = choose_variant(ctx, cp.npdu, cp.n_max, cp.c_max, cp.count);
         plan.classes.push_back(cp);
     }
+    if (merge) merge_window_classes(plan);
     return AFPS_OK;
 }
 
@@ -547,7 +644,7 @@ int upload(afps_ctx* ctx, DevBuf& dst, const void* src, size_t bytes, cudaStream
 int build_plan_consecutive(afps_ctx* ctx, const int64_t* pt_off, int32_t B, const int32_t* C,
                            const int32_t* M, const int32_t* K, const int64_t* start,
                            const int64_t* out_off, BatchPlan& plan,
-                           const uint32_t* method = nullptr) {
+                           const uint32_t* method = nullptr, bool merge = true) {
     if (B < 1 || !pt_off || !out_off)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
     std::vector<int64_t> pb((size_t)B), np((size_t)B), ob((size_t)B), oc((size_t)B);
@@ -558,26 +655,27 @@ int build_plan_consecutive(afps_ctx* ctx, const int64_t* pt_off, int32_t B, cons
         oc[b] = out_off[b + 1] - out_off[b];
     }
     return build_plan(ctx, B, pb.data(), np.data(), ob.data(), oc.data(), C, M, K, start, plan,
-                      method);
+                      method, merge);
 }
 
 // Run a plan out of the context's shared workspace (no graph).
 int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* d_out,
              cudaStream_t stream, bool host_resident = false) {
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);
-    AFPS_CUDA(ctx, grow(ctx, ctx->counters, plan.classes.size() * sizeof(unsigned int)));
     bool table = false;  // some class reads the item table
     bool queue = false;  // some class uses a work-queue counter
     for (const ClassPlan& cp : plan.classes) {
         table = table || !cp.uniform;
-        queue = queue || (cp.v.kind == afps::KIND_WARP &&
-                          (size_t)grid_for(cp.v, cp.count) * (size_t)cp.v.W < cp.count);
+        queue = queue || uses_queue(cp.v, cp.count);
+    }
+    if (queue) {  // a new counter buffer is cleared after the workspace's last use
+        AFPS_CUDA(ctx, cudaStreamWaitEvent(stream, ctx->ev_done, 0));
+        int grc = grow_counters(ctx, ctx->counters, plan.classes.size(), stream);
+        if (grc != AFPS_OK) return grc;
     }
     if (table) {  // the upload waits for the workspace's last use
         int urc = upload(ctx, ctx->items, plan.items.data(), bytes, stream);
         if (urc != AFPS_OK) return urc;
-    } else if (queue) {  // the counters are reset on this stream: same wait
-        AFPS_CUDA(ctx, cudaStreamWaitEvent(stream, ctx->ev_done, 0));
     }
     const ItemDesc* d_items = static_cast<const ItemDesc*>(ctx->items.p);
     unsigned int* counters = static_cast<unsigned int*>(ctx->counters.p);
@@ -637,6 +735,8 @@ int make_graph(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);
     AFPS_CUDA(ctx, grow(ctx, g.items, bytes));
     AFPS_CUDA(ctx, grow(ctx, g.counters, plan.classes.size() * sizeof(unsigned int)));
+    // the graph's own queue counters start at zero; each replay leaves them so
+    AFPS_CUDA(ctx, cudaMemset(g.counters.p, 0, g.counters.bytes));
     if (bytes)  // classes of equal-cloud runs need no table
         AFPS_CUDA(ctx, cudaMemcpy(g.items.p, plan.items.data(), bytes, cudaMemcpyHostToDevice));
     const ItemDesc* d_items = static_cast<const ItemDesc*>(g.items.p);
@@ -680,8 +780,8 @@ int tune_if_new(afps_ctx* ctx, const float* d_xyz, const int64_t* pt_off, int32_
                 const uint32_t* method) {
     const std::string key = graph_key(nullptr, nullptr, pt_off, B, C, M, K, start, out_off, method);
     if (ctx->checked.count(key)) return AFPS_OK;
-    BatchPlan plan;
-    int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan, method);
+    BatchPlan plan;  // the classes the tuner times (unmerged)
+    int rc = build_plan_consecutive(ctx, pt_off, B, C, M, K, start, out_off, plan, method, false);
     if (rc != AFPS_OK) return rc;
     bool tuned = true;
     for (const ClassPlan& cp : plan.classes)
@@ -1036,7 +1136,7 @@ int afps_sample_ex(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int3
     a.counter = nullptr;
     a.status = ctx->d_status;
     a.timeout_ns = ctx->timeout_ns;
-    a.stall_copy = (ctx->flags & AFPS_FLAG_TEST_STALL_COPY) ? 1u : 0u;
+    a.stall = stall_bits(ctx->flags);
     a.npdu_skip = v.skip ? 1u : 0u;
     cudaError_t e = afps::launch_sector(v, npdu, a, grid_for(v, (size_t)M),
                                         static_cast<cudaStream_t>(stream));
@@ -1359,8 +1459,9 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
     if (!d_xyz || !d_out) return fail(ctx, AFPS_ERR_INVALID_ARG, "autotune: NULL device pointer");
     DeviceGuard guard(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    BatchPlan plan;
-    int rc = build_plan_consecutive(ctx, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, plan);
+    BatchPlan plan;  // unmerged: every shape class is tuned on its own
+    int rc = build_plan_consecutive(ctx, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, plan,
+                                    nullptr, false);
     if (rc != AFPS_OK) return rc;
     // upload the table once, then time each candidate class by class
     rc = run_plan(ctx, plan, d_xyz, d_out, st);
@@ -1368,6 +1469,9 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
     cudaEvent_t e0, e1;
     AFPS_CUDA(ctx, cudaEventCreate(&e0));
     AFPS_CUDA(ctx, cudaEventCreate(&e1));
+    // candidates may use a work queue where the plan's variants do not
+    rc = grow_counters(ctx, ctx->counters, plan.classes.size(), st);
+    if (rc != AFPS_OK) return rc;
     const ItemDesc* d_items = static_cast<const ItemDesc*>(ctx->items.p);
     unsigned int* counters = static_cast<unsigned int*>(ctx->counters.p);
     int tuned = 0;
@@ -1436,6 +1540,26 @@ int afps_describe_plan(afps_ctx* ctx, int64_t n_sector, int32_t c_sector, int32_
     const Variant v =
         choose_variant(ctx, npdu_window > 0, n_sector, c_sector, (size_t)n_items);
     const std::string s = describe(v);
+    snprintf(buf, (size_t)buf_len, "%s", s.c_str());
+    return (int)s.size();
+}
+
+int afps_describe_batched(afps_ctx* ctx, const int64_t* h_pt_off, int32_t B,
+                          const int32_t* h_C, const int32_t* h_M, const int32_t* h_win,
+                          const int64_t* h_start, const int64_t* h_out_off, char* buf,
+                          int32_t buf_len) {
+    if (!ctx) return AFPS_ERR_INVALID_ARG;
+    if (!buf || buf_len < 1 || B < 1 || !h_pt_off || !h_C || !h_M || !h_win || !h_start ||
+        !h_out_off)
+        return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_describe_batched: NULL argument or B < 1");
+    DeviceGuard guard(ctx->device);
+    BatchPlan plan;
+    int rc = build_plan_consecutive(ctx, h_pt_off, B, h_C, h_M, h_win, h_start, h_out_off, plan);
+    if (rc != AFPS_OK) return rc;
+    std::ostringstream os;
+    for (size_t i = 0; i < plan.classes.size(); ++i)
+        os << (i ? "; " : "") << describe(plan.classes[i].v) << " items=" << plan.classes[i].count;
+    const std::string s = os.str();
     snprintf(buf, (size_t)buf_len, "%s", s.c_str());
     return (int)s.size();
 }

@@ -106,6 +106,10 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
     // cluster stride phase: every CTA's 1e10-test verdict, two alternating buffers
     __shared__ __align__(16) uint32_t cl_ok[CLUSTER ? 2 : 1][CLUSTER ? 16 : 1][4];
     uint32_t npro = 0;  // stride phases run (buffer parity)
+    // cluster: every CTA's stop verdict of each item, two alternating buffers
+    __shared__ __align__(16) uint32_t cl_stop[CLUSTER ? 2 : 1][CLUSTER ? 16 : 1][4];
+    uint32_t nvote = 0;
+    bool halted = false;  // a timeout was seen: leave the remaining items undone
     const int group = CLUSTER ? (int)dev::cluster_id_x() : (int)blockIdx.x;
     const int ngroups = CLUSTER ? (int)dev::ncluster_x() : (int)gridDim.x;
 
@@ -120,19 +124,40 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
         dev::fence_proxy_async_smem();
         __syncthreads();
         bool bulk = false;
+        bool late = false;
+        int seen = 0;
         const float* pts = reinterpret_cast<const float*>(buf);
-        if (cn > 0)
+        if (cn > 0 && !halted)
             pts = dev::stage_points(a.xyz + 3 * (d.src + c0), cn, buf, bar, tid == 0, tid, T,
-                                    &bulk, a.stall_copy != 0, a.host_resident != 0);
+                                    &bulk, (a.stall & STALL_COPY) != 0, a.host_resident != 0);
+        // a timeout recorded by any CTA so far (the load overlaps the copy)
+        if (!halted) seen = dev::load_status(a.status);
         if (bulk) {
-            if (!dev::mbar_wait_bounded(bar, phase, a.timeout_ns)) {
+            late = !dev::mbar_wait_bounded(bar, phase, a.timeout_ns);
+            if (late) {
                 dev::record_status(a.status, DEV_TIMEOUT_STAGE);
                 if (!dev::mbar_wait_bounded(bar, phase, a.timeout_ns))
                     dev::record_status(a.status, DEV_TIMEOUT_DRAIN);
             }
             phase ^= 1u;
         }
-        __syncthreads();
+        // After a timeout (here, in a peer or anywhere on the context) nothing
+        // is computed on shared memory a copy may not have filled.  The CTAs
+        // of a cluster agree on it item by item (each CTA's verdict to every
+        // peer, one cluster barrier), so they all skip the same items and
+        // pass the same sequence of cluster barriers.
+        bool stop = __syncthreads_or(halted || late || dev::is_timeout(seen)) != 0;
+        if (CLUSTER) {
+            const int par = nvote & 1;
+            if (tid < CS)
+                dev::st_cluster_v4(dev::mapa(dev::smem_u32(&cl_stop[par][rank][0]), (uint32_t)tid),
+                                   stop ? 1u : 0u, 0u, 0u, 0u);
+            dev::cluster_sync();
+            for (int r = 0; r < CS; ++r) stop = stop || cl_stop[par][r][0] != 0u;
+            ++nvote;
+        }
+        halted = stop;
+        if (halted) continue;
 
         // rows i = 2h, 2h+1 share packed registers (f32x2 arithmetic)
         constexpr int PP = (P + 1) / 2;
@@ -306,7 +331,9 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             const uint32_t xbar = xb ? xbar1 : xbar0;
             Rec* R = recs + xb * E;
             if (CLUSTER) {
-                if (lane < CS) {
+                // fault injection: the cluster's last CTA sends no records
+                const bool send = !((a.stall & STALL_EXCHANGE) && rank == CS - 1);
+                if (lane < CS && send) {
                     const float wx = pts[3 * jw], wy = pts[3 * jw + 1], wz = pts[3 * jw + 2];
                     const uint32_t slot = dev::smem_u32(&R[rank * W + w]);
                     const uint32_t remote = dev::mapa(slot, (uint32_t)lane);
@@ -319,9 +346,10 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             }
 
             // 3. wait for every record of this exchange
+            bool xlate = false;
             if (CLUSTER) {
-                if (!dev::mbar_wait_bounded(xbar, xb ? xphase1 : xphase0, a.timeout_ns))
-                    dev::record_status(a.status, DEV_TIMEOUT_EXCHANGE);
+                xlate = !dev::mbar_wait_bounded(xbar, xb ? xphase1 : xphase0, a.timeout_ns);
+                if (xlate) dev::record_status(a.status, DEV_TIMEOUT_EXCHANGE);
                 if (xb)
                     xphase1 ^= 1u;
                 else
@@ -341,7 +369,12 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             const unsigned hi = (unsigned)(bkey >> 32), lo = (unsigned)bkey;
             const unsigned mm = __reduce_max_sync(dev::kFull, hi);
             const unsigned lo2 = __reduce_max_sync(dev::kFull, hi == mm ? lo : 0u);
-            p = dev::checked((int)(0xffffffffu - lo2), 0, n, a.status);
+            p = (int)(0xffffffffu - lo2);
+            // After a timed-out exchange some records were never written and p
+            // may be anything: it is kept inside the sector, so the lookups
+            // below stay in bounds, until the CTA stops at its next barrier.
+            if (CLUSTER) p = min(max(p, 0), n - 1);
+            p = dev::checked(p, 0, n, a.status);
             if (CLUSTER) {
                 // the winner's record sits at (owner rank, owner warp)
                 const int r = (int)dev::SmallDiv((uint32_t)chunk)((uint32_t)p);
@@ -358,7 +391,10 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
                 qz = pts[3 * p + 2];
             }
             if (CLUSTER) {  // re-arm this buffer once every local reader is done
-                __syncthreads();
+                // a record that did not come: stop this item here (peers stop
+                // at their next exchange, which this CTA no longer feeds)
+                halted = __syncthreads_or(xlate) != 0;
+                if (halted) break;
                 if (tid == 0) dev::mbar_arrive_expect_tx(xbar, xbytes);
             }
             ++xchg;
@@ -367,13 +403,14 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
                 if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
             }
         }
-        if (emitter && lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
+        if (emitter && !halted && lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
     }
     if (CLUSTER) dev::cluster_sync();  // no CTA leaves while a peer may still store to it
 }
 
 using SectorKernel = void (*)(LaunchArgs);
 SectorKernel warp_kernel_for(int P, bool npdu, bool rows);
+SectorKernel win_kernel_for(int rows, bool host_rows);
 
 static SectorKernel cta_kernel_for(int P, bool npdu, bool cluster) {
 #define AFPS_CTA_CASE(PP)                                                             \
@@ -395,12 +432,17 @@ static SectorKernel cta_kernel_for(int P, bool npdu, bool cluster) {
 size_t variant_smem(const Variant& v) {
     if (v.kind == KIND_WARP)
         return 16 * ((8 * (size_t)v.W + 15) / 16) + (size_t)v.W * (12 * 32 * (size_t)v.P + 16);
+    if (v.kind == KIND_WIN)  // per warp: xyz (12 bytes a point + 16) and distances (4 bytes)
+        return 16 * ((8 * (size_t)v.W + 15) / 16) + (size_t)v.W * (16 * 32 * (size_t)v.P + 16);
     return 32 + 2 * (size_t)v.CS * v.W * sizeof(Rec) + 12 * 32 * (size_t)v.W * v.P + 16;
 }
 
 bool variant_supported(const Variant& v) {
     if (v.kind == KIND_WARP)
         return warp_kernel_for(v.P, false, false) != nullptr && v.W >= 1 && v.W <= 8 && v.CS == 1;
+    if (v.kind == KIND_WIN)
+        return v.P >= 1 && v.P <= kWinMaxRows && v.W >= 1 && v.W <= 8 && v.CS == 1 &&
+               variant_smem(v) <= 227 * 1024;
     if (v.kind != KIND_CTA) return false;
     if (!cta_kernel_for(v.P, false, false)) return false;
     if (v.W < 1 || v.W > (v.P >= 16 ? 8 : 32) || v.CS < 1 || v.CS > 16) return false;
@@ -411,6 +453,7 @@ bool variant_supported(const Variant& v) {
 // store them as rows of 32)
 static SectorKernel kernel_for(const Variant& v, bool npdu, bool rows = false) {
     if (v.kind == KIND_WARP) return warp_kernel_for(v.P, npdu, rows);
+    if (v.kind == KIND_WIN) return win_kernel_for(v.P, rows);
     return cta_kernel_for(v.P, npdu, v.CS > 1);
 }
 
@@ -443,9 +486,12 @@ static cudaError_t prepare(SectorKernel fn, const Variant& v, size_t smem) {
     return cudaSuccess;
 }
 
-cudaError_t launch_sector(const Variant& v, bool npdu, const LaunchArgs& a, int grid,
+cudaError_t launch_sector(const Variant& v, bool npdu, const LaunchArgs& args, int grid,
                           cudaStream_t stream) {
     if (!variant_supported(v) || grid < 1) return cudaErrorInvalidValue;
+    if (v.kind == KIND_WIN && !npdu) return cudaErrorInvalidValue;  // windows only
+    LaunchArgs a = args;
+    a.win_cap = v.kind == KIND_WIN ? 32 * v.P : 0;
     SectorKernel fn = kernel_for(v, npdu, a.host_resident != 0);
     const size_t smem = variant_smem(v);
     cudaError_t e = prepare(fn, v, smem);

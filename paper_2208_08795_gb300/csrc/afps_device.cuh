@@ -168,6 +168,33 @@ __device__ __forceinline__ void record_status(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
 }
 
+// Whether the status word holds a timeout (any launch on the context since
+// the last afps_sync).  A volatile load: issued where it stands, so it can be
+// placed ahead of a wait and its latency hidden behind it.
+__device__ __forceinline__ int load_status(const int* status) {
+    int v = 0;
+    if (status) asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(status) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool is_timeout(int status) {
+    return status == DEV_TIMEOUT_STAGE || status == DEV_TIMEOUT_DRAIN ||
+           status == DEV_TIMEOUT_EXCHANGE;
+}
+
+// Next item of a dynamic work queue (one ticket per warp, drawn by lane 0).
+// Every warp of the grid draws tickets until one lies past the last item, so
+// a launch draws exactly n_items + (warps in the grid) tickets; the warp that
+// draws the last of them is the last to touch the counter and sets it back
+// to zero for the next launch (no memset between launches).
+__device__ __forceinline__ int queue_next(const LaunchArgs& a, int nwarps, int lane) {
+    unsigned v = 0;
+    if (lane == 0) {
+        v = atomicAdd(a.counter, 1u);
+        if (v == (unsigned)a.n_items + (unsigned)nwarps - 1u) atomicExch(a.counter, 0u);
+    }
+    return (int)__shfl_sync(kFull, v, 0);
+}
+
 // Debug build (AFPS_DEBUG_CHECKS): index v must lie in [lo, hi); otherwise
 // the failure is recorded and v is clamped into the range, so the access it
 // guards stays in bounds.  The regular build returns v unchanged.

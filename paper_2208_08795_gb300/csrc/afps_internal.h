@@ -49,11 +49,14 @@ inline uint64_t div_magic(int32_t d) {
     return d >= 2 ? ~0ull / (uint64_t)d + 1ull : 0ull;
 }
 
-enum Kind : int32_t { KIND_WARP = 0, KIND_CTA = 1 };
+enum Kind : int32_t { KIND_WARP = 0, KIND_CTA = 1, KIND_WIN = 2 };
 
 // A kernel variant.  KIND_WARP: one warp per item, W items per CTA.
 // KIND_CTA: one CTA (CS == 1) or one cluster of CS CTAs per item, W warps
-// per CTA.  P = points held per thread, in registers.
+// per CTA.  P = points held per thread, in registers.  KIND_WIN (NPDU only):
+// one warp per item, W items per CTA, distances in shared memory with cached
+// row maxima; P = rows of 32 points a warp's buffer holds (sectors of up to
+// 32 P points, P <= kWinMaxRows).
 struct Variant {
     int32_t kind;
     int32_t P;
@@ -72,11 +75,17 @@ struct LaunchArgs {
     unsigned int* counter;  // dynamic work queue head (warp kind), or nullptr
     int* status;            // device error word (first error wins)
     uint64_t timeout_ns;
-    uint32_t stall_copy;    // fault injection: arm the barrier, issue no copy
+    uint32_t stall;         // fault injection (STALL_* bits)
     uint32_t npdu_skip;     // Variant::skip
     uint32_t host_resident; // points live in (mapped) host memory: plain loads only
-    uint32_t pad;
+    int32_t win_cap;        // KIND_WIN: points per warp buffer (32 P)
 };
+
+// LaunchArgs::stall bits (fault injection for tests of failure detection):
+// the stage-in arms its barrier but issues no copy; in cluster kernels the
+// last CTA of each cluster sends no exchange records.  Either way the
+// bounded waits run out.
+enum : uint32_t { STALL_COPY = 1u, STALL_EXCHANGE = 2u };
 
 // Device error codes written to *status.
 enum DeviceStatus : int {
@@ -87,9 +96,13 @@ enum DeviceStatus : int {
     DEV_CHECK_FAILED = 4,      // a device-side check of the debug build failed
 };
 
+// KIND_WIN: largest number of 32-point rows per sector (lane l of the warp
+// caches the maxima of rows l, l + 32, ..., up to kWinMaxRows / 32 of them).
+constexpr int kWinMaxRows = 256;
+
 // Points a variant can hold per item.
 inline int64_t variant_capacity(const Variant& v) {
-    return v.kind == KIND_WARP ? 32LL * v.P : 32LL * v.W * v.P * v.CS;
+    return v.kind == KIND_CTA ? 32LL * v.W * v.P * v.CS : 32LL * v.P;
 }
 
 // Dynamic shared memory of a variant (bytes).

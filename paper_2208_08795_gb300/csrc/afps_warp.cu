@@ -55,18 +55,14 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
     dev::pdl_wait();
     dev::pdl_launch_dependents();
     uint32_t phase = 0;
+    bool halted = false;  // a timeout was seen: leave the remaining items undone
 
     const int nwarps = gridDim.x * W;
-    int item;
-    if (a.counter) {
-        unsigned v = 0;
-        if (lane == 0) v = atomicAdd(a.counter, 1u);
-        item = (int)__shfl_sync(dev::kFull, v, 0);
-    } else {
-        item = blockIdx.x * W + w;
-    }
+    int item = a.counter ? dev::queue_next(a, nwarps, lane) : blockIdx.x * W + w;
 
-    while (item < a.n_items) {
+    for (; item < a.n_items;
+         item = a.counter ? dev::queue_next(a, nwarps, lane) : item + nwarps) {
+        if (halted) continue;
         const ItemDesc d = dev::load_item(a, item);
         const int n = dev::checked(d.n, 1, 32 * P + 1, a.status);  // fits the staging buffer
 
@@ -76,9 +72,13 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         bool bulk;
         const float* pts =
             dev::stage_points(a.xyz + 3 * d.src, n, buf, bar, lane == 0, lane, 32, &bulk,
-                              a.stall_copy != 0, a.host_resident != 0);
+                              (a.stall & STALL_COPY) != 0, a.host_resident != 0);
+        // a timeout recorded by any warp so far (the load overlaps the copy)
+        const int seen = dev::load_status(a.status);
+        bool late = false;
         if (bulk) {
-            if (!dev::mbar_wait_bounded(bar, phase, a.timeout_ns)) {
+            late = !dev::mbar_wait_bounded(bar, phase, a.timeout_ns);
+            if (late) {
                 dev::record_status(a.status, DEV_TIMEOUT_STAGE);
                 if (!dev::mbar_wait_bounded(bar, phase, a.timeout_ns))
                     dev::record_status(a.status, DEV_TIMEOUT_DRAIN);
@@ -86,6 +86,11 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
             phase ^= 1u;
         }
         __syncwarp();
+        // after a timeout (here or anywhere on the context) nothing is
+        // computed on shared memory the copy may not have filled; the warp
+        // only draws its remaining tickets
+        halted = __any_sync(dev::kFull, late || dev::is_timeout(seen));
+        if (halted) continue;
 
         // rows i = 2h, 2h+1 share packed registers (f32x2 arithmetic)
         constexpr int PP = (P + 1) / 2;
@@ -249,14 +254,6 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         if (full_first && t < c) round(t++, 0, n - 1);  // full-first-pass reading: the first update is the whole sector
         for (; t < c; ++t) round(t, p - kl, p + kr);
         if (rows_out && lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
-
-        if (a.counter) {
-            unsigned v = 0;
-            if (lane == 0) v = atomicAdd(a.counter, 1u);
-            item = (int)__shfl_sync(dev::kFull, v, 0);
-        } else {
-            item += nwarps;
-        }
     }
 }
 

@@ -1,0 +1,267 @@
+// afps_win.cu -- NPDU sectors (Sec. III-C) at a constant cost per iteration.
+//
+// One warp per (cloud, sector) work item, sectors of up to 32 * 32 * R points.
+// The register kernels (afps_warp.cu, afps_cta.cu) rescan every running
+// distance of the sector for each argmax, although NPDU changes only the k + 1
+// distances of the window.  Here the distances live in shared memory beside
+// the staged xyz, and the warp caches the maximum of each row of 32 points
+// (lane l holds the maxima of rows l, l + 32, ...: R slots).  An iteration
+// touches only what its window touches:
+//   update   lane i updates point wl + i of the window [wl, wh] (the k
+//            neighbours and the sample, clipped to the sector) in shared
+//            memory: d = (dx*dx + dy*dy) + dz*dz, D = min(D, d);
+//   rows     every row the window overlaps (at most two for k < 32) gets its
+//            maximum recomputed: redux.sync max of the distance bits, then
+//            redux.sync min of the lane among those that hold it;
+//   argmax   each lane offers the best of its cached rows that the window
+//            missed and of its own column of the touched rows; two redux.sync
+//            steps give the maximum and the lowest index that holds it.
+// Distances only decrease, so a row the window misses keeps its maximum and
+// the lowest index attaining it: the result is exactly the lowest-index
+// argmax of a full scan (Algorithm 1), bit for bit.
+//
+// The stride phase of the literal reading (every distance starts at 1e10, no
+// first full pass; the first samples are p, p + q, p + 2q, ... while points
+// past the last window are untouched) runs as one parallel pass, as in the
+// register kernels, and computes every row maximum on the way.
+#include "afps_device.cuh"
+
+namespace afps {
+
+namespace {
+
+// Row r's maximum (distance bits m, index idx) into the slot of its owner
+// lane r % 32 (slot r / 32).
+template <int R>
+__device__ __forceinline__ void set_row(unsigned (&rmb)[R], unsigned (&rmi)[R], int r,
+                                        unsigned m, unsigned idx, int lane) {
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+        if (r == lane + 32 * s) {
+            rmb[s] = m;
+            rmi[s] = idx;
+        }
+}
+
+// Every distance at 1e10 (points) or +0 (the padding of the last row, which
+// loses every tie); every row's maximum is 1e10 at its first point.
+template <int R>
+__device__ __forceinline__ void reset_rows(float* Ds, int n, int rows, unsigned (&rmb)[R],
+                                           unsigned (&rmi)[R], int lane) {
+    for (int j = lane; j < 32 * rows; j += 32) Ds[j] = j < n ? 1e10f : 0.f;
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+        const int r = lane + 32 * s;
+        rmb[s] = r < rows ? __float_as_uint(1e10f) : 0u;
+        rmi[s] = r < rows ? (unsigned)(32 * r) : 0xffffffffu;  // no row: loses every tie
+    }
+}
+
+// The lowest-index maximum of row r from its 32 distance bits (one per lane).
+__device__ __forceinline__ void row_max(unsigned b, int lane, unsigned& m, unsigned& l) {
+    m = __reduce_max_sync(dev::kFull, b);
+    l = __reduce_min_sync(dev::kFull, b == m ? (unsigned)lane : 32u);
+}
+
+}  // namespace
+
+// ROWS: the indices go to host memory (over the C2C link), as rows of 32.
+template <int R, bool ROWS>
+__global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    const int cap = a.win_cap;  // points per warp: xyz 12 cap + 16 bytes, distances 4 cap
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    unsigned char* buf = smem + 16 * ((8 * W + 15) / 16) + (size_t)w * (16 * (size_t)cap + 16);
+    float* Ds = reinterpret_cast<float*>(buf + 12 * (size_t)cap + 16);
+    const uint32_t bar = dev::smem_u32(&bars[w]);
+    if (lane == 0) {
+        dev::mbar_init(bar, 1);
+        dev::fence_mbar_init();
+    }
+    __syncwarp();
+    // A computed first item (no table, no queue) needs no memory access, so
+    // its points can be prefetched into L2 while the previous kernel of the
+    // stream still runs.
+    if (!a.items && !a.counter && !a.host_resident && blockIdx.x * W + w < a.n_items) {
+        const ItemDesc d0 = dev::load_item(a, blockIdx.x * W + w);
+        const char* g = reinterpret_cast<const char*>(a.xyz + 3 * d0.src);
+        for (int off = 128 * lane; off < 12 * d0.n; off += 32 * 128) dev::prefetch_l2(g + off);
+    }
+    // Programmatic dependent launch, as in the other sector kernels.
+    dev::pdl_wait();
+    dev::pdl_launch_dependents();
+    uint32_t phase = 0;
+    bool halted = false;  // a timeout was seen: leave the remaining items undone
+
+    const int nwarps = gridDim.x * W;
+    int item = a.counter ? dev::queue_next(a, nwarps, lane) : blockIdx.x * W + w;
+
+    while (item < a.n_items) {
+        if (!halted) {
+            const ItemDesc d = dev::load_item(a, item);
+            const int n = dev::checked(d.n, 1, cap + 1, a.status);  // fits the warp's buffer
+
+            // ---- stage-in (the previous item's readers are done: fence + sync)
+            dev::fence_proxy_async_smem();
+            __syncwarp();
+            bool bulk;
+            const float* pts =
+                dev::stage_points(a.xyz + 3 * d.src, n, buf, bar, lane == 0, lane, 32, &bulk,
+                                  (a.stall & STALL_COPY) != 0, a.host_resident != 0);
+            // a timeout recorded by any warp so far (the load overlaps the copy)
+            const int seen = dev::load_status(a.status);
+            bool late = false;
+            if (bulk) {
+                late = !dev::mbar_wait_bounded(bar, phase, a.timeout_ns);
+                if (late) {
+                    dev::record_status(a.status, DEV_TIMEOUT_STAGE);
+                    if (!dev::mbar_wait_bounded(bar, phase, a.timeout_ns))
+                        dev::record_status(a.status, DEV_TIMEOUT_DRAIN);
+                }
+                phase ^= 1u;
+            }
+            __syncwarp();
+            halted = __any_sync(dev::kFull, late || dev::is_timeout(seen));
+            if (!halted) {
+                const int rows = (n + 31) >> 5;
+                unsigned rmb[R], rmi[R];  // cached row maxima: bits, lowest index
+                reset_rows<R>(Ds, n, rows, rmb, rmi, lane);
+
+                int32_t* out = a.out + d.dst;
+                const int c = dev::checked(d.c, 1, n + 1, a.status);
+                const int kl = d.kl;
+                const int kr = d.kr;
+                const bool full_first = (d.flags & ITEM_FULL_FIRST) != 0;
+                int p = dev::checked(d.first, 0, n, a.status);
+                // Device indices: lane 0 stores each sample.  Host indices (C2C
+                // link, where each store is a transfer): lane t % 32 keeps
+                // sample t and the warp stores rows of 32.
+                int obuf = lane == 0 ? d.lo + p : 0;
+                if (lane == 0 && !ROWS) out[0] = d.lo + p;
+                int t0 = 1;
+                if (!full_first && p <= kl && kl <= kr) {
+                    // Stride phase (see afps_warp.cu): samples p, p + q, ...
+                    // (q = kr + 1) until a window reaches the sector's end;
+                    // their windows are applied at once (a point lies in at
+                    // most two of them), valid if every windowed distance is
+                    // below 1e10.  Rows are visited in order, so each row's
+                    // maximum comes from registers on the way.
+                    const int q = kr + 1;
+                    const int x = n - 1 - kr - p;
+                    const dev::SmallDiv divq((uint32_t)q);
+                    const int ts = x <= 0 ? 1 : (int)divq((uint32_t)(x + q - 1)) + 1;
+                    const int tn = min(ts, c);      // stride samples emitted
+                    const int tw = min(ts, c - 1);  // ... whose window is applied
+                    bool ok = true;
+                    for (int i = 0; i < rows; ++i) {
+                        const int j = 32 * i + lane;
+                        float v = 0.f;  // padding
+                        if (j < n) {
+                            v = 1e10f;
+                            const float px = pts[3 * j], py = pts[3 * j + 1], pz = pts[3 * j + 2];
+                            const int y = j - kr - p;
+                            // unsigned divisions: both operands are >= 0 (p <= kl)
+                            const int tlo = y <= 0 ? 0 : (int)divq((uint32_t)(y + q - 1));
+                            const int thi = min(tw - 1, (int)divq((uint32_t)(j + kl - p)));
+#pragma unroll
+                            for (int u = 0; u < 2; ++u) {
+                                if (tlo + u <= thi) {
+                                    const int sj = dev::checked(p + (tlo + u) * q, 0, n, a.status);
+                                    const float dd = dev::sqdist(px, py, pz, pts[3 * sj],
+                                                                 pts[3 * sj + 1], pts[3 * sj + 2]);
+                                    ok = ok && dd < 1e10f;
+                                    v = fminf(v, dd);
+                                }
+                            }
+                        }
+                        Ds[j] = v;
+                        unsigned m, l;
+                        row_max(__float_as_uint(v), lane, m, l);
+                        set_row<R>(rmb, rmi, i, m, (unsigned)(32 * i) + l, lane);
+                    }
+                    if (__all_sync(dev::kFull, ok)) {
+                        if (ROWS) {
+                            for (int r0 = 0; r0 + 32 <= tn; r0 += 32)
+                                out[r0 + lane] = d.lo + p + (r0 + lane) * q;
+                            obuf = d.lo + p + (((tn - 1) & ~31) + lane) * q;
+                        } else {
+                            for (int t = 1 + lane; t < tn; t += 32) out[t] = d.lo + p + t * q;
+                        }
+                        p += (tn - 1) * q;
+                        t0 = tn;  // re-applying the last window is a no-op
+                    } else {
+                        __syncwarp();
+                        reset_rows<R>(Ds, n, rows, rmb, rmi, lane);
+                    }
+                }
+                __syncwarp();
+
+                for (int t = t0; t < c; ++t) {
+                    // window of the last sample p (the whole sector for the
+                    // first update of the full-first-pass reading)
+                    const bool whole = full_first && t == 1;
+                    const int wl = whole ? 0 : max(p - kl, 0);
+                    const int wh = whole ? n - 1 : min(p + kr, n - 1);
+                    const float qx = pts[3 * p], qy = pts[3 * p + 1], qz = pts[3 * p + 2];
+                    for (int j = wl + lane; j <= wh; j += 32) {
+                        const float dd =
+                            dev::sqdist(pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], qx, qy, qz);
+                        Ds[j] = fminf(Ds[j], dd);
+                    }
+                    __syncwarp();
+                    const int r0 = wl >> 5, r1 = wh >> 5;
+                    // this lane's candidate: its cached rows the window missed ...
+                    unsigned cb = 0u, ci = 0xffffffffu;
+#pragma unroll
+                    for (int s = 0; s < R; ++s) {
+                        const int r = lane + 32 * s;
+                        const bool kept = r < r0 || r > r1;
+                        const bool better = rmb[s] > cb || (rmb[s] == cb && rmi[s] < ci);
+                        cb = kept && better ? rmb[s] : cb;
+                        ci = kept && better ? rmi[s] : ci;
+                    }
+                    // ... and its column of the rows it touched, whose maxima
+                    // are recomputed
+                    for (int r = r0; r <= r1; ++r) {
+                        const unsigned j = (unsigned)(32 * r + lane);
+                        const unsigned b = __float_as_uint(Ds[j]);
+                        const bool better = b > cb || (b == cb && j < ci);
+                        cb = better ? b : cb;
+                        ci = better ? j : ci;
+                        unsigned m, l;
+                        row_max(b, lane, m, l);
+                        set_row<R>(rmb, rmi, r, m, (unsigned)(32 * r) + l, lane);
+                    }
+                    const unsigned mx = __reduce_max_sync(dev::kFull, cb);
+                    p = dev::checked((int)__reduce_min_sync(dev::kFull, cb == mx ? ci : 0xffffffffu),
+                                     0, n, a.status);
+                    if (ROWS) {
+                        obuf = lane == (t & 31) ? d.lo + p : obuf;
+                        if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
+                    } else if (lane == 0) {
+                        out[t] = d.lo + p;
+                    }
+                }
+                if (ROWS && lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
+            }
+        }
+        item = a.counter ? dev::queue_next(a, nwarps, lane) : item + nwarps;
+    }
+}
+
+using SectorKernel = void (*)(LaunchArgs);
+
+// Kernel for sectors of up to 32 * rows points (rows <= kWinMaxRows).
+SectorKernel win_kernel_for(int rows, bool host_rows) {
+    const int slots = (rows + 31) / 32;
+    if (slots <= 1) return host_rows ? afps_win_kernel<1, true> : afps_win_kernel<1, false>;
+    if (slots <= 2) return host_rows ? afps_win_kernel<2, true> : afps_win_kernel<2, false>;
+    if (slots <= 4) return host_rows ? afps_win_kernel<4, true> : afps_win_kernel<4, false>;
+    if (slots <= 8) return host_rows ? afps_win_kernel<8, true> : afps_win_kernel<8, false>;
+    return nullptr;
+}
+
+}  // namespace afps

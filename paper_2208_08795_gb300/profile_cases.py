@@ -12,7 +12,7 @@ Cases (inputs from `synth`; kernel variants from the planner or the cache):
   fps2048      the same batch, plain FPS (M = 1)
   cluster32k   one 32768-point slab cloud, C = 8192, plain FPS (one thread-block cluster)
   npdu32k      the same cloud, NPDU-AFPS M = 32, k = 16
-  ragged       256 clouds of 2K-32K points, C = N/4, sectors of ~256 points, k = 16 (persistent)
+  ragged       256 clouds of 2K-32K points, C = N/4, sectors of ~256 points, k = 8 / 16 (persistent)
   chain        one LiDAR-like frame, levels 16384 -> 4096 -> 1024 -> 256, M = 32, k = 16
   sort         the object batch in random storage order, sorted by x
   group        ball query (r = 0.2, K = 32) around the headline samples of the batch
@@ -41,7 +41,7 @@ def run(case: str, reps: int, tune_cache: str | None = None) -> None:
     if case in ("headline", "fps2048", "ragged"):
         if case == "ragged":
             clouds, C, M = synth.ragged_batch(3, 256)
-            k = 16
+            k = [8 if m <= 8 else 16 for m in M]  # Sec. IV-D: k = 8 for M <= 8, else 16
         else:
             clouds, C = synth.object_batch(1, 32, 2048), 512
             M, k = (32, 16) if case == "headline" else (1, 0)

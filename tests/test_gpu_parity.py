@@ -87,9 +87,12 @@ def test_slab_large(S, N, M, npdu):
 def test_ragged_batch_256(S, npdu):
     clouds, Cs, Ms = synth.ragged_batch(3, 256)
     ks = [k_rule(m) if npdu else 0 for m in Ms]
-    got, _ = gpu_batch(S, clouds, Cs, Ms, ks)
+    got, ba = gpu_batch(S, clouds, Cs, Ms, ks)
     for b, P in enumerate(clouds):
         assert_same(got[b], oracle.afps(P, Cs[b], Ms[b], ks[b]), f"cloud {b}")
+    if npdu:  # every sector of the batch in one launch of the window kernel
+        plan = S.describe_batched(ba)
+        assert plan.startswith("win ") and ";" not in plan and plan.endswith("items=17576"), plan
 
 
 # --------------------------------------------------------------- edge cases
@@ -177,6 +180,14 @@ VARIANTS = [  # (N, C, M, k, kind, P, W, CS)
     (5000, 1000, 6, 0, 0, 32, 2, 1), (5000, 1000, 6, 16, 0, 32, 4, 1, 1),
     (4000, 800, 6, 16, 0, 24, 4, 1), (4000, 800, 6, 9, 0, 24, 2, 1, 1),
     (3000, 600, 4, 16, 1, 4, 8, 1, 1), (20000, 2000, 2, 8, 1, 8, 8, 5, 1),
+    # window kernel (NPDU only): P = rows of 32 points per warp buffer; one,
+    # two, four and eight row-maximum slots per lane; windows narrower and
+    # wider than a row; every point sampled
+    (3000, 300, 10, 9, 2, 10, 4, 1), (3000, 300, 10, 16, 2, 16, 2, 1),
+    (2000, 1000, 2, 16, 2, 32, 1, 1), (2100, 500, 2, 16, 2, 33, 2, 1),
+    (20000, 4000, 4, 8, 2, 157, 1, 1), (8192, 2048, 1, 8, 2, 256, 1, 1),
+    (640, 640, 20, 16, 2, 1, 8, 1), (4000, 1500, 8, 70, 2, 16, 8, 1),
+    (3000, 900, 3, 1, 2, 40, 2, 1),
 ]
 
 
@@ -196,6 +207,8 @@ def test_forced_variant(tmp_path, row):
         desc = s.describe_plan(n_max, c_max, k, M)
         if kind == 0:
             want = f"warp P={Pp} W={W}"
+        elif kind == 2:
+            want = f"win P={Pp} W={W}"
         elif CS > 1:
             want = f"cluster P={Pp} W={W} CS={CS}"
         else:
@@ -231,7 +244,8 @@ def test_table_iv_sizes(S, N, M, k):
 # outside the half window, the other window reading, and coordinates far
 # enough apart to reach 1e10.
 STRIDE_KERNELS = [(0, 2, 4, 1), (0, 8, 2, 1), (1, 2, 8, 1), (1, 8, 4, 1), (1, 16, 8, 1),
-                  (1, 4, 8, 4), (1, 16, 4, 2)]  # the last two: thread-block clusters
+                  (1, 4, 8, 4), (1, 16, 4, 2),  # these two: thread-block clusters
+                  (2, 9, 4, 1), (2, 40, 2, 1)]  # window kernel, one and two slots per lane
 
 
 def stride_len(n, k, r, method=0):
@@ -256,7 +270,7 @@ def stride_cases(n):
 def test_npdu_stride_phase(tmp_path, kern):
     kind, Pp, W, CS = kern
     build_mod.build()
-    cap = 32 * Pp if kind == 0 else 32 * W * Pp * CS
+    cap = 32 * W * Pp * CS if kind == 1 else 32 * Pp
     sizes = [cap - 3] + ([288] if cap >= 288 else [])
     for n in sizes:
         M = 3
@@ -679,14 +693,99 @@ def test_bounded_wait_reports_timeout_and_context_survives():
         s2.close()
 
 
+def _timed_stall(s, fn):
+    import time
+    t0 = time.perf_counter()
+    fn()
+    with pytest.raises(B.AfpsError) as ei:
+        s.sync()
+    assert ei.value.code == B.AFPS_ERR_TIMEOUT
+    s.sync()  # cleared
+    return time.perf_counter() - t0
+
+
+def test_timeout_halts_every_kernel_kind():
+    """After a bounded wait runs out, the kernels compute nothing more: each
+    warp, CTA or cluster leaves its remaining items undone, so a stalled call
+    costs a few timeouts, not one per item or per iteration.  Injected on the
+    host side: stage-in copies never issued (window kernel over the 17,576
+    items of the ragged batch, through its work queue; the warp and CTA
+    kernels; the 8-CTA cluster of plain FPS on a 32K-point cloud), and
+    cluster records never sent (the same cluster, 8,192 exchanges, which
+    without the halt would each wait out the timeout).  The GPU and a fresh
+    context keep working."""
+    build_mod.build()
+    clouds, Cs, Ms = synth.ragged_batch(3, 256)
+    ks = [k_rule(m) for m in Ms]
+    xyz, off = synth.pack(clouds)
+    xr = torch.from_numpy(xyz).cuda()
+    ba = B.BatchArgs(off, Cs, Ms, ks, 0)
+    P = synth.slab_cloud(2, 32768)
+    xs = torch.from_numpy(P).cuda()
+    tmo = 1_000_000  # 1 ms
+    x4k = xs[:4096].contiguous()
+    cases = [  # (flags, call, kernel kind the planner picks)
+        (B.AFPS_FLAG_TEST_STALL_COPY, lambda s: s.sample_batched(xr, ba), (17576, "win")),
+        (B.AFPS_FLAG_TEST_STALL_COPY, lambda s: s.sample(xs, 4096, 512, 0, 0), (512, "warp")),
+        (B.AFPS_FLAG_TEST_STALL_COPY, lambda s: s.sample(x4k, 1024, 1, 0, 0), (1, "cta")),
+        (B.AFPS_FLAG_TEST_STALL_COPY, lambda s: s.sample(xs, 1024, 1, 0, 0), (1, "cluster")),
+        (B.AFPS_FLAG_TEST_STALL_EXCHANGE, lambda s: s.sample(xs, 8192, 1, 0, 0), (1, "cluster")),
+    ]
+    for flags, call, (items, kind) in cases:
+        s = B.Sampler(0, timeout_ns=tmo, flags=flags)
+        try:
+            if items == 17576:
+                assert s.describe_batched(ba).startswith(kind)
+            else:
+                n = {512: 64, 1: 32768 if kind == "cluster" else 4096}[items]
+                assert s.describe_plan(n, 8, 0, items).startswith(kind)
+            secs = _timed_stall(s, lambda: call(s))
+            assert secs < 1.0, (flags, kind, secs)  # thousands of timeouts would take seconds
+        finally:
+            s.close()
+    s2 = B.Sampler(0)
+    try:
+        assert_same(gpu_one(s2, P, 8192, 1, 0), oracle.afps(P, 8192, 1, 0), "fresh context")
+        got, _ = gpu_batch(s2, clouds[:8], Cs[:8], Ms[:8], ks[:8])
+        for b in range(8):
+            assert_same(got[b], oracle.afps(clouds[b], Cs[b], Ms[b], ks[b]), f"cloud {b}")
+    finally:
+        s2.close()
+
+
+def test_timeout_halts_later_launches_until_sync():
+    """A recorded timeout makes later launches on the context skip their
+    work (their outputs stay untouched) until afps_sync reports it; after
+    that the same call computes normally."""
+    build_mod.build()
+    P = synth.uniform_cloud(4, 4096)
+    x = torch.from_numpy(P).cuda()
+    s = B.Sampler(0, timeout_ns=1_000_000, flags=B.AFPS_FLAG_TEST_STALL_EXCHANGE)
+    try:
+        s.sample(torch.from_numpy(synth.slab_cloud(2, 16384)).cuda(), 4096, 1, 0, 0)
+        out = torch.full((512,), -1, dtype=torch.int32, device="cuda")
+        s.sample(x, 512, 16, 16, 0, out=out)  # queued behind the stalled call
+        torch.cuda.synchronize()
+        assert bool((out == -1).all())
+        with pytest.raises(B.AfpsError) as ei:
+            s.sync()
+        assert ei.value.code == B.AFPS_ERR_TIMEOUT
+        s.sample(x, 512, 16, 16, 0, out=out)
+        s.sync()
+        assert_same(out.cpu().numpy(), oracle.afps(P, 512, 16, 16), "after sync")
+    finally:
+        s.close()
+
+
 def test_allocation_failure_is_reported_and_context_survives(objects):
     """Fault injection on the host: every growth of the context's workspace
-    fails as on an exhausted device.  Batched calls (which need a work-queue
-    counter) return AFPS_ERR_NO_MEMORY before launching anything, their
+    fails as on an exhausted device.  Batched calls that need an item table
+    return AFPS_ERR_NO_MEMORY before launching anything, their
     outputs untouched; a server cannot reserve its tables; the context, the
     GPU and a fresh context still work."""
     build_mod.build()
-    xyz, off = synth.pack(objects[:4])
+    # clouds of different sizes: the batch needs an item table
+    xyz, off = synth.pack([objects[0][:1500], objects[1], objects[2][:1900], objects[3]])
     x = torch.from_numpy(xyz).cuda()
     s = B.Sampler(0, flags=B.AFPS_FLAG_TEST_FAIL_ALLOC)
     try:
