@@ -340,7 +340,7 @@ std::vector<Variant> candidate_variants(int64_t n_max, bool npdu) {
             ok.push_back(s);
         }
     }
-    if (npdu && n_max <= 32LL * afps::kWinMaxRows)
+    if (npdu && win_default(n_max))  // (up to 64 points the register kernels win)
         for (int W : {1, 2, 4, 8}) {
             const Variant v = win_variant(n_max, W);
             if (afps::variant_supported(v)) ok.push_back(v);
@@ -1469,46 +1469,105 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
     cudaEvent_t e0, e1;
     AFPS_CUDA(ctx, cudaEventCreate(&e0));
     AFPS_CUDA(ctx, cudaEventCreate(&e1));
-    // candidates may use a work queue where the plan's variants do not
-    rc = grow_counters(ctx, ctx->counters, plan.classes.size(), st);
+    // candidates may use a work queue where the plan's variants do not (one
+    // more counter for the merged launches below)
+    rc = grow_counters(ctx, ctx->counters, plan.classes.size() + 1, st);
     if (rc != AFPS_OK) return rc;
     const ItemDesc* d_items = static_cast<const ItemDesc*>(ctx->items.p);
     unsigned int* counters = static_cast<unsigned int*>(ctx->counters.p);
+    // one warm-up round and three timed ones of four launches back to back
+    // (a single launch of a small class lasts little longer than its launch
+    // latency); < 0 if the variant cannot run
+    auto time_launch = [&](const Variant& v, bool npdu, const ItemDesc* items, size_t count,
+                           unsigned int* counter, const afps::SingleCloud* run) -> float {
+        if (grid_for(v, count) < 1 || afps::max_active_clusters(v) < 1) return -1.f;
+        float ms_sum = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 4 && ok; ++rep) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) ok = false;
+            for (int l = 0; l < 4 && ok; ++l)
+                if (launch_class(ctx, v, npdu, items, count, counter, d_xyz, d_out, st, false,
+                                 run) != AFPS_OK)
+                    ok = false;
+            if (ok && cudaEventRecord(e1, st) != cudaSuccess) ok = false;
+            float ms = 0.f;
+            if (ok && (cudaEventSynchronize(e1) != cudaSuccess ||
+                       cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                ok = false;
+            if (rep > 0) ms_sum += ms;
+        }
+        if (!ok) {
+            cudaGetLastError();
+            return -1.f;
+        }
+        return ms_sum;
+    };
     int tuned = 0;
+    std::vector<float> best_of(plan.classes.size(), 0.f);
     for (size_t i = 0; i < plan.classes.size() && rc == AFPS_OK; ++i) {
         ClassPlan& cp = plan.classes[i];
         float best_ms = 1e30f;
         Variant best = cp.v;
         for (const Variant& v : candidate_variants(cp.n_max, cp.npdu)) {
-            if (grid_for(v, cp.count) < 1 || afps::max_active_clusters(v) < 1) continue;
-            float ms_sum = 0.f;
-            bool ok = true;
-            for (int rep = 0; rep < 4 && ok; ++rep) {  // one warm-up, three timed
-                if (cudaEventRecord(e0, st) != cudaSuccess) ok = false;
-                if (ok && launch_class(ctx, v, cp.npdu,
-                                       cp.uniform ? nullptr : d_items + cp.first, cp.count,
-                                       counters + i, d_xyz, d_out, st, false,
-                                       cp.run()) != AFPS_OK)
-                    ok = false;
-                if (ok && cudaEventRecord(e1, st) != cudaSuccess) ok = false;
-                float ms = 0.f;
-                if (ok && (cudaEventSynchronize(e1) != cudaSuccess ||
-                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                    ok = false;
-                if (rep > 0) ms_sum += ms;
-            }
-            if (!ok) {
-                cudaGetLastError();
-                continue;
-            }
-            if (ms_sum < best_ms) {
-                best_ms = ms_sum;
+            const float ms = time_launch(v, cp.npdu, cp.uniform ? nullptr : d_items + cp.first,
+                                         cp.count, counters + i, cp.run());
+            if (ms >= 0.f && ms < best_ms) {
+                best_ms = ms;
                 best = v;
             }
         }
         ctx->tuned[class_key(cp.npdu, cp.n_max, cp.c_max, cp.count)] = best;
         cp.v = best;
+        best_of[i] = best_ms;
         ++tuned;
+    }
+    // Consecutive NPDU table classes the window kernel can serve with one
+    // template run as one launch when that is faster than their best
+    // separate launches (one queue over all their items has a shorter tail);
+    // their entries then name window variants with a common warp count,
+    // which the planner merges (merge_window_classes).
+    for (size_t i = 0; i < plan.classes.size();) {
+        auto fits = [&](const ClassPlan& c) {
+            return c.npdu && !c.uniform && c.n_max <= 32LL * afps::kWinMaxRows;
+        };
+        if (!fits(plan.classes[i])) {
+            ++i;
+            continue;
+        }
+        const int slots = win_slots(win_variant(plan.classes[i].n_max));
+        size_t j = i + 1;
+        while (j < plan.classes.size() && fits(plan.classes[j]) &&
+               win_slots(win_variant(plan.classes[j].n_max)) == slots &&
+               plan.classes[j].first == plan.classes[j - 1].first + plan.classes[j - 1].count)
+            ++j;
+        if (j - i >= 2) {
+            float separate = 0.f;
+            size_t count = 0;
+            int64_t n_max = 0;
+            for (size_t c = i; c < j; ++c) {
+                separate += best_of[c];
+                count += plan.classes[c].count;
+                n_max = std::max(n_max, plan.classes[c].n_max);
+            }
+            float best_ms = separate;
+            int best_w = 0;
+            for (int W : {1, 2, 4, 8}) {
+                const Variant v = win_variant(n_max, W);
+                if (!afps::variant_supported(v)) continue;
+                const float ms = time_launch(v, true, d_items + plan.classes[i].first, count,
+                                             counters + plan.classes.size(), nullptr);
+                if (ms >= 0.f && ms < best_ms) {
+                    best_ms = ms;
+                    best_w = W;
+                }
+            }
+            for (size_t c = i; best_w && c < j; ++c) {
+                ClassPlan& cp = plan.classes[c];
+                cp.v = win_variant(cp.n_max, best_w);
+                ctx->tuned[class_key(true, cp.n_max, cp.c_max, cp.count)] = cp.v;
+            }
+        }
+        i = j;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

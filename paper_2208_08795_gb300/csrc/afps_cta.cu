@@ -6,28 +6,27 @@
 // chunks, one per CTA; each CTA stages its chunk into shared memory by bulk
 // copy and thread t keeps chunk points t + T i (i < P) in registers.
 //
-// One iteration = one barrier:
+// One iteration = one CTA barrier:
 //   1. update + local argmax in registers (all points, or the NPDU window);
-//   2. warp argmax (two redux.sync steps), then the warp's record {distance
-//      bits, ~index} goes to slot (rank, warp): with CS > 1, lanes 0..CS-1
-//      store it with the point's x, y, z into CTA `lane` by a distributed-
-//      shared-memory store (st.shared::cluster); with CS == 1 lane 0 stores
-//      the 8-byte key;
-//   3. CS == 1: bar.sync.  CS > 1: the records travel by st.async, whose
-//      bytes complete a transaction count on the receiving CTA's mbarrier
-//      (one per record buffer); every thread waits on its own CTA's
-//      mbarrier, which is cheaper than a full cluster barrier (measured
-//      260-850 ns per exchange against 390-1120 ns for 2-16 CTAs).  After
-//      reading, the CTA re-arms that buffer's mbarrier behind a bar.sync; a
-//      peer can only write that buffer again after receiving this CTA's
-//      next records, which are sent after the re-arm;
-//   4. every warp reduces the CS * W records itself (a lane per record, then
-//      redux.sync), which yields the next sample without a second barrier;
-//      its coordinates come from this CTA's shared memory (CS == 1) or from
-//      the owner warp's record, whose slot follows from the index (CS > 1).
-//      Records are double-buffered by exchange parity, so a record is never
-//      overwritten before every reader passed the barrier that follows its
-//      read.
+//   2. warp argmax (two redux.sync steps) to a key {distance bits, ~index}.
+//      CS == 1: lane 0 stores the key as the warp's record, then bar.sync.
+//      CS > 1: the warps' keys meet in shared memory; behind a bar.sync
+//      warp 0 reduces them to the CTA's record and its lanes 0..CS-1 store
+//      that record, with the winning point's x, y, z, into slot `rank` of
+//      every CTA of the cluster (itself included) by st.async, whose bytes
+//      complete a transaction count on the receiving CTA's mbarrier (one per
+//      record buffer).  One record per CTA keeps each mbarrier at CS
+//      transfers per exchange; every thread then waits on its own CTA's
+//      mbarrier, which is cheaper than a cluster barrier.  The buffer of the
+//      previous exchange is re-armed behind the same bar.sync (all its
+//      readers have passed it), before this CTA's records can let a peer
+//      start the next exchange;
+//   3. every warp reduces the exchange's records itself (a lane per record,
+//      then redux.sync), which yields the next sample without a second
+//      barrier; its coordinates come from this CTA's shared memory (CS == 1)
+//      or from its owner CTA's record (CS > 1).  Records are double-buffered
+//      by exchange parity, so a record is never overwritten before every
+//      reader passed the barrier that follows its read.
 #include <map>
 #include <mutex>
 #include <set>
@@ -55,12 +54,17 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
     const int W = T >> 5;
     const int CS = CLUSTER ? (int)dev::cluster_nctarank() : 1;
     const int rank = CLUSTER ? (int)dev::cluster_ctarank() : 0;
-    const int E = CS * W;
+    // records per exchange buffer: one per CTA of the cluster, or one per
+    // warp of the CTA
+    const int E = CLUSTER ? CS : W;
 
-    // [stage-in barrier | exchange barriers x2 | pad] [records 2 x E] [points]
+    // [stage-in barrier | exchange barriers x2 | pad] [records 2 x E]
+    // [cluster: the warps' keys, W x 8 bytes, padded to 16] [points]
     uint64_t* barp = reinterpret_cast<uint64_t*>(smem);
     Rec* recs = reinterpret_cast<Rec*>(smem + 32);
-    unsigned char* buf = smem + 32 + 2 * E * sizeof(Rec);
+    uint2* wkeys = reinterpret_cast<uint2*>(smem + 32 + 2 * E * sizeof(Rec));
+    unsigned char* buf =
+        smem + 32 + 2 * E * sizeof(Rec) + (CLUSTER ? 16 * ((8 * W + 15) / 16) : 0);
     const uint32_t bar = dev::smem_u32(barp);
     const uint32_t xbar0 = dev::smem_u32(barp + 1), xbar1 = dev::smem_u32(barp + 2);
     const uint32_t xbytes = (uint32_t)(E * sizeof(Rec));  // expected per exchange
@@ -273,6 +277,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             }
         }
 
+        bool xlate = false;  // the last exchange timed out
         for (int t = t0; t < c; ++t) {
             // 1. update + local argmax (chunk-local offsets)
             const bool whole = full_first && t == 1;  // full first pass reading
@@ -331,22 +336,44 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             const uint32_t xbar = xb ? xbar1 : xbar0;
             Rec* R = recs + xb * E;
             if (CLUSTER) {
-                // fault injection: the cluster's last CTA sends no records
-                const bool send = !((a.stall & STALL_EXCHANGE) && rank == CS - 1);
-                if (lane < CS && send) {
-                    const float wx = pts[3 * jw], wy = pts[3 * jw + 1], wz = pts[3 * jw + 2];
-                    const uint32_t slot = dev::smem_u32(&R[rank * W + w]);
-                    const uint32_t remote = dev::mapa(slot, (uint32_t)lane);
-                    const uint32_t rbar = dev::mapa(xbar, (uint32_t)lane);
-                    dev::st_async_v4(remote, rbar, m, jinv, __float_as_uint(wx), __float_as_uint(wy));
-                    dev::st_async_v4(remote + 16, rbar, __float_as_uint(wz), 0u, 0u, 0u);
+                // The warps' keys meet in this CTA's shared memory; behind one
+                // CTA barrier warp 0 reduces them to the CTA's record and its
+                // lanes 0..CS-1 send that record, with the winner's x, y, z,
+                // to every CTA of the cluster (this one included): CS records
+                // per exchange instead of one per warp, so each receiving
+                // mbarrier counts CS transfers, not CS x W.
+                if (lane == 0) wkeys[w] = make_uint2(m, jinv);
+                // a record of the previous exchange that did not come stops
+                // the item here (peers stop at their next exchange, which
+                // this CTA no longer feeds)
+                halted = __syncthreads_or(xlate) != 0;
+                if (halted) break;
+                if (w == 0) {
+                    // every reader of the buffer the previous exchange used has
+                    // passed the barrier above: re-arm it before this CTA's
+                    // records can let a peer start the next exchange
+                    if (lane == 0 && xchg > 0) dev::mbar_arrive_expect_tx(xb ? xbar0 : xbar1, xbytes);
+                    const uint2 kv = lane < W ? wkeys[lane] : make_uint2(0u, 0u);
+                    const unsigned cm = __reduce_max_sync(dev::kFull, kv.x);
+                    const unsigned cj = __reduce_max_sync(dev::kFull, kv.x == cm ? kv.y : 0u);
+                    const int jl = dev::checked((int)(0xffffffffu - cj) - c0, 0, T * P, a.status);
+                    // fault injection: the cluster's last CTA sends no records
+                    const bool send = !((a.stall & STALL_EXCHANGE) && rank == CS - 1);
+                    if (lane < CS && send) {
+                        const float wx = pts[3 * jl], wy = pts[3 * jl + 1], wz = pts[3 * jl + 2];
+                        const uint32_t slot = dev::smem_u32(&R[rank]);
+                        const uint32_t remote = dev::mapa(slot, (uint32_t)lane);
+                        const uint32_t rbar = dev::mapa(xbar, (uint32_t)lane);
+                        dev::st_async_v4(remote, rbar, cm, cj, __float_as_uint(wx),
+                                         __float_as_uint(wy));
+                        dev::st_async_v4(remote + 16, rbar, __float_as_uint(wz), 0u, 0u, 0u);
+                    }
                 }
             } else if (lane == 0) {
                 *reinterpret_cast<uint2*>(&R[w]) = make_uint2(m, jinv);
             }
 
             // 3. wait for every record of this exchange
-            bool xlate = false;
             if (CLUSTER) {
                 xlate = !dev::mbar_wait_bounded(xbar, xb ? xphase1 : xphase0, a.timeout_ns);
                 if (xlate) dev::record_status(a.status, DEV_TIMEOUT_EXCHANGE);
@@ -376,26 +403,16 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             if (CLUSTER) p = min(max(p, 0), n - 1);
             p = dev::checked(p, 0, n, a.status);
             if (CLUSTER) {
-                // the winner's record sits at (owner rank, owner warp)
-                const int r = (int)dev::SmallDiv((uint32_t)chunk)((uint32_t)p);
-                const int u = p - r * chunk;  // chunk-local index: thread u % T
-                const int e_star = dev::checked(
-                    r * W + ((u - (int)dev::SmallDiv((uint32_t)T)((uint32_t)u) * T) >> 5), 0, E,
-                    a.status);
-                qx = R[e_star].x;
-                qy = R[e_star].y;
-                qz = R[e_star].z;
+                // the winner's record is its owner CTA's
+                const int r = dev::checked((int)dev::SmallDiv((uint32_t)chunk)((uint32_t)p), 0, CS,
+                                           a.status);
+                qx = R[r].x;
+                qy = R[r].y;
+                qz = R[r].z;
             } else {
                 qx = pts[3 * p];
                 qy = pts[3 * p + 1];
                 qz = pts[3 * p + 2];
-            }
-            if (CLUSTER) {  // re-arm this buffer once every local reader is done
-                // a record that did not come: stop this item here (peers stop
-                // at their next exchange, which this CTA no longer feeds)
-                halted = __syncthreads_or(xlate) != 0;
-                if (halted) break;
-                if (tid == 0) dev::mbar_arrive_expect_tx(xbar, xbytes);
             }
             ++xchg;
             if (emitter) {
@@ -403,6 +420,8 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
                 if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
             }
         }
+        // the item's last exchange timed out: stop here
+        if (CLUSTER && !halted) halted = __syncthreads_or(xlate) != 0;
         if (emitter && !halted && lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
     }
     if (CLUSTER) dev::cluster_sync();  // no CTA leaves while a peer may still store to it
@@ -434,7 +453,11 @@ size_t variant_smem(const Variant& v) {
         return 16 * ((8 * (size_t)v.W + 15) / 16) + (size_t)v.W * (12 * 32 * (size_t)v.P + 16);
     if (v.kind == KIND_WIN)  // per warp: xyz (12 bytes a point + 16) and distances (4 bytes)
         return 16 * ((8 * (size_t)v.W + 15) / 16) + (size_t)v.W * (16 * 32 * (size_t)v.P + 16);
-    return 32 + 2 * (size_t)v.CS * v.W * sizeof(Rec) + 12 * 32 * (size_t)v.W * v.P + 16;
+    // records (one per CTA of a cluster, else one per warp), double-buffered;
+    // a cluster's CTAs also keep their warps' keys; then the points
+    const size_t E = v.CS > 1 ? (size_t)v.CS : (size_t)v.W;
+    return 32 + 2 * E * sizeof(Rec) + (v.CS > 1 ? 16 * ((8 * (size_t)v.W + 15) / 16) : 0) +
+           12 * 32 * (size_t)v.W * v.P + 16;
 }
 
 bool variant_supported(const Variant& v) {

@@ -6,10 +6,13 @@
 // whose host application owns every allocation, or a real-time loop that must
 // never take the allocator's locks or trigger an implicit device
 // synchronisation.  For them this entry point needs no context and allocates
-// nothing, neither device memory nor host heap memory.  Its only scratch,
+// no device memory (on the host heap only the first launch of each kernel
+// variant on a device records the attributes set for it).  Its only scratch,
 // the work-item table of the batched sector kernels plus a status word, is
 // the file-scope array below, which every GPU that loads the library holds
-// until the process exits.
+// until the process exits.  The table goes up from a static host copy in
+// pageable memory, so a call may wait for its stream, and a call on a
+// capturing stream is refused.
 //
 // The sector kernels are the existing ones (afps_warp.cu, afps_cta.cu),
 // launched without the persistent work queue: one warp, CTA or cluster per
@@ -30,7 +33,10 @@ constexpr int kMaxItems = AFPS_NOALLOC_MAX_ITEMS;
 constexpr size_t kHeader = 256;  // status word, padded to the table's alignment
 constexpr size_t kScratchBytes = kHeader + sizeof(afps::ItemDesc) * kMaxItems;
 constexpr int kMaxDevices = 64;
-constexpr int kMaxClasses = 64;
+// Launch classes: (variant, NPDU on/off) pairs na_variant can yield: 8 warp
+// variants, CTA variants of 3-32 warps and clusters of 2-16 CTAs (53), each
+// with and without NPDU, 106 in all.
+constexpr int kMaxClasses = 128;
 
 // The scratch: [status word | padding to 256 B | kMaxItems work items].
 // In host code `g_noalloc_scratch` is a host-side stand-in, not a device
@@ -135,6 +141,16 @@ extern "C" int afps_sample_batched_noalloc(const float* d_xyz, const int64_t* h_
     if (reinterpret_cast<uintptr_t>(d_xyz) % 4 || reinterpret_cast<uintptr_t>(d_out) % 4 ||
         h_pt_off[0] < 0 || h_out_off[0] < 0)
         return AFPS_ERR_INVALID_ARG;
+    // not under stream capture: the table's upload from the static host copy
+    // would be recorded, and replays would read whatever a later call left there
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return AFPS_ERR_INVALID_ARG;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return AFPS_ERR_INVALID_ARG;
+    }
 
     // pass 1: validate, size the item table, form launch classes
     NaClass cls[kMaxClasses];
@@ -220,7 +236,7 @@ extern "C" int afps_sample_batched_noalloc(const float* d_xyz, const int64_t* h_
         a.counter = nullptr;
         a.status = reinterpret_cast<int*>(base);
         a.timeout_ns = 2000000000ull;
-        a.stall_copy = 0;
+        a.stall = 0;
         a.npdu_skip = cls[c].v.skip ? 1u : 0u;
         const int grid = cls[c].v.kind == afps::KIND_WARP
                              ? (cls[c].count + cls[c].v.W - 1) / cls[c].v.W

@@ -43,18 +43,23 @@ __device__ __forceinline__ void set_row(unsigned (&rmb)[R], unsigned (&rmi)[R], 
         }
 }
 
-// Every distance at 1e10 (points) or +0 (the padding of the last row, which
-// loses every tie); every row's maximum is 1e10 at its first point.
+// Every row's maximum is 1e10 at its first point; a slot past the last row
+// holds +0 at no index and loses every tie.
 template <int R>
-__device__ __forceinline__ void reset_rows(float* Ds, int n, int rows, unsigned (&rmb)[R],
-                                           unsigned (&rmi)[R], int lane) {
-    for (int j = lane; j < 32 * rows; j += 32) Ds[j] = j < n ? 1e10f : 0.f;
+__device__ __forceinline__ void reset_slots(int rows, unsigned (&rmb)[R], unsigned (&rmi)[R],
+                                            int lane) {
 #pragma unroll
     for (int s = 0; s < R; ++s) {
         const int r = lane + 32 * s;
         rmb[s] = r < rows ? __float_as_uint(1e10f) : 0u;
-        rmi[s] = r < rows ? (unsigned)(32 * r) : 0xffffffffu;  // no row: loses every tie
+        rmi[s] = r < rows ? (unsigned)(32 * r) : 0xffffffffu;
     }
+}
+
+// Every distance at 1e10 (points) or +0 (the padding of the last row, which
+// loses every tie).
+__device__ __forceinline__ void reset_dist(float* Ds, int n, int rows, int lane) {
+    for (int j = lane; j < 32 * rows; j += 32) Ds[j] = j < n ? 1e10f : 0.f;
 }
 
 // The lowest-index maximum of row r from its 32 distance bits (one per lane).
@@ -128,8 +133,7 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
             if (!halted) {
                 const int rows = (n + 31) >> 5;
                 unsigned rmb[R], rmi[R];  // cached row maxima: bits, lowest index
-                reset_rows<R>(Ds, n, rows, rmb, rmi, lane);
-
+                reset_slots<R>(rows, rmb, rmi, lane);
                 int32_t* out = a.out + d.dst;
                 const int c = dev::checked(d.c, 1, n + 1, a.status);
                 const int kl = d.kl;
@@ -142,13 +146,17 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                 int obuf = lane == 0 ? d.lo + p : 0;
                 if (lane == 0 && !ROWS) out[0] = d.lo + p;
                 int t0 = 1;
+                bool fresh = true;  // distances still to be set to 1e10
                 if (!full_first && p <= kl && kl <= kr) {
                     // Stride phase (see afps_warp.cu): samples p, p + q, ...
                     // (q = kr + 1) until a window reaches the sector's end;
-                    // their windows are applied at once (a point lies in at
-                    // most two of them), valid if every windowed distance is
-                    // below 1e10.  Rows are visited in order, so each row's
-                    // maximum comes from registers on the way.
+                    // their windows are applied at once, valid if every
+                    // windowed distance is below 1e10.  Point j lies in window
+                    // u = floor((j + kl - p) / q) (the last one starting at or
+                    // before it, which always reaches it since kl <= kr) and
+                    // possibly in window u - 1.  Every distance, padding
+                    // included, is written here, and rows are visited in
+                    // order, so each row's maximum comes from registers.
                     const int q = kr + 1;
                     const int x = n - 1 - kr - p;
                     const dev::SmallDiv divq((uint32_t)q);
@@ -162,16 +170,16 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                         if (j < n) {
                             v = 1e10f;
                             const float px = pts[3 * j], py = pts[3 * j + 1], pz = pts[3 * j + 2];
-                            const int y = j - kr - p;
-                            // unsigned divisions: both operands are >= 0 (p <= kl)
-                            const int tlo = y <= 0 ? 0 : (int)divq((uint32_t)(y + q - 1));
-                            const int thi = min(tw - 1, (int)divq((uint32_t)(j + kl - p)));
+                            // unsigned division: j + kl - p >= 0 (p <= kl)
+                            const int u = (int)divq((uint32_t)(j + kl - p));
 #pragma unroll
-                            for (int u = 0; u < 2; ++u) {
-                                if (tlo + u <= thi) {
-                                    const int sj = dev::checked(p + (tlo + u) * q, 0, n, a.status);
-                                    const float dd = dev::sqdist(px, py, pz, pts[3 * sj],
-                                                                 pts[3 * sj + 1], pts[3 * sj + 2]);
+                            for (int e = 0; e < 2; ++e) {
+                                const int tt = u - e;  // windows u and u - 1
+                                const int sj = p + tt * q;
+                                if (tt >= 0 && tt < tw && j <= sj + kr) {
+                                    const int sc = dev::checked(sj, 0, n, a.status);
+                                    const float dd = dev::sqdist(px, py, pz, pts[3 * sc],
+                                                                 pts[3 * sc + 1], pts[3 * sc + 2]);
                                     ok = ok && dd < 1e10f;
                                     v = fminf(v, dd);
                                 }
@@ -182,6 +190,7 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                         row_max(__float_as_uint(v), lane, m, l);
                         set_row<R>(rmb, rmi, i, m, (unsigned)(32 * i) + l, lane);
                     }
+                    fresh = false;
                     if (__all_sync(dev::kFull, ok)) {
                         if (ROWS) {
                             for (int r0 = 0; r0 + 32 <= tn; r0 += 32)
@@ -193,18 +202,21 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                         p += (tn - 1) * q;
                         t0 = tn;  // re-applying the last window is a no-op
                     } else {
-                        __syncwarp();
-                        reset_rows<R>(Ds, n, rows, rmb, rmi, lane);
+                        fresh = true;
+                        reset_slots<R>(rows, rmb, rmi, lane);
                     }
+                }
+                if (fresh) {
+                    __syncwarp();
+                    reset_dist(Ds, n, rows, lane);
                 }
                 __syncwarp();
 
-                for (int t = t0; t < c; ++t) {
-                    // window of the last sample p (the whole sector for the
-                    // first update of the full-first-pass reading)
-                    const bool whole = full_first && t == 1;
-                    const int wl = whole ? 0 : max(p - kl, 0);
-                    const int wh = whole ? n - 1 : min(p + kr, n - 1);
+                // General round: the window [wl, wh] of the last sample p (the
+                // whole sector for the first update of the full-first-pass
+                // reading, or a window wider than a row): one lane per point,
+                // every touched row's maximum recomputed.
+                auto round_any = [&](int t, int wl, int wh) {
                     const float qx = pts[3 * p], qy = pts[3 * p + 1], qz = pts[3 * p + 2];
                     for (int j = wl + lane; j <= wh; j += 32) {
                         const float dd =
@@ -244,6 +256,68 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                     } else if (lane == 0) {
                         out[t] = d.lo + p;
                     }
+                };
+                int t = t0;
+                if (full_first && t < c) round_any(t++, 0, n - 1);
+                if (kl + kr <= 31) {
+                    // Narrow window (at most 32 points): lane i updates point
+                    // wl + i; the window touches row r0 and perhaps r1 = r0 + 1.
+                    // The maxima of the touched rows (m0, m1) and of the cached
+                    // rows it missed (mk) are reduced side by side; the sample is
+                    // the lowest index holding the largest of the three.  The
+                    // touched rows' lowest-index lanes, needed only by the next
+                    // rounds' cache, come after it.
+                    const int nm1 = n - 1;
+#pragma unroll 1
+                    for (; t < c; ++t) {
+                        const int wl = max(p - kl, 0);
+                        const int wh = min(p + kr, nm1);
+                        const int j = wl + lane;
+                        const float qx = pts[3 * p], qy = pts[3 * p + 1], qz = pts[3 * p + 2];
+                        if (j <= wh) {
+                            const float dd = dev::sqdist(pts[3 * j], pts[3 * j + 1],
+                                                         pts[3 * j + 2], qx, qy, qz);
+                            Ds[j] = fminf(Ds[j], dd);
+                        }
+                        __syncwarp();
+                        const int r0 = wl >> 5, r1 = wh >> 5;
+                        const unsigned j0 = (unsigned)(32 * r0 + lane);
+                        const unsigned j1 = (unsigned)(32 * r1 + lane);
+                        const unsigned b0 = __float_as_uint(Ds[j0]);
+                        const unsigned b1 = __float_as_uint(Ds[j1]);  // = b0 with one row
+                        unsigned kb = 0u, ki = 0xffffffffu;  // best cached row it missed
+#pragma unroll
+                        for (int s = 0; s < R; ++s) {
+                            const int r = lane + 32 * s;
+                            const bool take = r != r0 && r != r1 && (rmb[s] > kb || ki == 0xffffffffu);
+                            kb = take ? rmb[s] : kb;
+                            ki = take ? rmi[s] : ki;
+                        }
+                        const unsigned m0 = __reduce_max_sync(dev::kFull, b0);
+                        const unsigned m1 = __reduce_max_sync(dev::kFull, b1);
+                        const unsigned mk = __reduce_max_sync(dev::kFull, kb);
+                        const unsigned mx = max(max(m0, m1), mk);
+                        unsigned cand = b1 == mx ? j1 : 0xffffffffu;
+                        cand = b0 == mx ? j0 : cand;
+                        cand = kb == mx && ki < cand ? ki : cand;
+                        p = dev::checked((int)__reduce_min_sync(dev::kFull, cand), 0, n, a.status);
+                        const unsigned l0 = __reduce_min_sync(dev::kFull, b0 == m0 ? (unsigned)lane : 32u);
+                        set_row<R>(rmb, rmi, r0, m0, (unsigned)(32 * r0) + l0, lane);
+                        if (r1 != r0) {
+                            const unsigned l1 =
+                                __reduce_min_sync(dev::kFull, b1 == m1 ? (unsigned)lane : 32u);
+                            set_row<R>(rmb, rmi, r1, m1, (unsigned)(32 * r1) + l1, lane);
+                        }
+                        if (ROWS) {
+                            obuf = lane == (t & 31) ? d.lo + p : obuf;
+                            if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
+                        } else if (lane == 0) {
+                            out[t] = d.lo + p;
+                        }
+                    }
+                } else {
+#pragma unroll 1
+                    for (; t < c; ++t) round_any(t, max(p - kl, 0), min(p + kr, n - 1));
                 }
                 if (ROWS && lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
             }

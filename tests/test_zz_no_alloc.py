@@ -65,3 +65,40 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     torch.cuda.synchronize()
     assert rc == B.AFPS_ERR_SCRATCH_TOO_SMALL
     assert int((out != -1).sum()) == 0  # nothing launched, nothing written
+
+
+def test_noalloc_refuses_stream_capture():
+    """On a stream that is capturing a CUDA graph the call does nothing and
+    returns AFPS_ERR_INVALID_ARG (a captured upload would replay from the
+    static host copy after later calls had overwritten it); the capture
+    itself is unharmed and the next call outside it works."""
+    build_mod.build()
+    L = B.load()
+    clouds = synth.object_batch(2, 4, 2048)
+    xyz, off = synth.pack(clouds)
+    x = torch.from_numpy(xyz).cuda()
+    ba = B.BatchArgs(off, 512, 32, 16, 0)
+    out = torch.full((ba.total_out,), -1, dtype=torch.int32, device="cuda")
+    y = torch.zeros(16, device="cuda")
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        g.capture_begin()
+        rc = L.afps_sample_batched_noalloc(x.data_ptr(), *ba.args(), out.data_ptr(),
+                                           side.cuda_stream)
+        y.add_(1.0)  # the capture records this
+        g.capture_end()
+    assert rc == B.AFPS_ERR_INVALID_ARG
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(y[0]) == 1.0 and int((out != -1).sum()) == 0
+    rc = L.afps_sample_batched_noalloc(x.data_ptr(), *ba.args(), out.data_ptr(),
+                                       torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert rc == B.AFPS_OK
+    S = B.Sampler(0)
+    try:
+        assert np.array_equal(out.cpu().numpy(), _existing(S, x, ba))
+    finally:
+        S.close()
