@@ -11,6 +11,8 @@ Cases (inputs from `synth`; kernel variants from the planner or the cache):
   headline     32 object clouds x 2048 points, C = 512, NPDU-AFPS M = 32, k = 16 (batched)
   fps2048      the same batch, plain FPS (M = 1)
   cluster32k   one 32768-point slab cloud, C = 8192, plain FPS (one thread-block cluster)
+  clusters     plain FPS on slab clouds of 8K / 16K / 32K points, C = N/4, every cluster shape
+               (P, W, CS) the autotuner tries, forced one by one; prints each one's time
   npdu32k      the same cloud, NPDU-AFPS M = 32, k = 16
   ragged       256 clouds of 2K-32K points, C = N/4, sectors of ~256 points, k = 8 / 16 (persistent)
   chain        one LiDAR-like frame, levels 16384 -> 4096 -> 1024 -> 256, M = 32, k = 16
@@ -28,8 +30,8 @@ import torch
 
 from . import afps, build, synth
 
-CASES = ("headline", "fps2048", "cluster32k", "npdu32k", "ragged", "chain", "sort", "group",
-         "knn", "coverage")
+CASES = ("headline", "fps2048", "cluster32k", "clusters", "npdu32k", "ragged", "chain", "sort",
+         "group", "knn", "coverage")
 
 
 def run(case: str, reps: int, tune_cache: str | None = None) -> None:
@@ -57,6 +59,32 @@ def run(case: str, reps: int, tune_cache: str | None = None) -> None:
             s.sample_batched(x, ba, out=out)
         if case != "ragged":
             print("variant:", s.describe_plan(-(-2048 // M), -(-C // M), k, 32 * M))
+    elif case == "clusters":
+        import tempfile
+        for N in (8192, 16384, 32768):
+            x = torch.from_numpy(synth.slab_cloud(2, N)).to(dev)
+            C = N // 4
+            for P in (4, 8, 16):
+                for W in (4, 8, 16, 32):
+                    CS = -(-N // (32 * W * P))
+                    if CS < 2 or CS > 16:
+                        continue
+                    path = os.path.join(tempfile.gettempdir(), "afps_profile_cluster.txt")
+                    with open(path, "w") as f:
+                        f.write(f"full:n{N}:c{C}:i1 1 {P} {W} {CS} 0 0\n")
+                    sc = afps.Sampler(0, tune_cache=path)
+                    out = sc.sample(x, C, 1, 0, 0)
+                    sc.sync()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(reps):
+                        sc.sample(x, C, 1, 0, 0, out=out)
+                    e1.record()
+                    sc.sync()
+                    ms = e0.elapsed_time(e1) / reps
+                    print(f"N={N} {sc.describe_plan(N, C, 0, 1):28s} {ms:8.3f} ms "
+                          f"{ms * 1e6 / C:7.1f} ns/iteration", flush=True)
+                    sc.close()
     elif case in ("cluster32k", "npdu32k"):
         x = torch.from_numpy(synth.slab_cloud(2, 32768)).to(dev)
         M, k = (1, 0) if case == "cluster32k" else (32, 16)
