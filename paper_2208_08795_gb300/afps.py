@@ -556,15 +556,24 @@ def afps_server_destroy(srv) -> None:
 
 
 class ServerResult:
-    """One finished request: per-level frame indices (copied) and times."""
+    """One finished request: per-level frame indices and times.  With
+    copy=False the indices are a view of the runtime's page-locked result
+    slot, valid until the next poll."""
 
-    def __init__(self, r: afps_server_result):
+    def __init__(self, r: afps_server_result, copy: bool = True):
         self.tag = int(r.tag)
         self.status = int(r.status)
-        counts = [int(r.count[l]) for l in range(r.n_levels)]
-        flat = np.ctypeslib.as_array(r.indices, shape=(sum(counts),)).copy()
-        self.levels = np.split(flat, np.cumsum(counts)[:-1])
+        self._counts = list(r.count)[:r.n_levels]
+        total = sum(self._counts)
+        addr = ctypes.cast(r.indices, ctypes.c_void_p).value
+        flat = np.frombuffer((ctypes.c_int32 * total).from_address(addr), dtype=np.int32)
+        self.indices = flat.copy() if copy else flat
         self.submit_ms, self.admit_ms, self.done_ms = r.submit_ms, r.admit_ms, r.done_ms
+
+    @property
+    def levels(self):
+        """The frame indices of each level's samples, in emission order."""
+        return np.split(self.indices, np.cumsum(self._counts)[:-1])
 
 
 class Server:
@@ -618,11 +627,13 @@ class Server:
             raise AfpsError(rc, afps_last_error(self.sampler.ctx))
         return rc
 
-    def poll(self):
+    def poll(self, copy: bool = True):
+        """Finished requests.  copy=False: their indices are views of the
+        runtime's result slots, valid until the next poll (no copy)."""
         n = afps_server_poll(self.srv, self._buf, len(self._buf))
         if n < 0:
             raise AfpsError(n, "afps_server_poll failed")
-        return [ServerResult(self._buf[i]) for i in range(n)]
+        return [ServerResult(self._buf[i], copy) for i in range(n)]
 
     def stats(self):
         q, f, u = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

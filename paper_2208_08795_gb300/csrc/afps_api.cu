@@ -1283,7 +1283,11 @@ int afps_sort_by_key(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const fl
     if (B < 1 || !h_pt_off || !d_xyz || !d_xyz_sorted || !d_perm || key < AFPS_KEY_X ||
         key > AFPS_KEY_AZIMUTH || h_pt_off[0] < 0)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "afps_sort_by_key: bad argument");
-    std::vector<afps::SortDesc> descs((size_t)B);
+    // small clouds: one CTA each (global scratch); large ones: one cluster
+    // each, held in distributed shared memory
+    std::vector<afps::SortDesc> small, large;
+    int64_t small_points = 0;
+    int32_t large_max = 0;
     for (int32_t b = 0; b < B; ++b) {
         const int64_t n = h_pt_off[b + 1] - h_pt_off[b];
         if (n < 0 || n > INT32_MAX) {
@@ -1291,25 +1295,44 @@ int afps_sort_by_key(afps_ctx* ctx, int32_t B, const int64_t* h_pt_off, const fl
             os << "afps_sort_by_key: cloud " << b << " has " << n << " points";
             return fail(ctx, AFPS_ERR_INVALID_ARG, os.str());
         }
-        descs[b] = afps::SortDesc{h_pt_off[b], (int32_t)n, 0};
+        const afps::SortDesc sd{h_pt_off[b], (int32_t)n, 0};
+        if (n > afps::kSortClusterMin && n <= afps::sort_cluster_capacity()) {
+            large.push_back(sd);
+            large_max = std::max(large_max, (int32_t)n);
+        } else {
+            small.push_back(sd);
+            small_points = std::max(small_points, h_pt_off[b + 1]);
+        }
     }
     DeviceGuard guard(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t total = h_pt_off[B];
-    // scratch: keys and indices, twice (ping-pong); earlier users are ordered
-    // before the reallocation by cudaFree's device synchronisation
-    AFPS_CUDA(ctx, grow(ctx, ctx->sort_scratch, (size_t)total * 16 + 16));
+    // scratch of the small clouds' sort: keys and indices, twice (ping-pong),
+    // indexed by point; earlier users are ordered before a reallocation by
+    // cudaFree's device synchronisation
+    if (!small.empty()) AFPS_CUDA(ctx, grow(ctx, ctx->sort_scratch, (size_t)small_points * 16 + 16));
+    std::vector<afps::SortDesc> descs(small);
+    descs.insert(descs.end(), large.begin(), large.end());
     int rc = upload(ctx, ctx->items, descs.data(), descs.size() * sizeof(afps::SortDesc), st);
     if (rc != AFPS_OK) return rc;
-    unsigned char* base = static_cast<unsigned char*>(ctx->sort_scratch.p);
-    uint32_t* keys_a = reinterpret_cast<uint32_t*>(base);
-    int32_t* idx_a = reinterpret_cast<int32_t*>(base + 4 * total);
-    uint32_t* keys_b = reinterpret_cast<uint32_t*>(base + 8 * total);
-    int32_t* idx_b = reinterpret_cast<int32_t*>(base + 12 * total);
-    cudaError_t e = afps::launch_sort(static_cast<const afps::SortDesc*>(ctx->items.p), B, d_xyz,
-                                      key, keys_a, idx_a, keys_b, idx_b, d_xyz_sorted, d_perm, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "sort launch");
-    ctx->launches += 1;
+    const afps::SortDesc* d_descs = static_cast<const afps::SortDesc*>(ctx->items.p);
+    if (!small.empty()) {
+        const int64_t total = small_points;
+        unsigned char* base = static_cast<unsigned char*>(ctx->sort_scratch.p);
+        uint32_t* keys_a = reinterpret_cast<uint32_t*>(base);
+        int32_t* idx_a = reinterpret_cast<int32_t*>(base + 4 * total);
+        uint32_t* keys_b = reinterpret_cast<uint32_t*>(base + 8 * total);
+        int32_t* idx_b = reinterpret_cast<int32_t*>(base + 12 * total);
+        cudaError_t e = afps::launch_sort(d_descs, (int32_t)small.size(), d_xyz, key, keys_a,
+                                          idx_a, keys_b, idx_b, d_xyz_sorted, d_perm, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "sort launch");
+        ctx->launches += 1;
+    }
+    if (!large.empty()) {
+        cudaError_t e = afps::launch_sort_cluster(d_descs + small.size(), (int32_t)large.size(),
+                                                  large_max, d_xyz, key, d_xyz_sorted, d_perm, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster sort launch");
+        ctx->launches += 1;
+    }
     AFPS_CUDA(ctx, cudaEventRecord(ctx->ev_done, st));
     return AFPS_OK;
 }

@@ -139,6 +139,21 @@ cudaError_t launch_gather(const GatherDesc* d_descs, int32_t B, int32_t max_n,
                           cudaStream_t stream);
 constexpr int32_t kGatherMaxPoints = 65536;
 
+// Frames admitted by a serving step: from page-locked host memory (read by
+// the kernel over the C2C link) into the device arena, one launch for all.
+struct FrameCopy {
+    const void* src;  // device-visible address of the host frame
+    void* dst;        // arena address
+    int64_t bytes;    // a multiple of 4
+};
+constexpr int kFrameCopyMax = 256;  // frames per launch (kernel-parameter batch)
+struct FrameCopyBatch {
+    int32_t n;
+    int32_t pad;
+    FrameCopy c[kFrameCopyMax];
+};
+cudaError_t launch_frame_copy(const FrameCopyBatch& batch, int64_t max_bytes, cudaStream_t stream);
+
 // Coverage radius (afps_coverage_radius).
 struct CoverageDesc {
     int64_t pt_off;   // first point of the cloud
@@ -174,6 +189,14 @@ struct SortDesc {
 cudaError_t launch_sort(const SortDesc* d_descs, int32_t B, const float* xyz, int key,
                         uint32_t* keys_a, int32_t* idx_a, uint32_t* keys_b, int32_t* idx_b,
                         float* xyz_out, int32_t* perm, cudaStream_t stream);
+// Large clouds: one thread-block cluster per cloud, the cloud in distributed
+// shared memory (no scratch); clouds of up to sort_cluster_capacity() points.
+cudaError_t launch_sort_cluster(const SortDesc* d_descs, int32_t B, int32_t max_n,
+                                const float* xyz, int key, float* xyz_out, int32_t* perm,
+                                cudaStream_t stream);
+int sort_cluster_capacity();
+// Clouds above this size go to the cluster sort (when they fit it).
+constexpr int32_t kSortClusterMin = 4096;
 
 }  // namespace afps
 

@@ -103,7 +103,9 @@ class ReplicaRouter:
     def step(self) -> int:
         return sum(r.step() for r in self.replicas)
 
-    def poll(self):
+    def poll(self, copy: bool = True):
+        """Finished requests of every replica (always copied: a replica's
+        result slots are reused at its next poll)."""
         out = []
         for i, r in enumerate(self.replicas):
             off = self.offset[i]
@@ -198,8 +200,8 @@ class RemoteReplica:
             self._results.append(_Result(tag, status, levels, sub, sub, now))
         return advanced
 
-    def poll(self):
-        out, self._results = self._results, []
+    def poll(self, copy: bool = True):
+        out, self._results = self._results, []  # received by message: copies already
         return out
 
     def stats(self):

@@ -40,7 +40,7 @@ def poisson_run(server, frames, rate_hz: float, n_requests: int, seed: int = 0,
         if a > 0:
             steps += 1
             advanced += a
-        for r in server.poll():
+        for r in server.poll(copy=keep_results):  # without a copy: views valid until the next poll
             done[r.tag] = r
         if a == 0 and i < n_requests and not server.stats()[1]:
             # idle: wait for the next arrival

@@ -58,7 +58,7 @@ class FakeServer:
         self.steps += 1
         return finished * len(LEVELS) + len(self.running)
 
-    def poll(self):
+    def poll(self, copy=True):
         out, self.done = self.done, []
         return out
 
