@@ -755,6 +755,13 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     fps_steps, fps_warm = max(3, min(args.steps, 5)), 3
     ms_fps = arm(1, 0, fps_steps, fps_warm)
     ms_full = arm(Ms, 0, max(3, min(args.steps, 20)), 3)
+    # the same windows under the full-first-pass reading (Sec. III-C): every
+    # round after the first updates a window, none is decided by the stride
+    # phase of the literal reading; isolated steps, as p50/p99
+    ba_ff = A.BatchArgs(off, Cs, Ms, ks, 0, method=A.AFPS_METHOD_FULL_FIRST_PASS)
+    out_ff = torch.empty(ba_ff.total_out, dtype=torch.int32, device=dev)
+    lat_ff, _ = time_device(sampler, x, ba_ff, out_ff, max(3, min(args.steps, 20)), 3, flush)
+    iso_ff = max_over_ranks(float(np.mean(lat_ff)), world, dev)
 
     # end to end through host buffers: pipelined calls (the throughput) and
     # one synchronous call at a time (the latency of a call)
@@ -838,6 +845,10 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         "afps_no_npdu": {"value": n_clouds * world / (ms_full / 1e3), "unit": UNIT,
                          "ms_per_step": ms_full, "speedup_npdu_afps": ms_full / ms_step,
                          "what": "AFPS with the same M and no NPDU window"},
+        "npdu_no_stride": {"isolated_step_ms": iso_ff, "vs_isolated_headline": iso_ff / iso_ms,
+                           "what": "the same windows under the full-first-pass reading: no round "
+                                   "is decided by the stride phase of the literal reading; "
+                                   "isolated steps after an L2 flush, as p50/p99"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"

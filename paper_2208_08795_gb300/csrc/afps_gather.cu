@@ -12,6 +12,9 @@
 // destinations in parallel.  Counting (not flags) keeps repeated indices,
 // should a degenerate cloud produce any.  The output xyz must not overlap the
 // input.
+#include <mutex>
+#include <set>
+
 #include "afps_device.cuh"
 
 namespace afps {
@@ -132,15 +135,61 @@ __global__ void __launch_bounds__(1024) afps_gather_kernel(
     }
 }
 
+// Frame copies of a serving step: grid.y = frame, grid.x = 16 KB chunks of
+// it; 16-byte vectors where both ends allow, else 4-byte words.  The
+// descriptors travel in the kernel's parameters, so a step's admission is
+// one launch instead of a copy call per frame.
+__global__ void __launch_bounds__(256) afps_frame_copy_kernel(const __grid_constant__ FrameCopyBatch b) {
+    const int f = blockIdx.y;
+    if (f >= b.n) return;
+    const FrameCopy c = b.c[f];
+    constexpr int64_t kChunk = 16384;
+    const int64_t lo = (int64_t)blockIdx.x * kChunk;
+    if (lo >= c.bytes) return;
+    const int64_t hi = min(c.bytes, lo + kChunk);
+    const char* src = static_cast<const char*>(c.src);
+    char* dst = static_cast<char*>(c.dst);
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+    if (vec) {
+        const int64_t v_hi = lo + ((hi - lo) & ~int64_t(15));
+        for (int64_t o = lo + 16 * threadIdx.x; o < v_hi; o += 16 * blockDim.x)
+            *reinterpret_cast<uint4*>(dst + o) = *reinterpret_cast<const uint4*>(src + o);
+        for (int64_t o = v_hi + 4 * threadIdx.x; o < hi; o += 4 * blockDim.x)
+            *reinterpret_cast<uint32_t*>(dst + o) = *reinterpret_cast<const uint32_t*>(src + o);
+    } else {
+        for (int64_t o = lo + 4 * threadIdx.x; o < hi; o += 4 * blockDim.x)
+            *reinterpret_cast<uint32_t*>(dst + o) = *reinterpret_cast<const uint32_t*>(src + o);
+    }
+}
+
+cudaError_t launch_frame_copy(const FrameCopyBatch& batch, int64_t max_bytes, cudaStream_t stream) {
+    if (batch.n < 1) return cudaSuccess;
+    const dim3 grid((unsigned)((max_bytes + 16383) / 16384), (unsigned)batch.n, 1);
+    afps_frame_copy_kernel<<<grid, 256, 0, stream>>>(batch);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const GatherDesc* d_descs, int32_t B, int32_t max_n,
                           const float* in_xyz, const int32_t* in_frame, const int32_t* sel,
                           float* out_xyz, int32_t* out_frame, int32_t* sel_frame,
                           cudaStream_t stream) {
     if (B < 1) return cudaSuccess;
     const size_t smem = 4 * (size_t)((max_n + 1) / 2) + 16;
-    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(afps_gather_kernel),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    {  // the largest dynamic shared memory any cloud can need, once per device
+        static std::mutex mu;
+        static std::set<int> done;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lock(mu);
+        if (!done.count(dev)) {
+            e = cudaFuncSetAttribute(reinterpret_cast<const void*>(afps_gather_kernel),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(4 * (size_t)((kGatherMaxPoints + 1) / 2) + 16));
+            if (e != cudaSuccess) return e;
+            done.insert(dev);
+        }
+    }
     afps_gather_kernel<<<B, 1024, smem, stream>>>(d_descs, in_xyz, in_frame, sel, out_xyz,
                                                   out_frame, sel_frame);
     return cudaGetLastError();

@@ -4,9 +4,14 @@
 // Each request owns one arena block laid out as
 //   xyz (points, 12 B each):  frame N | cloud 1: C0 | ... | cloud L: C_{L-1}
 //   int32:                    out_0: C0 | ... | out_{L-1} | frame index of
-//                             clouds 1..L-1 | results: C0 + ... + C_{L-1}
+//                             clouds 1..L-1
 // where cloud l+1 is level l's samples in ascending frame index (built by the
 // gather kernel) and out_l the level's sample indices relative to cloud l.
+// Its results (every level's samples as frame indices) are written by the
+// gather kernel straight into its page-locked result slot, over the C2C link,
+// and its frame comes in by one copy kernel per step that reads the
+// page-locked frames of every admitted request: a step costs a few launches,
+// not a copy call per request.
 // Blocks start on 48-byte boundaries so that every xyz part starts on a point
 // boundary of the arena (point offsets = byte offsets / 12) and every int32
 // part on a 4-byte one.
@@ -89,6 +94,7 @@ struct Request {
     int64_t N = 0;
     Block staged;              // the frame in the page-locked pool until admitted
     const float* borrowed = nullptr;  // or the caller's page-locked frame (submit_pinned)
+    const void* src_dev = nullptr;    // the frame's device-visible address (either case)
     State state = QUEUED;
     int level = 0;             // next level to sample
     Block block;
@@ -96,7 +102,6 @@ struct Request {
     int64_t xyz_pt[AFPS_SERVER_MAX_LEVELS + 1];  // cloud l, in points from the arena base
     int64_t out_el[AFPS_SERVER_MAX_LEVELS];      // out_l, in int32 elements
     int64_t fidx_el[AFPS_SERVER_MAX_LEVELS + 1]; // frame index of cloud l (l >= 1)
-    int64_t res_el = 0;                          // results, all levels
     cudaEvent_t done_ev = nullptr;
     double t_submit = 0, t_admit = 0, t_done = 0;
 };
@@ -119,6 +124,8 @@ struct afps_server {
     // step's event: they are free once the event completes
     std::deque<std::pair<cudaEvent_t, std::vector<Block>>> pool_pending;
     int32_t* pinned = nullptr;  // max_inflight result slots
+    int32_t* pinned_dev = nullptr;  // their device-visible address
+    unsigned char* pool_dev = nullptr;  // device-visible address of the staging pool
     std::vector<int> free_slots;
     std::deque<std::unique_ptr<Request>> queue;
     std::vector<std::unique_ptr<Request>> active;  // ACTIVE or COMPLETING
@@ -140,7 +147,6 @@ int64_t footprint(const afps_server* s, int64_t N) {
     for (int l = 0; l < s->cfg.n_levels; ++l) {
         pts += s->levels[l];   // cloud l+1
         ints += s->levels[l];  // out_l
-        ints += s->levels[l];  // results of level l
         if (l + 1 < s->cfg.n_levels) ints += s->levels[l];  // frame index of cloud l+1
     }
     return 12 * pts + 4 * ints + kBlockAlign;
@@ -212,7 +218,6 @@ bool admit_one(afps_server* s, Request& r) {
         r.fidx_el[l] = el;
         el += s->levels[l - 1];
     }
-    r.res_el = el;
     r.state = ACTIVE;
     r.level = 0;
     r.t_admit = s->now();
@@ -271,6 +276,15 @@ int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_confi
         return AFPS_ERR_NO_MEMORY;
     }
     s->pinned = static_cast<int32_t*>(h);
+    void* hd = nullptr;
+    if (cudaHostGetDevicePointer(&hd, h, 0) != cudaSuccess || !hd) {
+        cudaGetLastError();
+        cudaFreeHost(h);
+        cudaFree(p);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        return AFPS_ERR_CUDA;  // page-locked memory not mapped into the device
+    }
+    s->pinned_dev = static_cast<int32_t*>(hd);
     for (int i = s->cfg.max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
     if (s->cfg.host_pool_bytes <= 0) s->cfg.host_pool_bytes = 64ll << 20;
     void* hp = nullptr;
@@ -282,6 +296,16 @@ int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_confi
         return AFPS_ERR_NO_MEMORY;
     }
     s->pool_base = static_cast<unsigned char*>(hp);
+    void* hpd = nullptr;
+    if (cudaHostGetDevicePointer(&hpd, hp, 0) != cudaSuccess || !hpd) {
+        cudaGetLastError();
+        cudaFreeHost(hp);
+        cudaFreeHost(h);
+        cudaFree(p);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        return AFPS_ERR_CUDA;
+    }
+    s->pool_dev = static_cast<unsigned char*>(hpd);
     s->pool.reset(new Arena(s->cfg.host_pool_bytes / kBlockAlign * kBlockAlign));
     // the largest step table: every slot's request at its widest level
     int32_t widest = 1;
@@ -322,6 +346,7 @@ int afps_server_submit(afps_server* s, const float* h_xyz, int64_t N, uint64_t t
     r->tag = tag;
     r->N = N;
     r->staged = staged;
+    r->src_dev = s->pool_dev + staged.off;
     memcpy(s->pool_base + staged.off, h_xyz, (size_t)(12 * N));
     r->t_submit = s->now();
     s->queue.push_back(std::move(r));
@@ -333,7 +358,8 @@ int afps_server_submit_pinned(afps_server* s, const float* h_xyz, int64_t N, uin
     if (!s || !h_xyz || N < s->levels[0] || N > 65536) return AFPS_ERR_INVALID_ARG;
     if (footprint(s, N) > s->cfg.hbm_budget_bytes) return AFPS_ERR_INVALID_ARG;
     cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, h_xyz) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+    if (cudaPointerGetAttributes(&at, h_xyz) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+        !at.devicePointer || reinterpret_cast<uintptr_t>(at.devicePointer) % 4) {
         cudaGetLastError();
         return AFPS_ERR_INVALID_ARG;
     }
@@ -343,6 +369,7 @@ int afps_server_submit_pinned(afps_server* s, const float* h_xyz, int64_t N, uin
     r->tag = tag;
     r->N = N;
     r->borrowed = h_xyz;
+    r->src_dev = at.devicePointer;
     r->t_submit = s->now();
     s->queue.push_back(std::move(r));
     return AFPS_OK;
@@ -399,13 +426,21 @@ int afps_server_step(afps_server* s) {
     float* xyz = reinterpret_cast<float*>(s->arena_base);
     int32_t* ints = reinterpret_cast<int32_t*>(s->arena_base);
     std::vector<Block> copied;  // staging blocks read by this step's copies
+    afps::FrameCopyBatch batch;
+    batch.n = 0;
+    int64_t batch_max = 0;
+    auto flush = [&]() -> bool {
+        const bool ok = afps::launch_frame_copy(batch, batch_max, s->stream) == cudaSuccess;
+        batch.n = 0;
+        batch_max = 0;
+        return ok;
+    };
     while (!s->queue.empty() && (int)s->active.size() < s->cfg.max_inflight) {
         Request& r = *s->queue.front();
         if (!admit_one(s, r)) break;
-        const void* src = r.borrowed ? static_cast<const void*>(r.borrowed)
-                                     : static_cast<const void*>(s->pool_base + r.staged.off);
-        if (cudaMemcpyAsync(xyz + 3 * r.xyz_pt[0], src, (size_t)(12 * r.N),
-                            cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+        batch.c[batch.n++] = afps::FrameCopy{r.src_dev, xyz + 3 * r.xyz_pt[0], 12 * r.N};
+        batch_max = std::max(batch_max, 12 * r.N);
+        if (batch.n == afps::kFrameCopyMax && !flush()) {
             cudaGetLastError();
             return AFPS_ERR_CUDA;
         }
@@ -413,6 +448,10 @@ int afps_server_step(afps_server* s) {
         r.staged = Block{};
         s->active.push_back(std::move(s->queue.front()));
         s->queue.pop_front();
+    }
+    if (batch.n > 0 && !flush()) {
+        cudaGetLastError();
+        return AFPS_ERR_CUDA;
     }
     if (!copied.empty()) {
         cudaEvent_t ce = take_event(s);
@@ -449,7 +488,7 @@ int afps_server_step(afps_server* s) {
             d.sel = r.out_el[l];
             d.out_xyz = r.xyz_pt[l + 1];
             d.out_frame = l + 1 < s->cfg.n_levels ? r.fidx_el[l + 1] : -1;
-            int64_t res = r.res_el;
+            int64_t res = (int64_t)r.slot * s->total_samples;  // in the result slot
             for (int q = 0; q < l; ++q) res += s->levels[q];
             d.sel_frame = res;
             d.n = (int32_t)n;
@@ -459,19 +498,15 @@ int afps_server_step(afps_server* s) {
                                         M.data(), K.data(), start.data(), ints, out_begin.data(),
                                         s->stream);
         if (rc != AFPS_OK) return rc;
-        rc = afps::gather_run(s->ctx, g.data(), B, xyz, ints, ints, xyz, ints, ints, s->stream);
+        rc = afps::gather_run(s->ctx, g.data(), B, xyz, ints, ints, xyz, ints, s->pinned_dev,
+                              s->stream);
         if (rc != AFPS_OK) return rc;
 
-        // finished chains: copy their results to pinned memory
+        // finished chains: their results are in their slots once the step's
+        // gather has completed
         cudaEvent_t fin = nullptr;
         for (Request* r : run) {
             if (++r->level < s->cfg.n_levels) continue;
-            if (cudaMemcpyAsync(s->pinned + (int64_t)r->slot * s->total_samples, ints + r->res_el,
-                                (size_t)s->total_samples * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                s->stream) != cudaSuccess) {
-                cudaGetLastError();
-                return AFPS_ERR_CUDA;
-            }
             r->state = COMPLETING;
             if (!fin) fin = take_event(s);
         }
