@@ -166,25 +166,25 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                     bool ok = true;
                     for (int i = 0; i < rows; ++i) {
                         const int j = 32 * i + lane;
-                        float v = 0.f;  // padding
-                        if (j < n) {
-                            v = 1e10f;
-                            const float px = pts[3 * j], py = pts[3 * j + 1], pz = pts[3 * j + 2];
-                            // unsigned division: j + kl - p >= 0 (p <= kl)
-                            const int u = (int)divq((uint32_t)(j + kl - p));
-#pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const int tt = u - e;  // windows u and u - 1
-                                const int sj = p + tt * q;
-                                if (tt >= 0 && tt < tw && j <= sj + kr) {
-                                    const int sc = dev::checked(sj, 0, n, a.status);
-                                    const float dd = dev::sqdist(px, py, pz, pts[3 * sc],
-                                                                 pts[3 * sc + 1], pts[3 * sc + 2]);
-                                    ok = ok && dd < 1e10f;
-                                    v = fminf(v, dd);
-                                }
-                            }
-                        }
+                        // both candidate windows' distances are computed (from a
+                        // clamped point) and selected, without a branch
+                        const int jc = min(j, n - 1);
+                        const float px = pts[3 * jc], py = pts[3 * jc + 1], pz = pts[3 * jc + 2];
+                        // unsigned division: jc + kl - p >= 0 (p <= kl)
+                        const int u = (int)divq((uint32_t)(jc + kl - p));
+                        const int s1 = p + u * q, s0 = s1 - q;  // windows u and u - 1
+                        const bool in1 = j < n && u < tw && jc <= s1 + kr;
+                        const bool in0 = j < n && u >= 1 && u - 1 < tw && jc <= s0 + kr;
+                        const int c1 = dev::checked(in1 ? s1 : jc, 0, n, a.status);
+                        const int c0 = dev::checked(in0 ? s0 : jc, 0, n, a.status);
+                        const float d1 = dev::sqdist(px, py, pz, pts[3 * c1], pts[3 * c1 + 1],
+                                                     pts[3 * c1 + 2]);
+                        const float d0 = dev::sqdist(px, py, pz, pts[3 * c0], pts[3 * c0 + 1],
+                                                     pts[3 * c0 + 2]);
+                        ok = ok && (!in1 || d1 < 1e10f) && (!in0 || d0 < 1e10f);
+                        float v = j < n ? 1e10f : 0.f;  // padding: +0
+                        v = in1 ? fminf(v, d1) : v;
+                        v = in0 ? fminf(v, d0) : v;
                         Ds[j] = v;
                         unsigned m, l;
                         row_max(__float_as_uint(v), lane, m, l);
@@ -272,13 +272,13 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                     for (; t < c; ++t) {
                         const int wl = max(p - kl, 0);
                         const int wh = min(p + kr, nm1);
-                        const int j = wl + lane;
+                        // lanes past the window's end all update its last point
+                        // with the same value: no branch, no divergence
+                        const int j = min(wl + lane, wh);
                         const float qx = pts[3 * p], qy = pts[3 * p + 1], qz = pts[3 * p + 2];
-                        if (j <= wh) {
-                            const float dd = dev::sqdist(pts[3 * j], pts[3 * j + 1],
-                                                         pts[3 * j + 2], qx, qy, qz);
-                            Ds[j] = fminf(Ds[j], dd);
-                        }
+                        const float dd = dev::sqdist(pts[3 * j], pts[3 * j + 1], pts[3 * j + 2],
+                                                     qx, qy, qz);
+                        Ds[j] = fminf(Ds[j], dd);
                         __syncwarp();
                         const int r0 = wl >> 5, r1 = wh >> 5;
                         const unsigned j0 = (unsigned)(32 * r0 + lane);
