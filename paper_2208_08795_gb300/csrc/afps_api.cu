@@ -249,11 +249,14 @@ const int kCtaP[] = {2, 4, 8, 16};
 // Window-kernel variant for NPDU sectors of up to n_max points: a buffer of
 // exactly the rows needed, and the most warps per CTA (a power of two, at
 // most 8) whose buffers fit in 64 KB, so that several CTAs share an SM.
-Variant win_variant(int64_t n_max, int W = 0) {
+// lean (Variant::skip): the round form with the fewest instructions, for
+// classes with many sectors; otherwise the one with the shortest chain.
+Variant win_variant(int64_t n_max, int W = 0, bool lean = false) {
     Variant v{};
     v.kind = afps::KIND_WIN;
     v.P = (int)((n_max + 31) / 32);
     v.CS = 1;
+    v.skip = lean ? 1 : 0;
     if (W > 0) {
         v.W = W;
         return v;
@@ -269,9 +272,11 @@ Variant win_variant(int64_t n_max, int W = 0) {
 // its full rescan is as cheap as the row cache) and up to its capacity.
 bool win_default(int64_t n_max) { return n_max > 64 && n_max <= 32LL * afps::kWinMaxRows; }
 
-// Default variant for sectors of up to n_max points.
-Variant default_variant(int64_t n_max, bool npdu) {
-    if (npdu && win_default(n_max)) return win_variant(n_max);
+// Default variant for sectors of up to n_max points; `many`: the class has
+// more sectors than the GPU runs at once several times over (its time is
+// then set by the instructions it issues, not by one sector's chain).
+Variant default_variant(int64_t n_max, bool npdu, bool many = false) {
+    if (npdu && win_default(n_max)) return win_variant(n_max, 0, many);
     Variant v{};
     v.CS = 1;
     v.occ = 0;
@@ -341,10 +346,11 @@ std::vector<Variant> candidate_variants(int64_t n_max, bool npdu) {
         }
     }
     if (npdu && win_default(n_max))  // (up to 64 points the register kernels win)
-        for (int W : {1, 2, 4, 8}) {
-            const Variant v = win_variant(n_max, W);
-            if (afps::variant_supported(v)) ok.push_back(v);
-        }
+        for (int W : {1, 2, 4, 8})
+            for (bool lean : {false, true}) {
+                const Variant v = win_variant(n_max, W, lean);
+                if (afps::variant_supported(v)) ok.push_back(v);
+            }
     return ok;
 }
 
@@ -362,7 +368,7 @@ Variant choose_variant(const afps_ctx* ctx, bool npdu, int64_t n_max, int32_t c_
     if (it != ctx->tuned.end() && afps::variant_capacity(it->second) >= n_max &&
         afps::variant_supported(it->second) && (npdu || it->second.kind != afps::KIND_WIN))
         return it->second;
-    return default_variant(n_max, npdu);
+    return default_variant(n_max, npdu, items >= 8 * (size_t)std::max(ctx->num_sms, 1));
 }
 
 std::string describe(const Variant& v) {
@@ -370,12 +376,12 @@ std::string describe(const Variant& v) {
     if (v.kind == afps::KIND_WARP)
         os << "warp P=" << v.P << " W=" << v.W;
     else if (v.kind == afps::KIND_WIN)
-        os << "win P=" << v.P << " W=" << v.W;
+        os << "win P=" << v.P << " W=" << v.W << (v.skip ? " lean" : "");
     else if (v.CS > 1)
         os << "cluster P=" << v.P << " W=" << v.W << " CS=" << v.CS;
     else
         os << "cta P=" << v.P << " W=" << v.W;
-    if (v.skip) os << " skip";
+    if (v.skip && v.kind != afps::KIND_WIN) os << " skip";
     return os.str();
 }
 
@@ -1574,19 +1580,22 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
             }
             float best_ms = separate;
             int best_w = 0;
-            for (int W : {1, 2, 4, 8}) {
-                const Variant v = win_variant(n_max, W);
-                if (!afps::variant_supported(v)) continue;
-                const float ms = time_launch(v, true, d_items + plan.classes[i].first, count,
-                                             counters + plan.classes.size(), nullptr);
-                if (ms >= 0.f && ms < best_ms) {
-                    best_ms = ms;
-                    best_w = W;
+            bool best_lean = false;
+            for (int W : {1, 2, 4, 8})
+                for (bool lean : {false, true}) {
+                    const Variant v = win_variant(n_max, W, lean);
+                    if (!afps::variant_supported(v)) continue;
+                    const float ms = time_launch(v, true, d_items + plan.classes[i].first, count,
+                                                 counters + plan.classes.size(), nullptr);
+                    if (ms >= 0.f && ms < best_ms) {
+                        best_ms = ms;
+                        best_w = W;
+                        best_lean = lean;
+                    }
                 }
-            }
             for (size_t c = i; best_w && c < j; ++c) {
                 ClassPlan& cp = plan.classes[c];
-                cp.v = win_variant(cp.n_max, best_w);
+                cp.v = win_variant(cp.n_max, best_w, best_lean);
                 ctx->tuned[class_key(true, cp.n_max, cp.c_max, cp.count)] = cp.v;
             }
         }

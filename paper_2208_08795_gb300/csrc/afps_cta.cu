@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
 
 using SectorKernel = void (*)(LaunchArgs);
 SectorKernel warp_kernel_for(int P, bool npdu, bool rows);
-SectorKernel win_kernel_for(int rows, bool host_rows);
+SectorKernel win_kernel_for(int rows, bool host_rows, bool lean);
 
 static SectorKernel cta_kernel_for(int P, bool npdu, bool cluster) {
 #define AFPS_CTA_CASE(PP)                                                             \
@@ -476,7 +476,7 @@ bool variant_supported(const Variant& v) {
 // store them as rows of 32)
 static SectorKernel kernel_for(const Variant& v, bool npdu, bool rows = false) {
     if (v.kind == KIND_WARP) return warp_kernel_for(v.P, npdu, rows);
-    if (v.kind == KIND_WIN) return win_kernel_for(v.P, rows);
+    if (v.kind == KIND_WIN) return win_kernel_for(v.P, rows, v.skip != 0);
     return cta_kernel_for(v.P, npdu, v.CS > 1);
 }
 

@@ -71,7 +71,10 @@ __device__ __forceinline__ void row_max(unsigned b, int lane, unsigned& m, unsig
 }  // namespace
 
 // ROWS: the indices go to host memory (over the C2C link), as rows of 32.
-template <int R, bool ROWS>
+// LEAN: the narrow round with the fewest instructions (the touched rows'
+// cache entries first, then the argmax over the cache) instead of the one
+// with the shortest dependency chain; the autotuner picks per shape class.
+template <int R, bool ROWS, bool LEAN>
 __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -259,7 +262,55 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                 };
                 int t = t0;
                 if (full_first && t < c) round_any(t++, 0, n - 1);
-                if (kl + kr <= 31) {
+                if (LEAN && kl + kr <= 31) {
+                    // Narrow window, fewest instructions: the touched rows' cache
+                    // entries are recomputed first (the second row only when the
+                    // window crosses into it), then the sample is the argmax over
+                    // the cache: every lane's best slot (slots ascend, so the
+                    // first of equal maxima has the lowest index), two redux.sync
+                    // steps.  One row: four redux.sync, two rows: six.
+                    const int nm1 = n - 1;
+#pragma unroll 1
+                    for (; t < c; ++t) {
+                        const int wl = max(p - kl, 0);
+                        const int wh = min(p + kr, nm1);
+                        const int j = min(wl + lane, wh);  // past the end: the last point again
+                        const float qx = pts[3 * p], qy = pts[3 * p + 1], qz = pts[3 * p + 2];
+                        const float dd = dev::sqdist(pts[3 * j], pts[3 * j + 1], pts[3 * j + 2],
+                                                     qx, qy, qz);
+                        Ds[j] = fminf(Ds[j], dd);
+                        __syncwarp();
+                        const int r0 = wl >> 5, r1 = wh >> 5;
+                        {
+                            const unsigned b0 = __float_as_uint(Ds[32 * r0 + lane]);
+                            unsigned m0, l0;
+                            row_max(b0, lane, m0, l0);
+                            set_row<R>(rmb, rmi, r0, m0, (unsigned)(32 * r0) + l0, lane);
+                        }
+                        if (r1 != r0) {
+                            const unsigned b1 = __float_as_uint(Ds[32 * r1 + lane]);
+                            unsigned m1, l1;
+                            row_max(b1, lane, m1, l1);
+                            set_row<R>(rmb, rmi, r1, m1, (unsigned)(32 * r1) + l1, lane);
+                        }
+                        unsigned cb = rmb[0], ci = rmi[0];
+#pragma unroll
+                        for (int s = 1; s < R; ++s) {
+                            const bool gt = rmb[s] > cb;
+                            cb = gt ? rmb[s] : cb;
+                            ci = gt ? rmi[s] : ci;
+                        }
+                        const unsigned mx = __reduce_max_sync(dev::kFull, cb);
+                        p = dev::checked((int)__reduce_min_sync(dev::kFull, cb == mx ? ci : 0xffffffffu),
+                                         0, n, a.status);
+                        if (ROWS) {
+                            obuf = lane == (t & 31) ? d.lo + p : obuf;
+                            if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
+                        } else if (lane == 0) {
+                            out[t] = d.lo + p;
+                        }
+                    }
+                } else if (kl + kr <= 31) {
                     // Narrow window (at most 32 points): lane i updates point
                     // wl + i; the window touches row r0 and perhaps r1 = r0 + 1.
                     // The maxima of the touched rows (m0, m1) and of the cached
@@ -329,12 +380,17 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
 using SectorKernel = void (*)(LaunchArgs);
 
 // Kernel for sectors of up to 32 * rows points (rows <= kWinMaxRows).
-SectorKernel win_kernel_for(int rows, bool host_rows) {
+SectorKernel win_kernel_for(int rows, bool host_rows, bool lean) {
+#define AFPS_WIN_CASE(RR)                                                                      \
+    if (host_rows)                                                                             \
+        return lean ? afps_win_kernel<RR, true, true> : afps_win_kernel<RR, true, false>;      \
+    return lean ? afps_win_kernel<RR, false, true> : afps_win_kernel<RR, false, false>;
     const int slots = (rows + 31) / 32;
-    if (slots <= 1) return host_rows ? afps_win_kernel<1, true> : afps_win_kernel<1, false>;
-    if (slots <= 2) return host_rows ? afps_win_kernel<2, true> : afps_win_kernel<2, false>;
-    if (slots <= 4) return host_rows ? afps_win_kernel<4, true> : afps_win_kernel<4, false>;
-    if (slots <= 8) return host_rows ? afps_win_kernel<8, true> : afps_win_kernel<8, false>;
+    if (slots <= 1) { AFPS_WIN_CASE(1) }
+    if (slots <= 2) { AFPS_WIN_CASE(2) }
+    if (slots <= 4) { AFPS_WIN_CASE(4) }
+    if (slots <= 8) { AFPS_WIN_CASE(8) }
+#undef AFPS_WIN_CASE
     return nullptr;
 }
 

@@ -188,6 +188,11 @@ VARIANTS = [  # (N, C, M, k, kind, P, W, CS)
     (20000, 4000, 4, 8, 2, 157, 1, 1), (8192, 2048, 1, 8, 2, 256, 1, 1),
     (640, 640, 20, 16, 2, 1, 8, 1), (4000, 1500, 8, 70, 2, 16, 8, 1),
     (3000, 900, 3, 1, 2, 40, 2, 1),
+    # the window kernel's lean round form (skip = 1): one and two row-maximum
+    # slots, windows within and across rows, the widest sector
+    (3000, 300, 10, 9, 2, 10, 4, 1, 1), (2100, 500, 2, 16, 2, 33, 2, 1, 1),
+    (640, 640, 20, 16, 2, 1, 8, 1, 1), (8192, 2048, 1, 8, 2, 256, 1, 1, 1),
+    (3000, 900, 3, 1, 2, 40, 2, 1, 1),
 ]
 
 
@@ -214,7 +219,7 @@ def test_forced_variant(tmp_path, row):
         else:
             want = f"cta P={Pp} W={W}"
         if skip:
-            want += " skip"
+            want += " lean" if kind == 2 else " skip"
         P = synth.uniform_cloud(N + 31 * M + k, N)
         x = torch.from_numpy(P).cuda()
         out = s.sample(x, C, M, k, 1)
@@ -245,7 +250,8 @@ def test_table_iv_sizes(S, N, M, k):
 # enough apart to reach 1e10.
 STRIDE_KERNELS = [(0, 2, 4, 1), (0, 8, 2, 1), (1, 2, 8, 1), (1, 8, 4, 1), (1, 16, 8, 1),
                   (1, 4, 8, 4), (1, 16, 4, 2),  # these two: thread-block clusters
-                  (2, 9, 4, 1), (2, 40, 2, 1)]  # window kernel, one and two slots per lane
+                  (2, 9, 4, 1), (2, 40, 2, 1),  # window kernel, one and two slots per lane
+                  (2, 9, 4, 1, 1), (2, 40, 2, 1, 1)]  # ... and its lean round form
 
 
 def stride_len(n, k, r, method=0):
@@ -268,7 +274,8 @@ def stride_cases(n):
 
 @pytest.mark.parametrize("kern", STRIDE_KERNELS, ids=[str(k) for k in STRIDE_KERNELS])
 def test_npdu_stride_phase(tmp_path, kern):
-    kind, Pp, W, CS = kern
+    kind, Pp, W, CS = kern[:4]
+    lean = kern[4] if len(kern) > 4 else 0
     build_mod.build()
     cap = 32 * W * Pp * CS if kind == 1 else 32 * Pp
     sizes = [cap - 3] + ([288] if cap >= 288 else [])
@@ -281,7 +288,7 @@ def test_npdu_stride_phase(tmp_path, kern):
             C = M * c
             key = f"npdu:n{n}:c{c}:i{pow2(M)}"
             path = tmp_path / "tune.txt"
-            path.write_text(f"{key} {kind} {Pp} {W} {CS} 0 0\n")
+            path.write_text(f"{key} {kind} {Pp} {W} {CS} 0 {lean}\n")
             s = B.Sampler(0, tune_cache=str(path))
             try:
                 P = (synth.uniform_cloud(7 * n + k + r, N) * scale).astype(np.float32)
