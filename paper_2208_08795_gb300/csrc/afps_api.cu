@@ -87,6 +87,7 @@ struct ClassPlan {
     // they are stored back to back: the kernel computes its items
     bool uniform = false;
     bool merged = false;  // several shape classes in one launch (window kernels)
+    bool narrow = true;   // every item's window has at most 17 points, read literally
     afps::SingleCloud single{};
     const afps::SingleCloud* run() const { return uniform ? &single : nullptr; }
 };
@@ -267,6 +268,23 @@ Variant win_variant(int64_t n_max, int W = 0, bool lean = false) {
     return v;
 }
 
+// Pair-kernel variant (two sectors per warp, 16-point rows) for narrow
+// NPDU windows and sectors of up to n_max points: W as for win_variant.
+Variant win2_variant(int64_t n_max, int W = 0) {
+    Variant v{};
+    v.kind = afps::KIND_WIN2;
+    v.P = (int)((n_max + 15) / 16);
+    v.CS = 1;
+    if (W > 0) {
+        v.W = W;
+        return v;
+    }
+    const int64_t per_warp = 2 * (16 * 16 * (int64_t)v.P + 16);
+    v.W = 8;
+    while (v.W > 1 && v.W * per_warp > 64 * 1024) v.W /= 2;
+    return v;
+}
+
 // Whether NPDU sectors of up to n_max points go to the window kernel by
 // default: above 64 points (two rows per lane in the register kernel, where
 // its full rescan is as cheap as the row cache) and up to its capacity.
@@ -314,7 +332,7 @@ Variant default_variant(int64_t n_max, bool npdu, bool many = false) {
 
 // Every variant the autotuner tries for sectors of up to n_max points (with
 // and without the NPDU row skip when the class uses NPDU).
-std::vector<Variant> candidate_variants(int64_t n_max, bool npdu) {
+std::vector<Variant> candidate_variants(int64_t n_max, bool npdu, bool narrow = false) {
     std::vector<Variant> out;
     if (n_max <= 1024) {
         for (int P : kWarpP) {
@@ -346,11 +364,15 @@ std::vector<Variant> candidate_variants(int64_t n_max, bool npdu) {
         }
     }
     if (npdu && win_default(n_max))  // (up to 64 points the register kernels win)
-        for (int W : {1, 2, 4, 8})
+        for (int W : {1, 2, 4, 8}) {
             for (bool lean : {false, true}) {
                 const Variant v = win_variant(n_max, W, lean);
                 if (afps::variant_supported(v)) ok.push_back(v);
             }
+            const Variant v2 = win2_variant(n_max, W);
+            if (narrow && afps::variant_supported(v2) && afps::variant_capacity(v2) >= n_max)
+                ok.push_back(v2);
+        }
     return ok;
 }
 
@@ -363,10 +385,13 @@ std::string class_key(bool npdu, int64_t n_max, int32_t c_max, size_t items) {
 }
 
 Variant choose_variant(const afps_ctx* ctx, bool npdu, int64_t n_max, int32_t c_max,
-                       size_t items) {
+                       size_t items, bool narrow = false) {
     auto it = ctx->tuned.find(class_key(npdu, n_max, c_max, items));
+    const bool windows = it != ctx->tuned.end() &&
+                         (it->second.kind == afps::KIND_WIN || it->second.kind == afps::KIND_WIN2);
     if (it != ctx->tuned.end() && afps::variant_capacity(it->second) >= n_max &&
-        afps::variant_supported(it->second) && (npdu || it->second.kind != afps::KIND_WIN))
+        afps::variant_supported(it->second) && (npdu || !windows) &&
+        (narrow || it->second.kind != afps::KIND_WIN2))
         return it->second;
     return default_variant(n_max, npdu, items >= 8 * (size_t)std::max(ctx->num_sms, 1));
 }
@@ -377,11 +402,13 @@ std::string describe(const Variant& v) {
         os << "warp P=" << v.P << " W=" << v.W;
     else if (v.kind == afps::KIND_WIN)
         os << "win P=" << v.P << " W=" << v.W << (v.skip ? " lean" : "");
+    else if (v.kind == afps::KIND_WIN2)
+        os << "pair P=" << v.P << " W=" << v.W;
     else if (v.CS > 1)
         os << "cluster P=" << v.P << " W=" << v.W << " CS=" << v.CS;
     else
         os << "cta P=" << v.P << " W=" << v.W;
-    if (v.skip && v.kind != afps::KIND_WIN) os << " skip";
+    if (v.skip && v.kind != afps::KIND_WIN && v.kind != afps::KIND_WIN2) os << " skip";
     return os.str();
 }
 
@@ -404,7 +431,8 @@ int grid_for(const Variant& v, size_t count) {
     } else {
         cap = it->second;
     }
-    size_t want = v.kind != afps::KIND_CTA ? (count + v.W - 1) / v.W : count;
+    const size_t per_cta = v.kind == afps::KIND_WIN2 ? 2 * (size_t)v.W : (size_t)v.W;
+    size_t want = v.kind != afps::KIND_CTA ? (count + per_cta - 1) / per_cta : count;
     if (cap > 0 && want > (size_t)cap) want = (size_t)cap;
     return (int)std::max<size_t>(want, 1);
 }
@@ -419,7 +447,8 @@ uint32_t stall_bits(uint32_t flags) {
 // dynamic work queue: warp-per-item kernels whose grid is capped below one
 // warp per item (persistent launch); otherwise items map to warps 1:1.
 bool uses_queue(const Variant& v, size_t count) {
-    return v.kind != afps::KIND_CTA && (size_t)grid_for(v, count) * (size_t)v.W < count;
+    const size_t per_cta = v.kind == afps::KIND_WIN2 ? 2 * (size_t)v.W : (size_t)v.W;
+    return v.kind != afps::KIND_CTA && (size_t)grid_for(v, count) * per_cta < count;
 }
 
 // Work-queue counters start at zero and every launch leaves its counter at
@@ -470,35 +499,30 @@ int64_t size_bucket(int64_t n_max) {
 
 // Cloud b: n_pts[b] points from point pt_begin[b] of the xyz base, C[b]
 // indices written from out_begin[b] of the output base (out_cap[b] slots).
-// Rows-per-lane template of a window-kernel variant (afps_win.cu).
-int win_slots(const Variant& v) {
-    int r = 1;
-    while (32 * r < v.P) r <<= 1;
-    return r;
-}
-
 // Work of an item, for largest-first ordering of a class's queue.
 int64_t item_cost(const ItemDesc& d, bool npdu) {
     return npdu ? (int64_t)d.c * (d.kl + d.kr + 1 + d.n / 32) : (int64_t)d.c * d.n;
 }
 
 // Consecutive table classes whose variants are window kernels of the same
-// template (slots per lane) run as one launch: the buffer for the larger
-// sectors holds the smaller ones, and one dynamic queue over all of them
-// (largest work first) leaves a shorter tail than launches one after the
-// other.  The items of consecutive classes are contiguous in the table.
+// kind run as one launch: the buffer and the template (row-maximum slots per
+// lane) for the largest sectors hold the smaller ones, and one dynamic queue
+// over all of them (largest work first) leaves a shorter tail than launches
+// one after the other.  The items of consecutive classes are contiguous in
+// the table.
 void merge_window_classes(BatchPlan& plan) {
     std::vector<ClassPlan> out;
     for (const ClassPlan& cp : plan.classes) {
         if (!out.empty()) {
             ClassPlan& last = out.back();
-            if (!last.uniform && !cp.uniform && last.npdu && cp.npdu &&
-                last.v.kind == afps::KIND_WIN && cp.v.kind == afps::KIND_WIN &&
-                win_slots(last.v) == win_slots(cp.v) && last.first + last.count == cp.first) {
+            const bool windows = last.v.kind == afps::KIND_WIN || last.v.kind == afps::KIND_WIN2;
+            if (!last.uniform && !cp.uniform && last.npdu && cp.npdu && windows &&
+                last.v.kind == cp.v.kind && last.first + last.count == cp.first) {
                 if (cp.v.P > last.v.P) last.v = cp.v;
                 last.count += cp.count;
                 last.n_max = std::max(last.n_max, cp.n_max);
                 last.c_max = std::max(last.c_max, cp.c_max);
+                last.narrow = last.narrow && cp.narrow;
                 last.merged = true;  // re-sorted below
                 continue;
             }
@@ -590,7 +614,8 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
                 cp.n_max = m0.chk.n_max;
                 cp.c_max = m0.chk.c_max;
                 cp.count = g.second.size() * (size_t)M[b0];
-                cp.v = choose_variant(ctx, cp.npdu, cp.n_max, cp.c_max, cp.count);
+                cp.narrow = w.kl + w.kr <= 16 && !(w.flags & afps::ITEM_FULL_FIRST);
+                cp.v = choose_variant(ctx, cp.npdu, cp.n_max, cp.c_max, cp.count, cp.narrow);
                 plan.classes.push_back(cp);
                 continue;
             }
@@ -611,6 +636,7 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
                 d.first = std::min<int32_t>(m.chk.start_r, d.n - 1);
                 d.lo = (int32_t)lo;
                 window_sides(K[b], method ? method[b] : 0u, d);
+                cp.narrow = cp.narrow && d.kl + d.kr <= 16 && !(d.flags & afps::ITEM_FULL_FIRST);
                 plan.items.push_back(d);
             }
         }
@@ -621,7 +647,7 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
                          [npdu](const ItemDesc& x, const ItemDesc& y) {
                              return item_cost(x, npdu) > item_cost(y, npdu);
                          });
-        cp.v = choose_variant(ctx, cp.npdu, cp.n_max, cp.c_max, cp.count);
+        cp.v = choose_variant(ctx, cp.npdu, cp.n_max, cp.c_max, cp.count, cp.narrow);
         plan.classes.push_back(cp);
     }
     if (merge) merge_window_classes(plan);
@@ -1118,7 +1144,10 @@ int afps_sample_ex(afps_ctx* ctx, const float* d_xyz, int64_t N, int32_t C, int3
     if (chk.code != AFPS_OK) return fail(ctx, chk.code, "afps_sample: " + chk.msg);
     DeviceGuard guard(ctx->device);
     const bool npdu = npdu_window > 0;
-    const Variant v = choose_variant(ctx, npdu, chk.n_max, chk.c_max, (size_t)M);
+    ItemDesc wsides{};
+    window_sides(npdu_window, method, wsides);
+    const bool narrow = wsides.kl + wsides.kr <= 16 && !(wsides.flags & afps::ITEM_FULL_FIRST);
+    const Variant v = choose_variant(ctx, npdu, chk.n_max, chk.c_max, (size_t)M, narrow);
     LaunchArgs a{};
     a.xyz = d_xyz;
     a.items = nullptr;
@@ -1537,7 +1566,7 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
         ClassPlan& cp = plan.classes[i];
         float best_ms = 1e30f;
         Variant best = cp.v;
-        for (const Variant& v : candidate_variants(cp.n_max, cp.npdu)) {
+        for (const Variant& v : candidate_variants(cp.n_max, cp.npdu, cp.narrow)) {
             const float ms = time_launch(v, cp.npdu, cp.uniform ? nullptr : d_items + cp.first,
                                          cp.count, counters + i, cp.run());
             if (ms >= 0.f && ms < best_ms) {
@@ -1559,14 +1588,13 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
         auto fits = [&](const ClassPlan& c) {
             return c.npdu && !c.uniform && c.n_max <= 32LL * afps::kWinMaxRows;
         };
+        // (the pair kernel joins in when every class of the run is narrow)
         if (!fits(plan.classes[i])) {
             ++i;
             continue;
         }
-        const int slots = win_slots(win_variant(plan.classes[i].n_max));
         size_t j = i + 1;
         while (j < plan.classes.size() && fits(plan.classes[j]) &&
-               win_slots(win_variant(plan.classes[j].n_max)) == slots &&
                plan.classes[j].first == plan.classes[j - 1].first + plan.classes[j - 1].count)
             ++j;
         if (j - i >= 2) {
@@ -1578,24 +1606,27 @@ int afps_autotune_batched(afps_ctx* ctx, const float* d_xyz, const int64_t* h_pt
                 count += plan.classes[c].count;
                 n_max = std::max(n_max, plan.classes[c].n_max);
             }
+            bool pairs_fit = afps::variant_supported(win2_variant(n_max));
+            for (size_t c = i; c < j; ++c) pairs_fit = pairs_fit && plan.classes[c].narrow;
             float best_ms = separate;
-            int best_w = 0;
-            bool best_lean = false;
+            int best_w = 0, best_form = 0;  // form: 0 window, 1 window lean, 2 pairs
             for (int W : {1, 2, 4, 8})
-                for (bool lean : {false, true}) {
-                    const Variant v = win_variant(n_max, W, lean);
+                for (int form = 0; form < (pairs_fit ? 3 : 2); ++form) {
+                    const Variant v = form == 2 ? win2_variant(n_max, W)
+                                                : win_variant(n_max, W, form == 1);
                     if (!afps::variant_supported(v)) continue;
                     const float ms = time_launch(v, true, d_items + plan.classes[i].first, count,
                                                  counters + plan.classes.size(), nullptr);
                     if (ms >= 0.f && ms < best_ms) {
                         best_ms = ms;
                         best_w = W;
-                        best_lean = lean;
+                        best_form = form;
                     }
                 }
             for (size_t c = i; best_w && c < j; ++c) {
                 ClassPlan& cp = plan.classes[c];
-                cp.v = win_variant(cp.n_max, best_w, best_lean);
+                cp.v = best_form == 2 ? win2_variant(cp.n_max, best_w)
+                                      : win_variant(cp.n_max, best_w, best_form == 1);
                 ctx->tuned[class_key(true, cp.n_max, cp.c_max, cp.count)] = cp.v;
             }
         }
@@ -1629,7 +1660,8 @@ int afps_describe_plan(afps_ctx* ctx, int64_t n_sector, int32_t c_sector, int32_
         n_items < 1)
         return AFPS_ERR_INVALID_ARG;
     const Variant v =
-        choose_variant(ctx, npdu_window > 0, n_sector, c_sector, (size_t)n_items);
+        choose_variant(ctx, npdu_window > 0, n_sector, c_sector, (size_t)n_items,
+                       npdu_window <= 16);
     const std::string s = describe(v);
     snprintf(buf, (size_t)buf_len, "%s", s.c_str());
     return (int)s.size();

@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
 using SectorKernel = void (*)(LaunchArgs);
 SectorKernel warp_kernel_for(int P, bool npdu, bool rows);
 SectorKernel win_kernel_for(int rows, bool host_rows, bool lean);
+SectorKernel win2_kernel_for(int rows16, bool host_rows);
 
 static SectorKernel cta_kernel_for(int P, bool npdu, bool cluster) {
 #define AFPS_CTA_CASE(PP)                                                             \
@@ -453,6 +454,8 @@ size_t variant_smem(const Variant& v) {
         return 16 * ((8 * (size_t)v.W + 15) / 16) + (size_t)v.W * (12 * 32 * (size_t)v.P + 16);
     if (v.kind == KIND_WIN)  // per warp: xyz (12 bytes a point + 16) and distances (4 bytes)
         return 16 * ((8 * (size_t)v.W + 15) / 16) + (size_t)v.W * (16 * 32 * (size_t)v.P + 16);
+    if (v.kind == KIND_WIN2)  // two barriers and two such buffers (per half) per warp
+        return 16 * (size_t)v.W + 2 * (size_t)v.W * (16 * 16 * (size_t)v.P + 16);
     // records (one per CTA of a cluster, else one per warp), double-buffered;
     // a cluster's CTAs also keep their warps' keys; then the points
     const size_t E = v.CS > 1 ? (size_t)v.CS : (size_t)v.W;
@@ -466,6 +469,9 @@ bool variant_supported(const Variant& v) {
     if (v.kind == KIND_WIN)
         return v.P >= 1 && v.P <= kWinMaxRows && v.W >= 1 && v.W <= 8 && v.CS == 1 &&
                variant_smem(v) <= 227 * 1024;
+    if (v.kind == KIND_WIN2)
+        return v.P >= 1 && v.P <= kWin2MaxRows && v.W >= 1 && v.W <= 8 && v.CS == 1 &&
+               variant_smem(v) <= 227 * 1024;
     if (v.kind != KIND_CTA) return false;
     if (!cta_kernel_for(v.P, false, false)) return false;
     if (v.W < 1 || v.W > (v.P >= 16 ? 8 : 32) || v.CS < 1 || v.CS > 16) return false;
@@ -477,6 +483,7 @@ bool variant_supported(const Variant& v) {
 static SectorKernel kernel_for(const Variant& v, bool npdu, bool rows = false) {
     if (v.kind == KIND_WARP) return warp_kernel_for(v.P, npdu, rows);
     if (v.kind == KIND_WIN) return win_kernel_for(v.P, rows, v.skip != 0);
+    if (v.kind == KIND_WIN2) return win2_kernel_for(v.P, rows);
     return cta_kernel_for(v.P, npdu, v.CS > 1);
 }
 
@@ -512,9 +519,10 @@ static cudaError_t prepare(SectorKernel fn, const Variant& v, size_t smem) {
 cudaError_t launch_sector(const Variant& v, bool npdu, const LaunchArgs& args, int grid,
                           cudaStream_t stream) {
     if (!variant_supported(v) || grid < 1) return cudaErrorInvalidValue;
-    if (v.kind == KIND_WIN && !npdu) return cudaErrorInvalidValue;  // windows only
+    if ((v.kind == KIND_WIN || v.kind == KIND_WIN2) && !npdu)
+        return cudaErrorInvalidValue;  // windows only
     LaunchArgs a = args;
-    a.win_cap = v.kind == KIND_WIN ? 32 * v.P : 0;
+    a.win_cap = v.kind == KIND_WIN ? 32 * v.P : v.kind == KIND_WIN2 ? 16 * v.P : 0;
     SectorKernel fn = kernel_for(v, npdu, a.host_resident != 0);
     const size_t smem = variant_smem(v);
     cudaError_t e = prepare(fn, v, smem);

@@ -186,13 +186,16 @@ __device__ __forceinline__ bool is_timeout(int status) {
 // a launch draws exactly n_items + (warps in the grid) tickets; the warp that
 // draws the last of them is the last to touch the counter and sets it back
 // to zero for the next launch (no memset between launches).
-__device__ __forceinline__ int queue_next(const LaunchArgs& a, int nwarps, int lane) {
+__device__ __forceinline__ int queue_next_of(unsigned* counter, int n, int nwarps, int lane) {
     unsigned v = 0;
     if (lane == 0) {
-        v = atomicAdd(a.counter, 1u);
-        if (v == (unsigned)a.n_items + (unsigned)nwarps - 1u) atomicExch(a.counter, 0u);
+        v = atomicAdd(counter, 1u);
+        if (v == (unsigned)n + (unsigned)nwarps - 1u) atomicExch(counter, 0u);
     }
     return (int)__shfl_sync(kFull, v, 0);
+}
+__device__ __forceinline__ int queue_next(const LaunchArgs& a, int nwarps, int lane) {
+    return queue_next_of(a.counter, a.n_items, nwarps, lane);
 }
 
 // Debug build (AFPS_DEBUG_CHECKS): index v must lie in [lo, hi); otherwise

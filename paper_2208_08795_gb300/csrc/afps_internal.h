@@ -49,14 +49,17 @@ inline uint64_t div_magic(int32_t d) {
     return d >= 2 ? ~0ull / (uint64_t)d + 1ull : 0ull;
 }
 
-enum Kind : int32_t { KIND_WARP = 0, KIND_CTA = 1, KIND_WIN = 2 };
+enum Kind : int32_t { KIND_WARP = 0, KIND_CTA = 1, KIND_WIN = 2, KIND_WIN2 = 3 };
 
 // A kernel variant.  KIND_WARP: one warp per item, W items per CTA.
 // KIND_CTA: one CTA (CS == 1) or one cluster of CS CTAs per item, W warps
 // per CTA.  P = points held per thread, in registers.  KIND_WIN (NPDU only):
 // one warp per item, W items per CTA, distances in shared memory with cached
 // row maxima; P = rows of 32 points a warp's buffer holds (sectors of up to
-// 32 P points, P <= kWinMaxRows).
+// 32 P points, P <= kWinMaxRows).  KIND_WIN2 (NPDU windows of at most 17
+// points, literal reading): two items per warp, one per half-warp, W warps
+// per CTA; P = rows of 16 points a half's buffer holds (sectors of up to 16 P
+// points, P <= kWin2MaxRows).
 struct Variant {
     int32_t kind;
     int32_t P;
@@ -78,7 +81,7 @@ struct LaunchArgs {
     uint32_t stall;         // fault injection (STALL_* bits)
     uint32_t npdu_skip;     // Variant::skip
     uint32_t host_resident; // points live in (mapped) host memory: plain loads only
-    int32_t win_cap;        // KIND_WIN: points per warp buffer (32 P)
+    int32_t win_cap;        // KIND_WIN: points per warp buffer (32 P); KIND_WIN2: per half (16 P)
 };
 
 // LaunchArgs::stall bits (fault injection for tests of failure detection):
@@ -99,9 +102,12 @@ enum DeviceStatus : int {
 // KIND_WIN: largest number of 32-point rows per sector (lane l of the warp
 // caches the maxima of rows l, l + 32, ..., up to kWinMaxRows / 32 of them).
 constexpr int kWinMaxRows = 256;
+// KIND_WIN2: largest number of 16-point rows per sector (8 slots of 16).
+constexpr int kWin2MaxRows = 128;
 
 // Points a variant can hold per item.
 inline int64_t variant_capacity(const Variant& v) {
+    if (v.kind == KIND_WIN2) return 16LL * v.P;
     return v.kind == KIND_CTA ? 32LL * v.W * v.P * v.CS : 32LL * v.P;
 }
 

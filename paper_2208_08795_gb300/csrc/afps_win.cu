@@ -34,10 +34,10 @@ namespace {
 // lane r % 32 (slot r / 32).
 template <int R>
 __device__ __forceinline__ void set_row(unsigned (&rmb)[R], unsigned (&rmi)[R], int r,
-                                        unsigned m, unsigned idx, int lane) {
+                                        unsigned m, unsigned idx, int lane, int lanes = 32) {
 #pragma unroll
     for (int s = 0; s < R; ++s)
-        if (r == lane + 32 * s) {
+        if (r == lane + lanes * s) {
             rmb[s] = m;
             rmi[s] = idx;
         }
@@ -377,9 +377,246 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- pairs
+// Two sectors per warp, one per half-warp of 16 lanes, for windows of at most
+// 17 points (kl + kr <= 16) read literally (no full first pass).  A round's
+// bookkeeping (window bounds, the touched rows, the reductions, the store)
+// is then shared by two sectors: every instruction serves both halves, each
+// with its own data; a reduction takes two full-warp redux.sync steps (one
+// per half) or one ballot.  The sample's own distance becomes +0 without arithmetic
+// (its distance to itself is exactly +0), so its 16 neighbours take one lane
+// each.  Rows are 16 points; half-lane h caches rows h, h + 16, ... (R
+// slots, sectors of up to 256 R points).  Rounds take the lean form (the
+// touched rows' cache entries, then the argmax over the cache), and the two
+// halves run them in lockstep: the loop runs while either half has rounds
+// left, a half past its last round computes without storing, and both rows
+// a window may touch are reduced every round (the second is the first again
+// when the window stays in one row), so no branch splits the warp.
+// Per-half reductions with the full warp's mask: the other half's lanes
+// contribute the operation's identity, and each lane keeps its own half's
+// result.  (Each half naming only its own 16 lanes would give two different
+// member masks in one instruction.)
+__device__ __forceinline__ unsigned half_max(unsigned v, int half) {
+    const unsigned lo = __reduce_max_sync(dev::kFull, half ? 0u : v);
+    const unsigned hi = __reduce_max_sync(dev::kFull, half ? v : 0u);
+    return half ? hi : lo;
+}
+__device__ __forceinline__ unsigned half_min(unsigned v, int half) {
+    const unsigned lo = __reduce_min_sync(dev::kFull, half ? 0xffffffffu : v);
+    const unsigned hi = __reduce_min_sync(dev::kFull, half ? v : 0xffffffffu);
+    return half ? hi : lo;
+}
+// Lowest lane of this half (0..15) where pred holds; pred must hold somewhere.
+__device__ __forceinline__ unsigned half_first(bool pred, unsigned hmask, int half) {
+    return (unsigned)(__ffs((int)(__ballot_sync(dev::kFull, pred) & hmask)) - 1 - 16 * half);
+}
+
+template <int R, bool ROWS>
+__global__ void __launch_bounds__(256) afps_win2_kernel(const LaunchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int half = lane >> 4, hl = lane & 15;
+    const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
+    const int w = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    const int cap = a.win_cap;  // points per half buffer: xyz 12 cap + 16 bytes, distances 4 cap
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);  // two per warp
+    unsigned char* buf = smem + 16 * W + (size_t)(2 * w + half) * (16 * (size_t)cap + 16);
+    float* Ds = reinterpret_cast<float*>(buf + 12 * (size_t)cap + 16);
+    const uint32_t bar = dev::smem_u32(&bars[2 * w + half]);
+    if (hl == 0) {
+        dev::mbar_init(bar, 1);
+        dev::fence_mbar_init();
+    }
+    __syncwarp();
+    dev::pdl_wait();
+    dev::pdl_launch_dependents();
+    uint32_t phase = 0;   // of this half's barrier
+    bool halted = false;  // a timeout was seen: leave the remaining items undone
+
+    const int npairs = (a.n_items + 1) / 2;
+    const int nwarps = gridDim.x * W;
+    int pair = a.counter ? dev::queue_next_of(a.counter, npairs, nwarps, lane) : blockIdx.x * W + w;
+
+    while (pair < npairs) {
+        if (!halted) {
+            const int item = 2 * pair + half;
+            const bool has = item < a.n_items;  // the last pair's second half may be empty
+            ItemDesc d{};
+            d.n = 1;
+            if (has) d = dev::load_item(a, item);
+            const int n = dev::checked(d.n, 1, cap + 1, a.status);
+
+            // ---- stage-in, one bulk copy per half
+            dev::fence_proxy_async_smem();
+            __syncwarp();
+            bool bulk = false;
+            const float* pts = reinterpret_cast<const float*>(buf);
+            if (has)
+                pts = dev::stage_points(a.xyz + 3 * d.src, n, buf, bar, hl == 0, hl, 16, &bulk,
+                                        (a.stall & STALL_COPY) != 0, a.host_resident != 0);
+            const int seen = dev::load_status(a.status);
+            bool late = false;
+            if (bulk) {
+                late = !dev::mbar_wait_bounded(bar, phase, a.timeout_ns);
+                if (late) {
+                    dev::record_status(a.status, DEV_TIMEOUT_STAGE);
+                    if (!dev::mbar_wait_bounded(bar, phase, a.timeout_ns))
+                        dev::record_status(a.status, DEV_TIMEOUT_DRAIN);
+                }
+                phase ^= 1u;
+            }
+            __syncwarp();
+            halted = __any_sync(dev::kFull, late || dev::is_timeout(seen));
+            if (!halted) {
+                // Both halves run every step below in lockstep (no branch that
+                // differs between them inside the loops), each on its own
+                // data; a half without work (no item, its rounds done, no
+                // stride phase) computes on its own buffer and stores nothing.
+                const int rows = (n + 15) >> 4;
+                unsigned rmb[R], rmi[R];  // cached maxima of 16-point rows
+#pragma unroll
+                for (int s = 0; s < R; ++s) {
+                    const int r = hl + 16 * s;
+                    rmb[s] = r < rows ? __float_as_uint(1e10f) : 0u;
+                    rmi[s] = r < rows ? (unsigned)(16 * r) : 0xffffffffu;
+                }
+                int32_t* out = a.out + d.dst;
+                const int c = has ? dev::checked(d.c, 1, n + 1, a.status) : 0;
+                const int kl = d.kl;
+                const int kr = d.kr;
+                int p = dev::checked(d.first, 0, n, a.status);
+                int obuf = hl == 0 ? d.lo + p : 0;
+                if (has && hl == 0 && !ROWS) out[0] = d.lo + p;
+                int t = 1;
+                // stride phase, as in the full-warp kernel, over 16-point rows
+                const bool sp = has && p <= kl && kl <= kr;
+                const int q = kr + 1;
+                const dev::SmallDiv divq((uint32_t)q);
+                const int x = n - 1 - kr - p;
+                const int ts = x <= 0 ? 1 : (int)divq((uint32_t)(x + q - 1)) + 1;
+                const int tn = min(ts, c);
+                const int tw = min(ts, c - 1);
+                bool ok = true;
+                const int srows = sp ? rows : 0;
+                const int rmax = max(srows, __shfl_xor_sync(dev::kFull, srows, 16));
+                for (int i = 0; i < rmax; ++i) {
+                    const bool ract = i < srows;
+                    const int j = 16 * i + hl;
+                    const int jc = min(j, n - 1);
+                    const float px = pts[3 * jc], py = pts[3 * jc + 1], pz = pts[3 * jc + 2];
+                    const int u = (int)divq((uint32_t)(max(jc + kl - p, 0)));
+                    const int s1 = p + u * q, s0 = s1 - q;
+                    const bool in1 = ract && j < n && u < tw && jc <= s1 + kr;
+                    const bool in0 = ract && j < n && u >= 1 && u - 1 < tw && jc <= s0 + kr;
+                    const int c1 = dev::checked(in1 ? s1 : jc, 0, n, a.status);
+                    const int c0 = dev::checked(in0 ? s0 : jc, 0, n, a.status);
+                    const float d1 = dev::sqdist(px, py, pz, pts[3 * c1], pts[3 * c1 + 1],
+                                                 pts[3 * c1 + 2]);
+                    const float d0 = dev::sqdist(px, py, pz, pts[3 * c0], pts[3 * c0 + 1],
+                                                 pts[3 * c0 + 2]);
+                    ok = ok && (!in1 || d1 < 1e10f) && (!in0 || d0 < 1e10f);
+                    float v = j < n ? 1e10f : 0.f;
+                    v = in1 ? fminf(v, d1) : v;
+                    v = in0 ? fminf(v, d0) : v;
+                    if (ract) Ds[j] = v;
+                    const unsigned b = __float_as_uint(v);
+                    const unsigned m = half_max(b, half);
+                    const unsigned l = half_first(b == m, hmask, half);
+                    if (ract) set_row<R>(rmb, rmi, i, m, (unsigned)(16 * i) + l, hl, 16);
+                }
+                const bool stride_ok = sp && (__ballot_sync(dev::kFull, !ok) & hmask) == 0u;
+                if (stride_ok) {
+                    if (ROWS) {
+                        for (int r0 = 0; r0 + 16 <= tn; r0 += 16)
+                            out[r0 + hl] = d.lo + p + (r0 + hl) * q;
+                        obuf = d.lo + p + (((tn - 1) & ~15) + hl) * q;
+                    } else {
+                        for (int tt = 1 + hl; tt < tn; tt += 16) out[tt] = d.lo + p + tt * q;
+                    }
+                    p += (tn - 1) * q;
+                    t = tn;
+                } else {
+                    if (sp) {  // the stride test failed: start again from 1e10
+#pragma unroll
+                        for (int s = 0; s < R; ++s) {
+                            const int r = hl + 16 * s;
+                            rmb[s] = r < rows ? __float_as_uint(1e10f) : 0u;
+                            rmi[s] = r < rows ? (unsigned)(16 * r) : 0xffffffffu;
+                        }
+                    }
+                    for (int j = hl; j < 16 * rows; j += 16) Ds[j] = j < n ? 1e10f : 0.f;
+                }
+                __syncwarp();
+                const int nm1 = n - 1;
+#pragma unroll 1
+                while (__any_sync(dev::kFull, t < c)) {
+                    const bool act = t < c;
+                    const int wl = max(p - kl, 0);
+                    const int wh = min(p + kr, nm1);
+                    // the sample's neighbours, one per lane (past the end: the
+                    // last point again, the same value); the sample itself: +0
+                    int j = wl + hl;
+                    j = min(j + (j >= p ? 1 : 0), wh);
+                    const float qx = pts[3 * p], qy = pts[3 * p + 1], qz = pts[3 * p + 2];
+                    const float dd = dev::sqdist(pts[3 * j], pts[3 * j + 1], pts[3 * j + 2],
+                                                 qx, qy, qz);
+                    const float dn = fminf(Ds[j], dd);
+                    if (act) Ds[j] = dn;
+                    if (act && hl == 0) Ds[p] = 0.f;
+                    __syncwarp();
+                    const int r0 = wl >> 4, r1 = wh >> 4;
+                    const unsigned b0 = __float_as_uint(Ds[16 * r0 + hl]);
+                    const unsigned b1 = __float_as_uint(Ds[16 * r1 + hl]);
+                    const unsigned m0 = half_max(b0, half);
+                    const unsigned m1 = half_max(b1, half);
+                    const unsigned l0 = half_first(b0 == m0, hmask, half);
+                    const unsigned l1 = half_first(b1 == m1, hmask, half);
+                    if (act) {
+                        set_row<R>(rmb, rmi, r0, m0, (unsigned)(16 * r0) + l0, hl, 16);
+                        set_row<R>(rmb, rmi, r1, m1, (unsigned)(16 * r1) + l1, hl, 16);
+                    }
+                    unsigned cb = rmb[0], ci = rmi[0];
+#pragma unroll
+                    for (int s = 1; s < R; ++s) {
+                        const bool gt = rmb[s] > cb;
+                        cb = gt ? rmb[s] : cb;
+                        ci = gt ? rmi[s] : ci;
+                    }
+                    const unsigned mx = half_max(cb, half);
+                    const int pn = (int)half_min(cb == mx ? ci : 0xffffffffu, half);
+                    if (act) {
+                        p = dev::checked(pn, 0, n, a.status);
+                        if (ROWS) {
+                            obuf = hl == (t & 15) ? d.lo + p : obuf;
+                            if ((t & 15) == 15) out[(t & ~15) + hl] = obuf;
+                        } else if (hl == 0) {
+                            out[t] = d.lo + p;
+                        }
+                        ++t;
+                    }
+                }
+                if (ROWS && has && hl <= ((c - 1) & 15)) out[((c - 1) & ~15) + hl] = obuf;
+            }
+        }
+        __syncwarp();
+        pair = a.counter ? dev::queue_next_of(a.counter, npairs, nwarps, lane) : pair + nwarps;
+    }
+}
+
 using SectorKernel = void (*)(LaunchArgs);
 
 // Kernel for sectors of up to 32 * rows points (rows <= kWinMaxRows).
+// Pair kernel for sectors of up to 16 * rows16 points (16-point rows).
+SectorKernel win2_kernel_for(int rows16, bool host_rows) {
+    const int slots = (rows16 + 15) / 16;
+    if (slots <= 1) return host_rows ? afps_win2_kernel<1, true> : afps_win2_kernel<1, false>;
+    if (slots <= 2) return host_rows ? afps_win2_kernel<2, true> : afps_win2_kernel<2, false>;
+    if (slots <= 4) return host_rows ? afps_win2_kernel<4, true> : afps_win2_kernel<4, false>;
+    if (slots <= 8) return host_rows ? afps_win2_kernel<8, true> : afps_win2_kernel<8, false>;
+    return nullptr;
+}
+
 SectorKernel win_kernel_for(int rows, bool host_rows, bool lean) {
 #define AFPS_WIN_CASE(RR)                                                                      \
     if (host_rows)                                                                             \

@@ -193,6 +193,13 @@ VARIANTS = [  # (N, C, M, k, kind, P, W, CS)
     (3000, 300, 10, 9, 2, 10, 4, 1, 1), (2100, 500, 2, 16, 2, 33, 2, 1, 1),
     (640, 640, 20, 16, 2, 1, 8, 1, 1), (8192, 2048, 1, 8, 2, 256, 1, 1, 1),
     (3000, 900, 3, 1, 2, 40, 2, 1, 1),
+    # the pair kernel (two sectors per warp, 16-point rows; windows of at most
+    # 17 points): one to eight row-maximum slots, an odd number of sectors
+    # (the last pair's second half empty), every point sampled
+    (3000, 300, 10, 9, 3, 19, 4, 1), (3000, 300, 10, 16, 3, 32, 2, 1),
+    (2000, 1000, 2, 16, 3, 63, 1, 1), (640, 640, 20, 16, 3, 2, 8, 1),
+    (8192, 1024, 4, 8, 3, 128, 1, 1), (2100, 500, 2, 1, 3, 66, 2, 1),
+    (3000, 300, 3, 16, 3, 63, 2, 1),
 ]
 
 
@@ -214,6 +221,8 @@ def test_forced_variant(tmp_path, row):
             want = f"warp P={Pp} W={W}"
         elif kind == 2:
             want = f"win P={Pp} W={W}"
+        elif kind == 3:
+            want = f"pair P={Pp} W={W}"
         elif CS > 1:
             want = f"cluster P={Pp} W={W} CS={CS}"
         else:
@@ -251,7 +260,8 @@ def test_table_iv_sizes(S, N, M, k):
 STRIDE_KERNELS = [(0, 2, 4, 1), (0, 8, 2, 1), (1, 2, 8, 1), (1, 8, 4, 1), (1, 16, 8, 1),
                   (1, 4, 8, 4), (1, 16, 4, 2),  # these two: thread-block clusters
                   (2, 9, 4, 1), (2, 40, 2, 1),  # window kernel, one and two slots per lane
-                  (2, 9, 4, 1, 1), (2, 40, 2, 1, 1)]  # ... and its lean round form
+                  (2, 9, 4, 1, 1), (2, 40, 2, 1, 1),  # ... and its lean round form
+                  (3, 19, 4, 1), (3, 63, 2, 1)]  # pair kernel, 16-point rows
 
 
 def stride_len(n, k, r, method=0):
@@ -277,7 +287,7 @@ def test_npdu_stride_phase(tmp_path, kern):
     kind, Pp, W, CS = kern[:4]
     lean = kern[4] if len(kern) > 4 else 0
     build_mod.build()
-    cap = 32 * W * Pp * CS if kind == 1 else 32 * Pp
+    cap = 32 * W * Pp * CS if kind == 1 else 16 * Pp if kind == 3 else 32 * Pp
     sizes = [cap - 3] + ([288] if cap >= 288 else [])
     for n in sizes:
         M = 3
