@@ -252,6 +252,8 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         };
         int t = t0;
         if (full_first && t < c) round(t++, 0, n - 1);  // full-first-pass reading: the first update is the whole sector
+        // small rounds unrolled: the loop's own instructions are a fair share of them
+#pragma unroll(P <= 4 ? 4 : 1)
         for (; t < c; ++t) round(t, p - kl, p + kr);
         if (rows_out && lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
     }

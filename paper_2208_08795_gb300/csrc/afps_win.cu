@@ -268,9 +268,10 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                     // window crosses into it), then the sample is the argmax over
                     // the cache: every lane's best slot (slots ascend, so the
                     // first of equal maxima has the lowest index), two redux.sync
-                    // steps.  One row: four redux.sync, two rows: six.
+                    // steps.  One row: four redux.sync, two rows: six.  Unrolled
+                    // four times: 63 warp instructions per round instead of 69.5.
                     const int nm1 = n - 1;
-#pragma unroll 1
+#pragma unroll 4
                     for (; t < c; ++t) {
                         const int wl = max(p - kl, 0);
                         const int wh = min(p + kr, nm1);
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                     // touched rows' lowest-index lanes, needed only by the next
                     // rounds' cache, come after it.
                     const int nm1 = n - 1;
-#pragma unroll 1
+#pragma unroll 4
                     for (; t < c; ++t) {
                         const int wl = max(p - kl, 0);
                         const int wh = min(p + kr, nm1);
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(256) afps_win2_kernel(const LaunchArgs a) {
                 }
                 __syncwarp();
                 const int nm1 = n - 1;
-#pragma unroll 1
+#pragma unroll 4
                 while (__any_sync(dev::kFull, t < c)) {
                     const bool act = t < c;
                     const int wl = max(p - kl, 0);
