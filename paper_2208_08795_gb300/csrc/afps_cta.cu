@@ -226,27 +226,33 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             const int tw = min(ts, c - 1);                    // whose window is applied
             const float* G = CLUSTER ? a.xyz + 3 * d.src : pts;  // the sector's points
             bool ok = true;  // D is updated in place and reset if the test fails
+            // Window u = floor((j + kl - p) / q) is the last one starting at or
+            // before point j; window u - 1 may reach j too, no earlier one can
+            // (kl <= kr).  Both candidates' distances are computed and
+            // selected: no branch, one division a point; a point in neither
+            // measures against p (one broadcast load), the clamped index
+            // keeps an empty chunk's loads inside its buffer.
 #pragma unroll
-            for (int i = 0; i < 2 * PP; ++i) {
+            for (int i = 0; i < P; ++i) {
                 const int jl = tid + T * i;
-                if (i < P && jl < cn) {
-                    const int j = c0 + jl;  // sector-local index
-                    const float px = pts[3 * jl], py = pts[3 * jl + 1], pz = pts[3 * jl + 2];
-                    const int y = j - kr - p;
-                    // unsigned divisions: both operands are >= 0 (p <= kl)
-                    const int tlo = y <= 0 ? 0 : (int)divq((uint32_t)(y + q - 1));
-                    const int thi = min(tw - 1, (int)divq((uint32_t)(j + kl - p)));
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        if (tlo + u <= thi) {
-                            const int sj = dev::checked(p + (tlo + u) * q, 0, n, a.status);
-                            const float dd = dev::sqdist(px, py, pz, G[3 * sj], G[3 * sj + 1],
-                                                         G[3 * sj + 2]);
-                            ok = ok && dd < 1e10f;
-                            D[i] = fminf(D[i], dd);
-                        }
-                    }
-                }
+                const int jlc = max(min(jl, cn - 1), 0);
+                const int j = c0 + jlc;  // sector-local index
+                const float px = pts[3 * jlc], py = pts[3 * jlc + 1], pz = pts[3 * jlc + 2];
+                // unsigned division: j + kl - p >= 0 (p <= kl)
+                const int u = (int)divq((uint32_t)(j + kl - p));
+                const int s1 = p + u * q, s0 = s1 - q;
+                const bool in1 = jl < cn && u < tw && j <= s1 + kr;
+                const bool in0 = jl < cn && u >= 1 && u - 1 < tw && j < s1;
+                const int c1 = dev::checked(in1 ? s1 : p, 0, n, a.status);
+                const int c0s = dev::checked(in0 ? s0 : p, 0, n, a.status);
+                const float d1 = dev::sqdist(px, py, pz, G[3 * c1], G[3 * c1 + 1], G[3 * c1 + 2]);
+                const float d0 = dev::sqdist(px, py, pz, G[3 * c0s], G[3 * c0s + 1],
+                                             G[3 * c0s + 2]);
+                ok = ok && (!in1 || d1 < 1e10f) && (!in0 || d0 < 1e10f);
+                float v = D[i];
+                v = in1 ? fminf(v, d1) : v;
+                v = in0 ? fminf(v, d0) : v;
+                D[i] = v;
             }
             bool all = __syncthreads_and(ok) != 0;
             if (CLUSTER) {
@@ -296,19 +302,24 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
                     const bool hit =
                         !NPDU || !a.npdu_skip || (T * i0 + 2 * T - 1 >= wlo && T * i0 <= whi);
                     if (hit) {
-                        float d0, d1;
-                        dev::sqdist2(X2[h], Y2[h], Z2[h], qx2, qy2, qz2, d0, d1);
-                        d0 = fminf(D[i0], d0);
-                        d1 = fminf(D[i0 + 1], d1);
+                        // NPDU: a point outside the window takes x = +inf for
+                        // this update (distance +inf, D kept); the select
+                        // depends on p only, off the critical path.  Padding
+                        // holds D = +0, which no update lowers.
+                        unsigned long long xh = X2[h];
                         if (NPDU) {
                             const int j0 = tid + T * i0, j1 = j0 + T;
                             const unsigned span = (unsigned)(whi - wlo);
-                            D[i0] = ((unsigned)(j0 - wlo) <= span && j0 < cn) ? d0 : D[i0];
-                            D[i0 + 1] = ((unsigned)(j1 - wlo) <= span && j1 < cn) ? d1 : D[i0 + 1];
-                        } else {
-                            D[i0] = d0;
-                            D[i0 + 1] = d1;
+                            float x0, x1;
+                            dev::unpack2(xh, x0, x1);
+                            x0 = (unsigned)(j0 - wlo) <= span ? x0 : __int_as_float(0x7f800000);
+                            x1 = (unsigned)(j1 - wlo) <= span ? x1 : __int_as_float(0x7f800000);
+                            xh = dev::pack2(x0, x1);
                         }
+                        float d0, d1;
+                        dev::sqdist2(xh, Y2[h], Z2[h], qx2, qy2, qz2, d0, d1);
+                        D[i0] = fminf(D[i0], d0);
+                        D[i0 + 1] = fminf(D[i0 + 1], d1);
                     }
                     if (h == 0) {  // row 0 starts the thread's scan
                         best = D[0];

@@ -232,6 +232,10 @@ __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
     return r;
 }
 
+__device__ __forceinline__ void unpack2(unsigned long long r, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+
 // Squared distances of two points (packed x, y, z) to q (q broadcast in both
 // lanes): the same separately rounded (dx*dx + dy*dy) + dz*dz as sqdist.  The
 // differences and squares use packed f32x2 instructions; the two sums are

@@ -152,26 +152,31 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
             const int tn = min(ts, c);                        // of them emitted
             const int tw = min(ts, c - 1);                    // whose window is applied
             bool ok = true;  // D is updated in place and reset if the test fails
+            // Window u = floor((j + kl - p) / q) is the last one starting at or
+            // before point j (p <= kl, so the quotient is of a non-negative
+            // number); window u - 1 may reach j too, no earlier one can
+            // (kl <= kr).  Both candidates' distances are computed from
+            // clamped indices and selected: no branch, one division a point.
 #pragma unroll
-            for (int i = 0; i < 2 * PP; ++i) {
+            for (int i = 0; i < P; ++i) {
                 const int j = lane + 32 * i;
-                if (i < P && j < n) {
-                    const float px = pts[3 * j], py = pts[3 * j + 1], pz = pts[3 * j + 2];
-                    const int y = j - kr - p;
-                    // unsigned divisions: both operands are >= 0 (p <= kl)
-                    const int tlo = y <= 0 ? 0 : (int)divq((uint32_t)(y + q - 1));
-                    const int thi = min(tw - 1, (int)divq((uint32_t)(j + kl - p)));
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        if (tlo + u <= thi) {
-                            const int sj = dev::checked(p + (tlo + u) * q, 0, n, a.status);
-                            const float dd = dev::sqdist(px, py, pz, pts[3 * sj],
-                                                         pts[3 * sj + 1], pts[3 * sj + 2]);
-                            ok = ok && dd < 1e10f;
-                            D[i] = fminf(D[i], dd);
-                        }
-                    }
-                }
+                const int jc = min(j, n - 1);
+                const float px = pts[3 * jc], py = pts[3 * jc + 1], pz = pts[3 * jc + 2];
+                const int u = (int)divq((uint32_t)(jc + kl - p));
+                const int s1 = p + u * q, s0 = s1 - q;
+                const bool in1 = j < n && u < tw && jc <= s1 + kr;
+                const bool in0 = j < n && u >= 1 && u - 1 < tw && jc < s1;
+                const int c1 = dev::checked(in1 ? s1 : jc, 0, n, a.status);
+                const int c0 = dev::checked(in0 ? s0 : jc, 0, n, a.status);
+                const float d1 = dev::sqdist(px, py, pz, pts[3 * c1], pts[3 * c1 + 1],
+                                             pts[3 * c1 + 2]);
+                const float d0 = dev::sqdist(px, py, pz, pts[3 * c0], pts[3 * c0 + 1],
+                                             pts[3 * c0 + 2]);
+                ok = ok && (!in1 || d1 < 1e10f) && (!in0 || d0 < 1e10f);
+                float v = D[i];
+                v = in1 ? fminf(v, d1) : v;
+                v = in0 ? fminf(v, d0) : v;
+                D[i] = v;
             }
             if (__all_sync(dev::kFull, ok)) {
                 if (rows_out) {
@@ -211,18 +216,25 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
                     const bool hit = !NPDU || PP == 1 || !a.npdu_skip ||
                                      (32 * i0 + 63 >= wl && 32 * i0 <= wh);
                     if (hit) {
-                        float d0, d1;
-                        dev::sqdist2(X2[h], Y2[h], Z2[h], qx2, qy2, qz2, d0, d1);
-                        d0 = fminf(D[i0], d0);
-                        d1 = fminf(D[i0 + 1], d1);
+                        // NPDU: a point outside the window takes x = +inf for
+                        // this update, so its distance is +inf and the min
+                        // keeps D; inside, the arithmetic is unchanged.  The
+                        // select depends only on p, not on the sample's
+                        // coordinates, so it stays off the round's critical
+                        // path.  (Padding holds D = +0, which no update lowers.)
+                        unsigned long long xh = X2[h];
                         if (NPDU) {
                             const int j0 = lane + 32 * i0, j1 = j0 + 32;
-                            D[i0] = (((unsigned)j0 - wlo) <= wspan && j0 < n) ? d0 : D[i0];
-                            D[i0 + 1] = (((unsigned)j1 - wlo) <= wspan && j1 < n) ? d1 : D[i0 + 1];
-                        } else {
-                            D[i0] = d0;
-                            D[i0 + 1] = d1;
+                            float x0, x1;
+                            dev::unpack2(xh, x0, x1);
+                            x0 = ((unsigned)j0 - wlo) <= wspan ? x0 : __int_as_float(0x7f800000);
+                            x1 = ((unsigned)j1 - wlo) <= wspan ? x1 : __int_as_float(0x7f800000);
+                            xh = dev::pack2(x0, x1);
                         }
+                        float d0, d1;
+                        dev::sqdist2(xh, Y2[h], Z2[h], qx2, qy2, qz2, d0, d1);
+                        D[i0] = fminf(D[i0], d0);
+                        D[i0 + 1] = fminf(D[i0 + 1], d1);
                     }
                     if (h == 0) {  // row 0 starts the lane's scan
                         best = D[0];
