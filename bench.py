@@ -451,9 +451,9 @@ def kernel_source_hash() -> str:
 # DRAM traffic of the headline kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch over the ragged batch), valid only for
 # the kernel sources it was taken on (their hash); otherwise reported as null.
-NCU_TRAFFIC = {"source_hash": "aefaf0a6b6829ee2", "bytes_per_launch": 54907904}
+NCU_TRAFFIC = {"source_hash": "6a1f5787c31fdc46", "bytes_per_launch": 54936064}
 # warp instructions of one headline launch (ncu smsp__inst_executed.sum), same rule
-NCU_INST = {"source_hash": "aefaf0a6b6829ee2", "warp_inst_per_launch": 69117257}
+NCU_INST = {"source_hash": "6a1f5787c31fdc46", "warp_inst_per_launch": 57026726}
 
 
 # ------------------------------------------------------------------ other configs
