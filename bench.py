@@ -381,6 +381,27 @@ def time_e2e_stream(sampler, xyz, ba, steps: int, warmup: int, expect):
     return ms, xyz.nbytes, ba.total_out * 4
 
 
+def c2c_copy_gbs(nbytes: int, reps: int = 10) -> float:
+    """Host-to-device bandwidth of the C2C link as the copy engine sees it:
+    page-locked host memory to device memory, one cudaMemcpyAsync of nbytes
+    per repetition, CUDA events on the stream (the ceiling of the end-to-end
+    path, whose kernels read the same bytes over the same link)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        d.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        d.copy_(h, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    return nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
 def time_e2e_sync(sampler, h_xyz, ba, h_out, steps: int, warmup: int):
     """One synchronous afps_sample_batched_host call at a time (page-locked
     buffers): the latency a caller sees for a single batch."""
@@ -775,6 +796,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     barrier()
     e2e_call_ms = max_over_ranks(float(np.mean(ts)), world, dev)
     e2e_ok = bool(np.array_equal(h_out, head_out))
+    link_gbs = c2c_copy_gbs(int(h2d_bytes))
 
     # ---------------------------------------------------------- object batch (config 2)
     obj = object_batch_section(args, sampler, dev, world, barrier) if args.configs else None
@@ -871,7 +893,15 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
                        "host memory over the C2C link; inputs rotating over copies larger "
                        "than L2, one output per step), one stream, one synchronisation, host "
                        "clock; every output checked",
-                "sync_call_ms": e2e_call_ms, "sync_call_matches_device_path": e2e_ok},
+                "sync_call_ms": e2e_call_ms, "sync_call_matches_device_path": e2e_ok,
+                "link": {"bound": "c2c", "unit": "GB/s",
+                         "achieved": (h2d_bytes + d2h_bytes) / (e2e_ms / 1e3) / 1e9,
+                         "peak": link_gbs,
+                         "frac": (h2d_bytes + d2h_bytes) / (e2e_ms / 1e3) / 1e9 / link_gbs,
+                         "how": "bytes moved over the C2C link per step (points in, indices "
+                                "out) / the end-to-end step; peak: a cudaMemcpyAsync of the "
+                                "step's input bytes from page-locked memory to the device, "
+                                "measured in this run"}},
         "object_batch": obj,
         "serving": serving_stats,
         "large_clouds": large,
