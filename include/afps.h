@@ -334,7 +334,12 @@ int afps_save_tuning(afps_ctx* ctx, const char* path);
  * Describe the kernel variant the planner would use for n_items sectors of
  * at most n_sector points and c_sector samples (for afps_sample, n_items is
  * M): writes a short text (kind, points per thread, warps per CTA, cluster
- * size) into buf.  Returns the text length or a negative error.
+ * size) into buf.  Kinds: "warp" (a warp per sector, P points a lane),
+ * "cta" / "cluster" (a CTA or a thread-block cluster of CS CTAs per sector),
+ * "win" (NPDU window kernel, P rows of 32 points per warp buffer; "lean":
+ * the round form with the fewest instructions) and "pair" (two NPDU
+ * sectors per warp, P rows of 16 points per half).  "skip" marks row skips
+ * outside the NPDU window.  Returns the text length or a negative error.
  */
 int afps_describe_plan(afps_ctx* ctx, int64_t n_sector, int32_t c_sector,
                        int32_t npdu_window, int32_t n_items, char* buf, int32_t buf_len);
