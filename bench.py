@@ -475,6 +475,9 @@ def kernel_source_hash() -> str:
 NCU_TRAFFIC = {"source_hash": "6a1f5787c31fdc46", "bytes_per_launch": 54936064}
 # warp instructions of one headline launch (ncu smsp__inst_executed.sum), same rule
 NCU_INST = {"source_hash": "6a1f5787c31fdc46", "warp_inst_per_launch": 57026726}
+# shared-memory wavefronts of one headline launch (ncu
+# l1tex__data_pipe_lsu_wavefronts_mem_shared.sum; 128 bytes each), same rule
+NCU_SMEM = {"source_hash": "6a1f5787c31fdc46", "wavefronts_per_launch": 7640458}
 
 
 # ------------------------------------------------------------------ other configs
@@ -501,12 +504,19 @@ def large_clouds(sampler, flush, dev, steps: int):
             out = torch.empty(ba.total_out, dtype=torch.int32, device=dev)
             ms, p99 = time_batch(sampler, x, ba, out, steps, 3, flush)
             plan = sampler.describe_plan(-(-N // M), -(-(N // 4) // M), k, M)
+            rounds = -(-(N // 4) // M)  # iterations of the longest sector's chain
             rows.append({"N": N, "C": N // 4, "M": M, "k": k, "ms": round(ms, 4),
-                         "p99_ms": round(p99, 4), "variant": plan})
+                         "p99_ms": round(p99, 4), "variant": plan,
+                         "iterations_per_sector": rounds,
+                         "ns_per_iteration": round(ms * 1e6 / rounds, 1)})
     for r in rows:  # speedup over plain FPS at equal N and C
         base = next(b for b in rows if b["N"] == r["N"] and b["M"] == 1)
         r["speedup_vs_fps"] = round(base["ms"] / r["ms"], 2)
-    return {"workload": "slab clouds 8K/16K/32K, C=N/4", "runs": rows}
+    return {"workload": "slab clouds 8K/16K/32K, C=N/4", "runs": rows,
+            "latency": "few sectors: each launch is the latency of its longest sector's chain "
+                       "of iterations, so each run also gives the step time per iteration "
+                       "(ns_per_iteration; cycles_per_iteration at the median SM clock), "
+                       "stage-in and launch included"}
 
 
 # Table IV of the paper: Transmuter (gem5) seconds, for context only
@@ -821,6 +831,9 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
     achieved = hbm_bytes / (ms / 1e3) / 1e9
     evals, compares = npdu_work(head_out, ba)
     sm_mhz = clk["sm_mhz"] or 2070.0
+    if large:
+        for r in large["runs"]:
+            r["cycles_per_iteration"] = round(r["ns_per_iteration"] * sm_mhz / 1e3)
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12  # FP32 lanes x clock, Tops/s
@@ -835,6 +848,14 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
         "warp_inst_per_launch": inst,
         "how": f"ncu smsp__inst_executed.sum of one launch / the launch's duration; peak = "
                f"{n_sm} SMs x 4 schedulers x the median SM clock under load"}
+    waves = NCU_SMEM["wavefronts_per_launch"] if NCU_SMEM["source_hash"] == src else None
+    smem_peak = n_sm * 128 * sm_mhz * 1e6 / 1e9  # 128 bytes a clock per SM, GB/s
+    smem = None if waves is None else {
+        "bound": "smem", "achieved": waves * 128 / kernel_s / 1e9, "peak": smem_peak,
+        "unit": "GB/s", "frac": waves * 128 / kernel_s / 1e9 / smem_peak,
+        "wavefronts_per_launch": waves,
+        "how": f"ncu l1tex__data_pipe_lsu_wavefronts_mem_shared.sum of one launch x 128 bytes / "
+               f"the launch's duration; peak = {n_sm} SMs x 128 bytes x the median SM clock"}
     plan_desc = sampler.describe_batched(ba)
 
     sum_c = int(ba.total_out)
@@ -881,6 +902,7 @@ def run_gpu(args, rank: int, world: int, local: int) -> int:
                             "sample written) / the step's duration (timed region / K on the "
                             "launching stream; one kernel launch per step)"},
         "roofline_issue": issue,
+        "roofline_smem": smem,
         "roofline_alu": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
                          "fp32_ops_per_launch": 9 * evals + compares,
