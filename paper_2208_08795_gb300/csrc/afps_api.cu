@@ -86,6 +86,9 @@ struct ClassPlan {
     // every cloud of the class has the same N, C, M, window and start, and
     // they are stored back to back: the kernel computes its items
     bool uniform = false;
+    // uniform clouds at scattered offsets: their (point, output) offset pairs
+    // start at pair cloud_first of BatchPlan::clouds (-1: back to back)
+    int64_t cloud_first = -1;
     bool merged = false;  // several shape classes in one launch (window kernels)
     bool narrow = true;   // every item's window has at most 17 points, read literally
     afps::SingleCloud single{};
@@ -95,6 +98,7 @@ struct ClassPlan {
 struct BatchPlan {
     std::vector<ItemDesc> items;  // class-major
     std::vector<ClassPlan> classes;
+    std::vector<int64_t> clouds;  // (point offset, output offset) pairs of scattered classes
 };
 
 struct GraphEntry {
@@ -542,7 +546,7 @@ void merge_window_classes(BatchPlan& plan) {
 int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t* n_pts,
                const int64_t* out_begin, const int64_t* out_cap, const int32_t* C,
                const int32_t* M, const int32_t* K, const int64_t* start, BatchPlan& plan,
-               const uint32_t* method = nullptr, bool merge = true) {
+               const uint32_t* method = nullptr, bool merge = true, bool scatter = false) {
     if (B < 1 || !pt_begin || !n_pts || !out_begin || !out_cap || !C || !M || !K || !start)
         return fail(ctx, AFPS_ERR_INVALID_ARG, "batched call: B < 1 or a NULL host array");
     struct Member {
@@ -577,6 +581,7 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
     }
     plan.items.clear();
     plan.classes.clear();
+    plan.clouds.clear();
     for (auto& g : groups) {
         ClassPlan cp;
         cp.npdu = g.first.first == 1;
@@ -586,22 +591,33 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
             const Member& m0 = g.second.front();
             const int32_t b0 = m0.b;
             const uint32_t meth0 = method ? method[b0] : 0u;
-            bool same = true;
+            bool same = true;    // every cloud of the class has the same shape ...
+            bool packed = true;  // ... and they lie back to back
             for (size_t j = 0; j < g.second.size() && same; ++j) {
                 const Member& m = g.second[j];
                 const int32_t b = m.b;
                 same = n_pts[b] == n_pts[b0] && C[b] == C[b0] && M[b] == M[b0] &&
                        K[b] == K[b0] && (method ? method[b] : 0u) == meth0 &&
-                       m.chk.start_r == m0.chk.start_r &&
-                       pt_begin[b] == pt_begin[b0] + (int64_t)j * n_pts[b0] &&
-                       out_begin[b] == out_begin[b0] + (int64_t)j * C[b0];
+                       m.chk.start_r == m0.chk.start_r;
+                packed = packed && pt_begin[b] == pt_begin[b0] + (int64_t)j * n_pts[b0] &&
+                         out_begin[b] == out_begin[b0] + (int64_t)j * C[b0];
             }
-            if (same && n_pts[b0] <= INT32_MAX) {
+            // scattered equal clouds: one offset pair per cloud instead of M
+            // table entries (worth it from two clouds on)
+            const bool scattered = scatter && !packed && g.second.size() >= 2;
+            if (same && (packed || scattered) && n_pts[b0] <= INT32_MAX) {
                 ItemDesc w{};
                 window_sides(K[b0], meth0, w);
                 cp.uniform = true;
-                cp.single.pt_off = pt_begin[b0];
-                cp.single.out_off = out_begin[b0];
+                if (scattered) {
+                    cp.cloud_first = (int64_t)(plan.clouds.size() / 2);
+                    for (const Member& m : g.second) {
+                        plan.clouds.push_back(pt_begin[m.b]);
+                        plan.clouds.push_back(out_begin[m.b]);
+                    }
+                }
+                cp.single.pt_off = scattered ? 0 : pt_begin[b0];
+                cp.single.out_off = scattered ? 0 : out_begin[b0];
                 cp.single.N = (int32_t)n_pts[b0];
                 cp.single.C = C[b0];
                 cp.single.M = M[b0];
@@ -658,15 +674,19 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
 // the next slot of the pinned upload ring (waiting only for that slot's
 // previous copy, kStageSlots uploads ago).  Device work that used the
 // workspace earlier, possibly on another stream, is ordered before the copy.
-int upload(afps_ctx* ctx, DevBuf& dst, const void* src, size_t bytes, cudaStream_t stream) {
+// A second part (src2, bytes2) goes right after the first in the same copy.
+int upload(afps_ctx* ctx, DevBuf& dst, const void* src, size_t bytes, cudaStream_t stream,
+           const void* src2 = nullptr, size_t bytes2 = 0) {
     const int s = ctx->stage_next;
     ctx->stage_next = (s + 1) % kStageSlots;
+    const size_t total = bytes + bytes2;
     AFPS_CUDA(ctx, cudaEventSynchronize(ctx->stage_ev[s]));
-    AFPS_CUDA(ctx, grow(ctx, ctx->stage[s], bytes));
-    AFPS_CUDA(ctx, grow(ctx, dst, bytes));
-    memcpy(ctx->stage[s].p, src, bytes);
+    AFPS_CUDA(ctx, grow(ctx, ctx->stage[s], total));
+    AFPS_CUDA(ctx, grow(ctx, dst, total));
+    if (bytes) memcpy(ctx->stage[s].p, src, bytes);
+    if (bytes2) memcpy(static_cast<char*>(ctx->stage[s].p) + bytes, src2, bytes2);
     AFPS_CUDA(ctx, cudaStreamWaitEvent(stream, ctx->ev_done, 0));
-    AFPS_CUDA(ctx, cudaMemcpyAsync(dst.p, ctx->stage[s].p, bytes, cudaMemcpyHostToDevice, stream));
+    AFPS_CUDA(ctx, cudaMemcpyAsync(dst.p, ctx->stage[s].p, total, cudaMemcpyHostToDevice, stream));
     AFPS_CUDA(ctx, cudaEventRecord(ctx->stage_ev[s], stream));
     return AFPS_OK;
 }
@@ -693,9 +713,10 @@ int build_plan_consecutive(afps_ctx* ctx, const int64_t* pt_off, int32_t B, cons
 // Run a plan out of the context's shared workspace (no graph).
 int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* d_out,
              cudaStream_t stream, bool host_resident = false) {
-    const size_t bytes = plan.items.size() * sizeof(ItemDesc);
-    bool table = false;  // some class reads the item table
-    bool queue = false;  // some class uses a work-queue counter
+    const size_t bytes = plan.items.size() * sizeof(ItemDesc);  // a multiple of 16
+    const size_t cbytes = plan.clouds.size() * sizeof(int64_t);
+    bool table = cbytes > 0;  // some class reads the item table or cloud offsets
+    bool queue = false;       // some class uses a work-queue counter
     for (const ClassPlan& cp : plan.classes) {
         table = table || !cp.uniform;
         queue = queue || uses_queue(cp.v, cp.count);
@@ -706,16 +727,21 @@ int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* 
         if (grc != AFPS_OK) return grc;
     }
     if (table) {  // the upload waits for the workspace's last use
-        int urc = upload(ctx, ctx->items, plan.items.data(), bytes, stream);
+        int urc = upload(ctx, ctx->items, plan.items.data(), bytes, stream, plan.clouds.data(),
+                         cbytes);
         if (urc != AFPS_OK) return urc;
     }
     const ItemDesc* d_items = static_cast<const ItemDesc*>(ctx->items.p);
+    const int64_t* d_clouds =
+        reinterpret_cast<const int64_t*>(static_cast<const char*>(ctx->items.p) + bytes);
     unsigned int* counters = static_cast<unsigned int*>(ctx->counters.p);
     for (size_t i = 0; i < plan.classes.size(); ++i) {
         const ClassPlan& cp = plan.classes[i];
+        afps::SingleCloud sc = cp.single;
+        if (cp.cloud_first >= 0) sc.cloud_off = d_clouds + 2 * cp.cloud_first;
         int rc = launch_class(ctx, cp.v, cp.npdu, cp.uniform ? nullptr : d_items + cp.first,
                               cp.count, counters + i, d_xyz, d_out, stream, host_resident,
-                              cp.run());
+                              cp.uniform ? &sc : nullptr);
         if (rc != AFPS_OK) return rc;
     }
     // the workspace's last use, for ordering its next upload (none used: no record)
@@ -1049,7 +1075,8 @@ int sample_scattered(afps_ctx* ctx, const float* xyz, int32_t B, const int64_t* 
     std::vector<int64_t> cap((size_t)std::max(B, 1));
     for (int32_t b = 0; b < B; ++b) cap[b] = C[b];
     BatchPlan plan;
-    int rc = build_plan(ctx, B, pt_begin, n_pts, out_begin, cap.data(), C, M, K, start, plan);
+    int rc = build_plan(ctx, B, pt_begin, n_pts, out_begin, cap.data(), C, M, K, start, plan,
+                        nullptr, true, true);
     if (rc != AFPS_OK) return rc;
     return run_plan(ctx, plan, xyz, out, stream);
 }

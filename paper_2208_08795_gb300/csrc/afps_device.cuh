@@ -279,9 +279,11 @@ struct SmallDiv {
 };
 
 // Item `i` of a launch: from the device table, or computed from the
-// parameters of a run of equal clouds stored back to back (cloud i / M,
-// sector i % M) with the sector rule floor(s*N/M), floor(s*C/M).  Computing
-// it saves the dependent load of a table entry ahead of the stage-in.
+// parameters of a run of equal clouds (cloud i / M, sector i % M) with the
+// sector rule floor(s*N/M), floor(s*C/M), the clouds stored back to back or
+// at the offsets of the `cloud_off` pairs.  Computing it saves the dependent
+// load of a table entry ahead of the stage-in (back to back: no load at all),
+// and the host builds one pair per cloud instead of M table entries.
 __device__ __forceinline__ ItemDesc load_item(const LaunchArgs& a, int i) {
     if (a.items) return a.items[i];
     const SingleCloud& s = a.single;
@@ -306,8 +308,14 @@ __device__ __forceinline__ ItemDesc load_item(const LaunchArgs& a, int i) {
         o1 = divM((sec + 1) * (uint32_t)s.C);
     }
     ItemDesc d;
-    d.src = s.pt_off + (int64_t)b * s.N + lo;
-    d.dst = s.out_off + (int64_t)b * s.C + o0;
+    if (s.cloud_off) {
+        const longlong2 off = reinterpret_cast<const longlong2*>(s.cloud_off)[b];
+        d.src = off.x + lo;
+        d.dst = off.y + o0;
+    } else {
+        d.src = s.pt_off + (int64_t)b * s.N + lo;
+        d.dst = s.out_off + (int64_t)b * s.C + o0;
+    }
     d.n = (int32_t)(hi - lo);
     d.c = (int32_t)(o1 - o0);
     d.first = s.start_r < d.n - 1 ? s.start_r : d.n - 1;

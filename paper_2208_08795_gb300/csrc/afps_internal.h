@@ -38,6 +38,10 @@ struct SingleCloud {
     int32_t start_r;        // offset of start_idx inside its own sector
     int32_t wide;           // M * N >= 2^32: sector bounds in 64-bit arithmetic
     uint64_t m_magic;       // div_magic(M): x / M = high 64 bits of x * m_magic (x < 2^32)
+    // Equal clouds at arbitrary offsets: a device array of (point offset,
+    // output offset) pairs, one per cloud in item order, replacing
+    // pt_off + b N and out_off + b C; nullptr for clouds stored back to back.
+    const int64_t* cloud_off;
 };
 
 // Multiplier for unsigned division of 32-bit numerators by d >= 2:
