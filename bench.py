@@ -656,7 +656,7 @@ def serving_sweep(sampler, seconds_per_rate: float = 0.25):
         import torch
         pinned = [torch.from_numpy(f).pin_memory().numpy() for f in frames]
         prow = []
-        for i, rate in enumerate(SERVING_RATES[2:] + [64000.0, 128000.0]):
+        for i, rate in enumerate(SERVING_RATES[2:] + [64000.0, 128000.0, 256000.0]):
             n = int(min(2000, max(100, rate * seconds_per_rate)))
             r = serving.poisson_run(srv, pinned, rate, n, seed=10 + i, pinned=True)
             prow.append({k: round(v, 3) if isinstance(v, float) else v for k, v in r.items()})

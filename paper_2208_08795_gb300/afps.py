@@ -555,20 +555,40 @@ def afps_server_destroy(srv) -> None:
     load().afps_server_destroy(srv)
 
 
+# afps_server_result as a NumPy record (the pointer as an address), so that a
+# poll reads all its results' fields at once
+_RESULT_DTYPE = np.dtype({
+    "names": ["tag", "status", "n_levels", "count", "indices", "submit_ms", "admit_ms", "done_ms"],
+    "formats": ["<u8", "<i4", "<i4", ("<i4", (AFPS_SERVER_MAX_LEVELS,)), "<u8", "<f8", "<f8",
+                "<f8"],
+    "offsets": [getattr(afps_server_result, f).offset for f in
+                ("tag", "status", "n_levels", "count", "indices", "submit_ms", "admit_ms",
+                 "done_ms")],
+    "itemsize": ctypes.sizeof(afps_server_result)})
+
+
 class ServerResult:
     """One finished request: per-level frame indices and times.  With
     copy=False the indices are a view of the runtime's page-locked result
-    slot, valid until the next poll."""
+    slot, valid until the next poll (made when first read)."""
 
-    def __init__(self, r: afps_server_result, copy: bool = True):
-        self.tag = int(r.tag)
-        self.status = int(r.status)
-        self._counts = list(r.count)[:r.n_levels]
+    __slots__ = ("tag", "status", "_counts", "_addr", "_indices", "submit_ms", "admit_ms",
+                 "done_ms")
+
+    def __init__(self, tag, status, counts, addr, submit_ms, admit_ms, done_ms, copy=True):
+        self.tag, self.status, self._counts, self._addr = tag, status, counts, addr
+        self.submit_ms, self.admit_ms, self.done_ms = submit_ms, admit_ms, done_ms
+        self._indices = self._view().copy() if copy else None
+
+    def _view(self):
         total = sum(self._counts)
-        addr = ctypes.cast(r.indices, ctypes.c_void_p).value
-        flat = np.frombuffer((ctypes.c_int32 * total).from_address(addr), dtype=np.int32)
-        self.indices = flat.copy() if copy else flat
-        self.submit_ms, self.admit_ms, self.done_ms = r.submit_ms, r.admit_ms, r.done_ms
+        return np.frombuffer((ctypes.c_int32 * total).from_address(self._addr), dtype=np.int32)
+
+    @property
+    def indices(self):
+        if self._indices is None:
+            self._indices = self._view()
+        return self._indices
 
     @property
     def levels(self):
@@ -595,6 +615,7 @@ class Server:
         self.sampler = sampler
         self.srv = afps_server_create(sampler.ctx, cfg, stream)
         self._buf = (afps_server_result * 256)()
+        self._rows = np.frombuffer(self._buf, dtype=_RESULT_DTYPE)
 
     def close(self):
         if self.srv:
@@ -633,7 +654,15 @@ class Server:
         n = afps_server_poll(self.srv, self._buf, len(self._buf))
         if n < 0:
             raise AfpsError(n, "afps_server_poll failed")
-        return [ServerResult(self._buf[i], copy) for i in range(n)]
+        if n == 0:
+            return []
+        rows = self._rows[:n]
+        nl = rows["n_levels"].tolist()
+        counts = [c[:k] for c, k in zip(rows["count"].tolist(), nl)]
+        return [ServerResult(*f, copy=copy) for f in
+                zip(rows["tag"].tolist(), rows["status"].tolist(), counts,
+                    rows["indices"].tolist(), rows["submit_ms"].tolist(),
+                    rows["admit_ms"].tolist(), rows["done_ms"].tolist())]
 
     def stats(self):
         q, f, u = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

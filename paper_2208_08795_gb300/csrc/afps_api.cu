@@ -641,9 +641,11 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
             const int64_t N = n_pts[b];
             cp.n_max = std::max(cp.n_max, m.chk.n_max);
             cp.c_max = std::max(cp.c_max, m.chk.c_max);
+            int64_t hi = 0, o1 = 0;  // each sector's end is the next one's start
             for (int64_t s = 0; s < M[b]; ++s) {
-                const int64_t lo = sec_lo(N, M[b], s), hi = sec_lo(N, M[b], s + 1);
-                const int64_t o0 = sec_off(C[b], M[b], s), o1 = sec_off(C[b], M[b], s + 1);
+                const int64_t lo = hi, o0 = o1;
+                hi = sec_lo(N, M[b], s + 1);
+                o1 = sec_off(C[b], M[b], s + 1);
                 ItemDesc d{};
                 d.src = pt_begin[b] + lo;
                 d.dst = out_begin[b] + o0;
@@ -657,12 +659,21 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
             }
         }
         cp.count = plan.items.size() - cp.first;
-        // largest work first (longest-processing-time order for the queue)
+        // largest work first (longest-processing-time order for the queue),
+        // equal costs in table order; the keys are sorted, not the entries
         const bool npdu = cp.npdu;
-        std::stable_sort(plan.items.begin() + cp.first, plan.items.end(),
-                         [npdu](const ItemDesc& x, const ItemDesc& y) {
-                             return item_cost(x, npdu) > item_cost(y, npdu);
-                         });
+        std::vector<std::pair<int64_t, uint32_t>> key(cp.count);
+        bool ordered = true;
+        for (size_t j = 0; j < cp.count; ++j) {
+            key[j] = {-item_cost(plan.items[cp.first + j], npdu), (uint32_t)j};
+            ordered = ordered && (j == 0 || key[j].first >= key[j - 1].first);
+        }
+        if (!ordered) {
+            std::sort(key.begin(), key.end());
+            std::vector<ItemDesc> sorted(cp.count);
+            for (size_t j = 0; j < cp.count; ++j) sorted[j] = plan.items[cp.first + key[j].second];
+            std::copy(sorted.begin(), sorted.end(), plan.items.begin() + cp.first);
+        }
         cp.v = choose_variant(ctx, cp.npdu, cp.n_max, cp.c_max, cp.count, cp.narrow);
         plan.classes.push_back(cp);
     }

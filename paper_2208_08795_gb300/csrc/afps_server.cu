@@ -24,6 +24,8 @@
 #include <deque>
 #include <map>
 #include <memory>
+#include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/afps.h"
@@ -133,6 +135,9 @@ struct afps_server {
     std::vector<std::unique_ptr<Request>> handed;  // returned by the last poll
     std::deque<cudaEvent_t> step_events;           // steps in flight
     std::vector<cudaEvent_t> event_pool;
+    // completion events shared by the requests that finished in one step:
+    // the number of requests still holding each
+    std::unordered_map<cudaEvent_t, int> ev_refs;
     std::chrono::steady_clock::time_point t0;
     double now() const {
         return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
@@ -170,21 +175,40 @@ void give_event(afps_server* s, cudaEvent_t e) {
     if (e) s->event_pool.push_back(e);
 }
 
+// A request lets go of its completion event: a shared one returns to the
+// pool with its last holder.
+void drop_event(afps_server* s, cudaEvent_t e) {
+    auto it = s->ev_refs.find(e);
+    if (it != s->ev_refs.end() && --it->second > 0) return;
+    if (it != s->ev_refs.end()) s->ev_refs.erase(it);
+    give_event(s, e);
+}
+
 // Finished requests: the device work of their last step has completed.
 void reap(afps_server* s) {
+    // requests that finished in one step share its event: query each once
+    cudaEvent_t last = nullptr;
+    bool last_done = false;
+    auto complete = [&](cudaEvent_t e) {
+        if (e != last) {
+            last = e;
+            last_done = cudaEventQuery(e) == cudaSuccess;
+        }
+        return last_done;
+    };
     for (auto& r : s->active) {
-        if (r && r->state == COMPLETING && cudaEventQuery(r->done_ev) == cudaSuccess) {
+        if (r && r->state == COMPLETING && complete(r->done_ev)) {
             r->state = DONE;
             r->t_done = s->now();
             s->arena->release(r->block);
             r->block = Block{};
-            give_event(s, r->done_ev);
+            drop_event(s, r->done_ev);
             r->done_ev = nullptr;
             s->done.push_back(std::move(r));
-        } else if (r && r->state == CANCELLED && cudaEventQuery(r->done_ev) == cudaSuccess) {
+        } else if (r && r->state == CANCELLED && complete(r->done_ev)) {
             // no launched step uses its memory any more: drop it
             s->arena->release(r->block);
-            give_event(s, r->done_ev);
+            drop_event(s, r->done_ev);
             s->free_slots.push_back(r->slot);
             r.reset();
         }
@@ -512,19 +536,14 @@ int afps_server_step(afps_server* s) {
         }
         if (fin) {
             if (cudaEventRecord(fin, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
-            // each finishing request keeps its own handle on the step's completion
-            bool first = true;
+            // the finishing requests share the step's completion event
+            int holders = 0;
             for (Request* r : run) {
                 if (r->state != COMPLETING || r->done_ev) continue;
-                if (first) {
-                    r->done_ev = fin;
-                    first = false;
-                } else {
-                    cudaEvent_t e = take_event(s);
-                    if (!e || cudaEventRecord(e, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
-                    r->done_ev = e;
-                }
+                r->done_ev = fin;
+                ++holders;
             }
+            s->ev_refs[fin] = holders;
         }
         advanced += (int)run.size();
     }
@@ -543,9 +562,9 @@ int afps_server_poll(afps_server* s, afps_server_result* out, int32_t max_result
     s->handed.clear();
     reap(s);
     int n = 0;
-    while (n < max_results && !s->done.empty()) {
-        std::unique_ptr<Request> r = std::move(s->done.front());
-        s->done.erase(s->done.begin());
+    size_t k = 0;  // results taken from the front of `done`
+    while (n < max_results && k < s->done.size()) {
+        std::unique_ptr<Request> r = std::move(s->done[k++]);
         afps_server_result& o = out[n++];
         memset(&o, 0, sizeof(o));
         o.tag = r->tag;
@@ -558,6 +577,7 @@ int afps_server_poll(afps_server* s, afps_server_result* out, int32_t max_result
         o.done_ms = r->t_done;
         s->handed.push_back(std::move(r));
     }
+    s->done.erase(s->done.begin(), s->done.begin() + (std::ptrdiff_t)k);
     return n;
 }
 
@@ -574,8 +594,10 @@ double afps_server_clock_ms(const afps_server* s) { return s ? s->now() : 0.0; }
 void afps_server_destroy(afps_server* s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    std::unordered_set<cudaEvent_t> held;  // shared events are destroyed once
     for (auto& r : s->active)
-        if (r && r->done_ev) cudaEventDestroy(r->done_ev);
+        if (r && r->done_ev) held.insert(r->done_ev);
+    for (cudaEvent_t e : held) cudaEventDestroy(e);
     for (cudaEvent_t e : s->step_events) cudaEventDestroy(e);
     for (auto& pp : s->pool_pending) cudaEventDestroy(pp.first);
     if (s->pool_base) cudaFreeHost(s->pool_base);
