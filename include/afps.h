@@ -459,7 +459,14 @@ typedef struct afps_server_result {
 } afps_server_result;
 
 /* Create a server on ctx's device, issuing its work on `stream` (NULL: a
- * stream of its own).  Allocates the arena and pinned result buffers. */
+ * stream of its own).  Allocates the arena and pinned result buffers.  When
+ * every step runs all levels (levels_per_step <= 0 or >= n_levels),
+ * consecutive steps share no request and the server alternates them between
+ * `stream` (with ctx) and a second stream with a second context of its own
+ * (ctx's flags, timeout and tuned variants; device errors still reach ctx's
+ * status word, read by afps_sync on ctx), so that one step's frame copies
+ * overlap the previous step's sampling; otherwise it uses `stream` alone.
+ * ctx must outlive the server. */
 int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_config* cfg,
                        void* stream);
 

@@ -86,8 +86,8 @@ struct ClassPlan {
     // every cloud of the class has the same N, C, M, window and start, and
     // they are stored back to back: the kernel computes its items
     bool uniform = false;
-    // uniform clouds at scattered offsets: their (point, output) offset pairs
-    // start at pair cloud_first of BatchPlan::clouds (-1: back to back)
+    // items computed from per-cloud records, which start at record
+    // cloud_first of BatchPlan::clouds (-1: equal clouds back to back)
     int64_t cloud_first = -1;
     bool merged = false;  // several shape classes in one launch (window kernels)
     bool narrow = true;   // every item's window has at most 17 points, read literally
@@ -98,7 +98,7 @@ struct ClassPlan {
 struct BatchPlan {
     std::vector<ItemDesc> items;  // class-major
     std::vector<ClassPlan> classes;
-    std::vector<int64_t> clouds;  // (point offset, output offset) pairs of scattered classes
+    std::vector<afps::CloudRec> clouds;  // per-cloud records of the record classes
 };
 
 struct GraphEntry {
@@ -119,6 +119,7 @@ struct afps_ctx {
     std::string tune_path;
     int num_sms = 0;
     int* d_status = nullptr;
+    bool status_borrowed = false;  // d_status belongs to another context (clone_context)
     std::string last_error;
     cudaEvent_t ev_done = nullptr;    // last device work that used the shared workspace
     cudaStream_t capture = nullptr;   // private stream for graph capture
@@ -591,33 +592,56 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
             const Member& m0 = g.second.front();
             const int32_t b0 = m0.b;
             const uint32_t meth0 = method ? method[b0] : 0u;
-            bool same = true;    // every cloud of the class has the same shape ...
+            bool same = true;    // every cloud of the class has the same M, window,
+                                 // reading and start offset ...
+            bool equal = true;   // ... the same N and C ...
             bool packed = true;  // ... and they lie back to back
+            int64_t wide_mn = 0;  // largest M * N
             for (size_t j = 0; j < g.second.size() && same; ++j) {
                 const Member& m = g.second[j];
                 const int32_t b = m.b;
-                same = n_pts[b] == n_pts[b0] && C[b] == C[b0] && M[b] == M[b0] &&
-                       K[b] == K[b0] && (method ? method[b] : 0u) == meth0 &&
-                       m.chk.start_r == m0.chk.start_r;
+                same = M[b] == M[b0] && K[b] == K[b0] && (method ? method[b] : 0u) == meth0 &&
+                       m.chk.start_r == m0.chk.start_r && n_pts[b] <= INT32_MAX;
+                equal = equal && n_pts[b] == n_pts[b0] && C[b] == C[b0];
                 packed = packed && pt_begin[b] == pt_begin[b0] + (int64_t)j * n_pts[b0] &&
                          out_begin[b] == out_begin[b0] + (int64_t)j * C[b0];
+                wide_mn = std::max(wide_mn, (int64_t)M[b] * n_pts[b]);
             }
-            // scattered equal clouds: one offset pair per cloud instead of M
-            // table entries (worth it from two clouds on)
-            const bool scattered = scatter && !packed && g.second.size() >= 2;
-            if (same && (packed || scattered) && n_pts[b0] <= INT32_MAX) {
+            // clouds elsewhere or of different sizes: one record per cloud
+            // instead of M table entries (worth it from two clouds on)
+            const bool records = scatter && !(equal && packed) && g.second.size() >= 2;
+            if (same && ((equal && packed) || records)) {
                 ItemDesc w{};
                 window_sides(K[b0], meth0, w);
                 cp.uniform = true;
-                if (scattered) {
-                    cp.cloud_first = (int64_t)(plan.clouds.size() / 2);
-                    for (const Member& m : g.second) {
-                        plan.clouds.push_back(pt_begin[m.b]);
-                        plan.clouds.push_back(out_begin[m.b]);
+                int64_t n_max = 0;
+                int32_t c_max = 0;
+                if (records) {
+                    // largest clouds first: the queue's items then come in
+                    // about the longest-processing-time order
+                    std::vector<Member> order(g.second);
+                    std::stable_sort(order.begin(), order.end(),
+                                     [&](const Member& x, const Member& y) {
+                                         return (int64_t)C[x.b] * n_pts[x.b] >
+                                                (int64_t)C[y.b] * n_pts[y.b];
+                                     });
+                    cp.cloud_first = (int64_t)plan.clouds.size();
+                    for (const Member& m : order) {
+                        afps::CloudRec r{};
+                        r.pt_off = pt_begin[m.b];
+                        r.out_off = out_begin[m.b];
+                        r.N = (int32_t)n_pts[m.b];
+                        r.C = C[m.b];
+                        plan.clouds.push_back(r);
+                        n_max = std::max(n_max, m.chk.n_max);
+                        c_max = std::max(c_max, m.chk.c_max);
                     }
+                } else {
+                    n_max = m0.chk.n_max;
+                    c_max = m0.chk.c_max;
                 }
-                cp.single.pt_off = scattered ? 0 : pt_begin[b0];
-                cp.single.out_off = scattered ? 0 : out_begin[b0];
+                cp.single.pt_off = records ? 0 : pt_begin[b0];
+                cp.single.out_off = records ? 0 : out_begin[b0];
                 cp.single.N = (int32_t)n_pts[b0];
                 cp.single.C = C[b0];
                 cp.single.M = M[b0];
@@ -625,10 +649,10 @@ int build_plan(afps_ctx* ctx, int32_t B, const int64_t* pt_begin, const int64_t*
                 cp.single.kr = w.kr;
                 cp.single.flags = w.flags;
                 cp.single.start_r = m0.chk.start_r;
-                cp.single.wide = (int64_t)M[b0] * n_pts[b0] > (int64_t)UINT32_MAX ? 1 : 0;
+                cp.single.wide = wide_mn > (int64_t)UINT32_MAX ? 1 : 0;
                 cp.single.m_magic = afps::div_magic(M[b0]);
-                cp.n_max = m0.chk.n_max;
-                cp.c_max = m0.chk.c_max;
+                cp.n_max = n_max;
+                cp.c_max = c_max;
                 cp.count = g.second.size() * (size_t)M[b0];
                 cp.narrow = w.kl + w.kr <= 16 && !(w.flags & afps::ITEM_FULL_FIRST);
                 cp.v = choose_variant(ctx, cp.npdu, cp.n_max, cp.c_max, cp.count, cp.narrow);
@@ -725,8 +749,8 @@ int build_plan_consecutive(afps_ctx* ctx, const int64_t* pt_off, int32_t B, cons
 int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* d_out,
              cudaStream_t stream, bool host_resident = false) {
     const size_t bytes = plan.items.size() * sizeof(ItemDesc);  // a multiple of 16
-    const size_t cbytes = plan.clouds.size() * sizeof(int64_t);
-    bool table = cbytes > 0;  // some class reads the item table or cloud offsets
+    const size_t cbytes = plan.clouds.size() * sizeof(afps::CloudRec);
+    bool table = cbytes > 0;  // some class reads the item table or cloud records
     bool queue = false;       // some class uses a work-queue counter
     for (const ClassPlan& cp : plan.classes) {
         table = table || !cp.uniform;
@@ -743,13 +767,13 @@ int run_plan(afps_ctx* ctx, const BatchPlan& plan, const float* d_xyz, int32_t* 
         if (urc != AFPS_OK) return urc;
     }
     const ItemDesc* d_items = static_cast<const ItemDesc*>(ctx->items.p);
-    const int64_t* d_clouds =
-        reinterpret_cast<const int64_t*>(static_cast<const char*>(ctx->items.p) + bytes);
+    const afps::CloudRec* d_clouds = reinterpret_cast<const afps::CloudRec*>(
+        static_cast<const char*>(ctx->items.p) + bytes);
     unsigned int* counters = static_cast<unsigned int*>(ctx->counters.p);
     for (size_t i = 0; i < plan.classes.size(); ++i) {
         const ClassPlan& cp = plan.classes[i];
         afps::SingleCloud sc = cp.single;
-        if (cp.cloud_first >= 0) sc.cloud_off = d_clouds + 2 * cp.cloud_first;
+        if (cp.cloud_first >= 0) sc.clouds = d_clouds + cp.cloud_first;
         int rc = launch_class(ctx, cp.v, cp.npdu, cp.uniform ? nullptr : d_items + cp.first,
                               cp.count, counters + i, d_xyz, d_out, stream, host_resident,
                               cp.uniform ? &sc : nullptr);
@@ -1078,6 +1102,32 @@ int reserve_workspace(afps_ctx* ctx, size_t bytes) {
     return AFPS_OK;
 }
 
+int clone_context(afps_ctx* src, afps_ctx** out) {
+    if (!src || !out) return AFPS_ERR_INVALID_ARG;
+    *out = nullptr;
+    afps_config cfg{};
+    cfg.device = src->device;
+    cfg.flags = src->flags;
+    cfg.timeout_ns = (int64_t)src->timeout_ns;
+    afps_ctx* c = nullptr;
+    const int rc = afps_create(&c, &cfg);
+    if (rc != AFPS_OK) return rc;
+    {
+        DeviceGuard guard(c->device);
+        cudaFree(c->d_status);
+        cudaGetLastError();
+    }
+    c->d_status = src->d_status;
+    c->status_borrowed = true;
+    c->tuned = src->tuned;
+    *out = c;
+    return AFPS_OK;
+}
+
+void copy_error(afps_ctx* to, const afps_ctx* from) {
+    if (to && from && to != from) to->last_error = from->last_error;
+}
+
 int sample_scattered(afps_ctx* ctx, const float* xyz, int32_t B, const int64_t* pt_begin,
                      const int64_t* n_pts, const int32_t* C, const int32_t* M, const int32_t* K,
                      const int64_t* start, int32_t* out, const int64_t* out_begin,
@@ -1153,7 +1203,7 @@ void afps_destroy(afps_ctx* ctx) {
             ctx->stage[i].release();
             if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
         }
-        if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->d_status && !ctx->status_borrowed) cudaFree(ctx->d_status);
         if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
         if (ctx->capture) cudaStreamDestroy(ctx->capture);
         cudaGetLastError();

@@ -82,12 +82,12 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
     }
     __syncthreads();
     if (CLUSTER) dev::cluster_sync();  // every peer's barriers exist before any remote store
-    // A computed first item (no table, no cloud offsets) needs no memory
+    // A computed first item (no table, no cloud records) needs no memory
     // access, so this CTA's part of its points can be prefetched into L2
     // while the previous kernel of the stream still runs.
     {
         const int g0 = CLUSTER ? (int)dev::cluster_id_x() : (int)blockIdx.x;
-        if (!a.items && !a.single.cloud_off && !a.host_resident && g0 < a.n_items) {
+        if (!a.items && !a.single.clouds && !a.host_resident && g0 < a.n_items) {
             const ItemDesc d0 = dev::load_item(a, g0);
             const int ch = CLUSTER ? (d0.n + CS - 1) / CS : d0.n;
             const int p0 = rank * ch, pn = max(0, min(d0.n - p0, ch));

@@ -278,12 +278,12 @@ struct SmallDiv {
     }
 };
 
-// Item `i` of a launch: from the device table, or computed from the
-// parameters of a run of equal clouds (cloud i / M, sector i % M) with the
-// sector rule floor(s*N/M), floor(s*C/M), the clouds stored back to back or
-// at the offsets of the `cloud_off` pairs.  Computing it saves the dependent
-// load of a table entry ahead of the stage-in (back to back: no load at all),
-// and the host builds one pair per cloud instead of M table entries.
+// Item `i` of a launch: from the device table, or computed (cloud i / M,
+// sector i % M) with the sector rule floor(s*N/M), floor(s*C/M) from the
+// parameters of a run of equal clouds stored back to back, or from the
+// cloud's record (offsets, N, C).  Back to back no memory is read at all
+// ahead of the stage-in; with records the host builds one per cloud instead
+// of M table entries.
 __device__ __forceinline__ ItemDesc load_item(const LaunchArgs& a, int i) {
     if (a.items) return a.items[i];
     const SingleCloud& s = a.single;
@@ -295,27 +295,33 @@ __device__ __forceinline__ ItemDesc load_item(const LaunchArgs& a, int i) {
     };
     const uint32_t b = divM((uint32_t)i);
     const uint32_t sec = (uint32_t)i - b * M;
+    int32_t N = s.N, C = s.C;
+    int64_t src0, dst0;
+    if (s.clouds) {
+        const CloudRec r = s.clouds[b];
+        N = r.N;
+        C = r.C;
+        src0 = r.pt_off;
+        dst0 = r.out_off;
+    } else {
+        src0 = s.pt_off + (int64_t)b * N;
+        dst0 = s.out_off + (int64_t)b * C;
+    }
     int64_t lo, hi, o0, o1;
     if (s.wide) {  // M * N does not fit in 32 bits
-        lo = (int64_t)sec * s.N / s.M;
-        hi = (int64_t)(sec + 1) * s.N / s.M;
-        o0 = (int64_t)sec * s.C / s.M;
-        o1 = (int64_t)(sec + 1) * s.C / s.M;
+        lo = (int64_t)sec * N / s.M;
+        hi = (int64_t)(sec + 1) * N / s.M;
+        o0 = (int64_t)sec * C / s.M;
+        o1 = (int64_t)(sec + 1) * C / s.M;
     } else {  // numerators below M * N < 2^32
-        lo = divM(sec * (uint32_t)s.N);
-        hi = divM((sec + 1) * (uint32_t)s.N);
-        o0 = divM(sec * (uint32_t)s.C);
-        o1 = divM((sec + 1) * (uint32_t)s.C);
+        lo = divM(sec * (uint32_t)N);
+        hi = divM((sec + 1) * (uint32_t)N);
+        o0 = divM(sec * (uint32_t)C);
+        o1 = divM((sec + 1) * (uint32_t)C);
     }
     ItemDesc d;
-    if (s.cloud_off) {
-        const longlong2 off = reinterpret_cast<const longlong2*>(s.cloud_off)[b];
-        d.src = off.x + lo;
-        d.dst = off.y + o0;
-    } else {
-        d.src = s.pt_off + (int64_t)b * s.N + lo;
-        d.dst = s.out_off + (int64_t)b * s.C + o0;
-    }
+    d.src = src0 + lo;
+    d.dst = dst0 + o0;
     d.n = (int32_t)(hi - lo);
     d.c = (int32_t)(o1 - o0);
     d.first = s.start_r < d.n - 1 ? s.start_r : d.n - 1;

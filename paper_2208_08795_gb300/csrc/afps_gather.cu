@@ -12,6 +12,7 @@
 // destinations in parallel.  Counting (not flags) keeps repeated indices,
 // should a degenerate cloud produce any.  The output xyz must not overlap the
 // input.
+#include <algorithm>
 #include <mutex>
 #include <set>
 
@@ -135,36 +136,48 @@ __global__ void __launch_bounds__(1024) afps_gather_kernel(
     }
 }
 
-// Frame copies of a serving step: grid.y = frame, grid.x = 16 KB chunks of
-// it; 16-byte vectors where both ends allow, else 4-byte words.  The
-// descriptors travel in the kernel's parameters, so a step's admission is
-// one launch instead of a copy call per frame.
+// Frame copies of a serving step: grid.y = frame, grid.x = the CTAs sharing
+// it, each thread with eight 16-byte loads in flight (4-byte words where an
+// end is not 16-byte aligned).  The frames come from page-locked host memory
+// over the C2C link, whose rate a few hundred KB in flight already reaches;
+// so the copy keeps to about 128 CTAs of 256 threads in all, and leaves the
+// SMs to the sampling launches of another stream meanwhile.  The descriptors
+// travel in the kernel's parameters: a step's admission is one launch.
 __global__ void __launch_bounds__(256) afps_frame_copy_kernel(const __grid_constant__ FrameCopyBatch b) {
     const int f = blockIdx.y;
     if (f >= b.n) return;
     const FrameCopy c = b.c[f];
-    constexpr int64_t kChunk = 16384;
-    const int64_t lo = (int64_t)blockIdx.x * kChunk;
-    if (lo >= c.bytes) return;
-    const int64_t hi = min(c.bytes, lo + kChunk);
     const char* src = static_cast<const char*>(c.src);
     char* dst = static_cast<char*>(c.dst);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+    int64_t tail = 0;  // first byte of the 4-byte-word part
     if (vec) {
-        const int64_t v_hi = lo + ((hi - lo) & ~int64_t(15));
-        for (int64_t o = lo + 16 * threadIdx.x; o < v_hi; o += 16 * blockDim.x)
-            *reinterpret_cast<uint4*>(dst + o) = *reinterpret_cast<const uint4*>(src + o);
-        for (int64_t o = v_hi + 4 * threadIdx.x; o < hi; o += 4 * blockDim.x)
-            *reinterpret_cast<uint32_t*>(dst + o) = *reinterpret_cast<const uint32_t*>(src + o);
-    } else {
-        for (int64_t o = lo + 4 * threadIdx.x; o < hi; o += 4 * blockDim.x)
-            *reinterpret_cast<uint32_t*>(dst + o) = *reinterpret_cast<const uint32_t*>(src + o);
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+        const int64_t n16 = c.bytes / 16;
+        int64_t i = t;
+        for (; i + 7 * stride < n16; i += 8 * stride) {
+            uint4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = s4[i + u * stride];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d4[i + u * stride] = v[u];
+        }
+        for (; i < n16; i += stride) d4[i] = s4[i];
+        tail = 16 * n16;
     }
+    for (int64_t o = tail + 4 * t; o < c.bytes; o += 4 * stride)
+        *reinterpret_cast<uint32_t*>(dst + o) = *reinterpret_cast<const uint32_t*>(src + o);
 }
 
 cudaError_t launch_frame_copy(const FrameCopyBatch& batch, int64_t max_bytes, cudaStream_t stream) {
     if (batch.n < 1) return cudaSuccess;
-    const dim3 grid((unsigned)((max_bytes + 16383) / 16384), (unsigned)batch.n, 1);
+    // about 128 CTAs in all, at most one per 32 KB of the largest frame
+    const int64_t per_frame =
+        std::max<int64_t>(1, std::min<int64_t>((max_bytes + 32767) / 32768, 128 / batch.n));
+    const dim3 grid((unsigned)per_frame, (unsigned)batch.n, 1);
     afps_frame_copy_kernel<<<grid, 256, 0, stream>>>(batch);
     return cudaGetLastError();
 }

@@ -30,6 +30,15 @@ enum : int32_t { ITEM_FULL_FIRST = 1 };  // the first update reaches the whole s
 // A run of equal clouds (N points, C samples, M sectors each) stored back to
 // back from point pt_off, their outputs back to back from out_off; a launch
 // over it has (number of clouds) x M items.
+// One cloud of a launch whose items are computed from per-cloud records.
+struct CloudRec {
+    int64_t pt_off;   // first point, in points from the xyz base
+    int64_t out_off;  // first output, in elements from the output base
+    int32_t N, C;
+    int32_t pad[2];
+};
+static_assert(sizeof(CloudRec) == 32, "CloudRec layout");
+
 struct SingleCloud {
     int64_t pt_off;
     int64_t out_off;
@@ -38,10 +47,11 @@ struct SingleCloud {
     int32_t start_r;        // offset of start_idx inside its own sector
     int32_t wide;           // M * N >= 2^32: sector bounds in 64-bit arithmetic
     uint64_t m_magic;       // div_magic(M): x / M = high 64 bits of x * m_magic (x < 2^32)
-    // Equal clouds at arbitrary offsets: a device array of (point offset,
-    // output offset) pairs, one per cloud in item order, replacing
-    // pt_off + b N and out_off + b C; nullptr for clouds stored back to back.
-    const int64_t* cloud_off;
+    // Clouds at arbitrary offsets, of any N and C (the same M, window,
+    // reading and start offset): a device array of records, one per cloud in
+    // item order, replacing pt_off + b N, out_off + b C, N and C; nullptr for
+    // equal clouds stored back to back.
+    const CloudRec* clouds;
 };
 
 // Multiplier for unsigned division of 32-bit numerators by d >= 2:
@@ -214,6 +224,14 @@ constexpr int32_t kSortClusterMin = 4096;
 struct afps_ctx;
 namespace afps {
 // Batched sampling of B clouds at arbitrary offsets of one xyz / output base.
+// A second context on src's device, with its flags, timeout and tuned
+// variants and a workspace of its own, sharing src's device status word (so
+// afps_sync on src also reports its device errors): it lets work on another
+// stream upload its tables without waiting for src's.  Destroy it with
+// afps_destroy before src.
+int clone_context(afps_ctx* src, afps_ctx** out);
+// The last error message of `from`, for a caller that holds `to`.
+void copy_error(afps_ctx* to, const afps_ctx* from);
 int sample_scattered(afps_ctx* ctx, const float* xyz, int32_t B, const int64_t* pt_begin,
                      const int64_t* n_pts, const int32_t* C, const int32_t* M, const int32_t* K,
                      const int64_t* start, int32_t* out, const int64_t* out_begin,

@@ -12,6 +12,11 @@
 // and its frame comes in by one copy kernel per step that reads the
 // page-locked frames of every admitted request: a step costs a few launches,
 // not a copy call per request.
+// When a step runs every level (the default), a request is admitted and
+// finished within one step, so consecutive steps share no request: steps
+// alternate between two streams (the caller's context and stream, and a
+// second context of the runtime's own), and one step's frame copy over the
+// C2C link overlaps the previous step's sampling on the SMs.
 // Blocks start on 48-byte boundaries so that every xyz part starts on a point
 // boundary of the arena (point offsets = byte offsets / 12) and every int32
 // part on a 4-byte one.
@@ -101,6 +106,7 @@ struct Request {
     int level = 0;             // next level to sample
     Block block;
     int slot = -1;             // pinned result slot
+    int lane = 0;              // the stream (and context) its work runs on
     int64_t xyz_pt[AFPS_SERVER_MAX_LEVELS + 1];  // cloud l, in points from the arena base
     int64_t out_el[AFPS_SERVER_MAX_LEVELS];      // out_l, in int32 elements
     int64_t fidx_el[AFPS_SERVER_MAX_LEVELS + 1]; // frame index of cloud l (l >= 1)
@@ -111,12 +117,18 @@ struct Request {
 }  // namespace
 
 struct afps_server {
-    afps_ctx* ctx = nullptr;
+    afps_ctx* ctx = nullptr;  // the caller's: lane 0
     afps_server_config cfg{};
     int levels[AFPS_SERVER_MAX_LEVELS] = {};
     int64_t total_samples = 0;  // sum of levels
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // lane 0
     bool own_stream = false;
+    // steps alternate over `lanes` (stream, context) pairs: lane 0 is
+    // (ctx, stream), lane 1 a stream and a clone of ctx owned here
+    int lanes = 1;
+    cudaStream_t lane_stream[2] = {};
+    afps_ctx* lane_ctx[2] = {};
+    uint64_t steps_run = 0;
     int device = 0;
     unsigned char* arena_base = nullptr;
     std::unique_ptr<Arena> arena;
@@ -344,6 +356,23 @@ int afps_server_create(afps_server** out, afps_ctx* ctx, const afps_server_confi
         if (s->own_stream) cudaStreamDestroy(s->stream);
         return rc;
     }
+    s->lane_stream[0] = s->stream;
+    s->lane_ctx[0] = ctx;
+    // a second lane when every step runs all levels (no request spans two
+    // steps); without its stream or context the server runs on one
+    const bool all_levels = s->cfg.levels_per_step <= 0 || s->cfg.levels_per_step >= s->cfg.n_levels;
+    if (all_levels && afps::clone_context(ctx, &s->lane_ctx[1]) == AFPS_OK) {
+        if (cudaStreamCreateWithFlags(&s->lane_stream[1], cudaStreamNonBlocking) == cudaSuccess &&
+            afps::reserve_workspace(s->lane_ctx[1], table) == AFPS_OK) {
+            s->lanes = 2;
+        } else {
+            cudaGetLastError();
+            if (s->lane_stream[1]) cudaStreamDestroy(s->lane_stream[1]);
+            afps_destroy(s->lane_ctx[1]);
+            s->lane_stream[1] = nullptr;
+            s->lane_ctx[1] = nullptr;
+        }
+    }
     *out = s.release();
     return AFPS_OK;
 }
@@ -415,7 +444,7 @@ int afps_server_cancel(afps_server* s, uint64_t tag) {
             // launched so far (all before this event) has completed
             cudaEvent_t e = take_event(s);
             if (!e) return AFPS_ERR_CUDA;
-            if (cudaEventRecord(e, s->stream) != cudaSuccess) {
+            if (cudaEventRecord(e, s->lane_stream[r->lane]) != cudaSuccess) {
                 cudaGetLastError();
                 give_event(s, e);
                 return AFPS_ERR_CUDA;
@@ -446,6 +475,11 @@ int afps_server_step(afps_server* s) {
     cudaGetLastError();
     reap(s);
 
+    // this step's lane (stream and context)
+    const int lane = (int)(s->steps_run % (uint64_t)s->lanes);
+    cudaStream_t st = s->lane_stream[lane];
+    afps_ctx* cx = s->lane_ctx[lane];
+
     // admission, first come first served, by arena footprint and slots
     float* xyz = reinterpret_cast<float*>(s->arena_base);
     int32_t* ints = reinterpret_cast<int32_t*>(s->arena_base);
@@ -454,7 +488,7 @@ int afps_server_step(afps_server* s) {
     batch.n = 0;
     int64_t batch_max = 0;
     auto flush = [&]() -> bool {
-        const bool ok = afps::launch_frame_copy(batch, batch_max, s->stream) == cudaSuccess;
+        const bool ok = afps::launch_frame_copy(batch, batch_max, st) == cudaSuccess;
         batch.n = 0;
         batch_max = 0;
         return ok;
@@ -462,6 +496,7 @@ int afps_server_step(afps_server* s) {
     while (!s->queue.empty() && (int)s->active.size() < s->cfg.max_inflight) {
         Request& r = *s->queue.front();
         if (!admit_one(s, r)) break;
+        r.lane = lane;
         batch.c[batch.n++] = afps::FrameCopy{r.src_dev, xyz + 3 * r.xyz_pt[0], 12 * r.N};
         batch_max = std::max(batch_max, 12 * r.N);
         if (batch.n == afps::kFrameCopyMax && !flush()) {
@@ -479,7 +514,7 @@ int afps_server_step(afps_server* s) {
     }
     if (!copied.empty()) {
         cudaEvent_t ce = take_event(s);
-        if (!ce || cudaEventRecord(ce, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
+        if (!ce || cudaEventRecord(ce, st) != cudaSuccess) return AFPS_ERR_CUDA;
         s->pool_pending.emplace_back(ce, std::move(copied));
     }
 
@@ -518,13 +553,15 @@ int afps_server_step(afps_server* s) {
             d.n = (int32_t)n;
             d.c = C[b];
         }
-        int rc = afps::sample_scattered(s->ctx, xyz, B, pt_begin.data(), n_pts.data(), C.data(),
+        int rc = afps::sample_scattered(cx, xyz, B, pt_begin.data(), n_pts.data(), C.data(),
                                         M.data(), K.data(), start.data(), ints, out_begin.data(),
-                                        s->stream);
-        if (rc != AFPS_OK) return rc;
-        rc = afps::gather_run(s->ctx, g.data(), B, xyz, ints, ints, xyz, ints, s->pinned_dev,
-                              s->stream);
-        if (rc != AFPS_OK) return rc;
+                                        st);
+        if (rc == AFPS_OK)
+            rc = afps::gather_run(cx, g.data(), B, xyz, ints, ints, xyz, ints, s->pinned_dev, st);
+        if (rc != AFPS_OK) {
+            afps::copy_error(s->ctx, cx);
+            return rc;
+        }
 
         // finished chains: their results are in their slots once the step's
         // gather has completed
@@ -535,7 +572,7 @@ int afps_server_step(afps_server* s) {
             if (!fin) fin = take_event(s);
         }
         if (fin) {
-            if (cudaEventRecord(fin, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
+            if (cudaEventRecord(fin, st) != cudaSuccess) return AFPS_ERR_CUDA;
             // the finishing requests share the step's completion event
             int holders = 0;
             for (Request* r : run) {
@@ -549,8 +586,9 @@ int afps_server_step(afps_server* s) {
     }
     if (advanced == 0) return 0;
     cudaEvent_t se = take_event(s);
-    if (!se || cudaEventRecord(se, s->stream) != cudaSuccess) return AFPS_ERR_CUDA;
+    if (!se || cudaEventRecord(se, st) != cudaSuccess) return AFPS_ERR_CUDA;
     s->step_events.push_back(se);
+    ++s->steps_run;
     return advanced;
 }
 
@@ -594,6 +632,7 @@ double afps_server_clock_ms(const afps_server* s) { return s ? s->now() : 0.0; }
 void afps_server_destroy(afps_server* s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    if (s->lane_stream[1]) cudaStreamSynchronize(s->lane_stream[1]);
     std::unordered_set<cudaEvent_t> held;  // shared events are destroyed once
     for (auto& r : s->active)
         if (r && r->done_ev) held.insert(r->done_ev);
@@ -605,6 +644,8 @@ void afps_server_destroy(afps_server* s) {
     if (s->arena_base) cudaFree(s->arena_base);
     if (s->pinned) cudaFreeHost(s->pinned);
     if (s->own_stream) cudaStreamDestroy(s->stream);
+    if (s->lane_stream[1]) cudaStreamDestroy(s->lane_stream[1]);
+    if (s->lane_ctx[1]) afps_destroy(s->lane_ctx[1]);
     cudaGetLastError();
     delete s;
 }

@@ -40,10 +40,10 @@ __global__ void __launch_bounds__(256) afps_warp_kernel(const LaunchArgs a) {
         dev::fence_mbar_init();
     }
     __syncwarp();
-    // A computed first item (no table, no cloud offsets, no queue) needs no
+    // A computed first item (no table, no cloud records, no queue) needs no
     // memory access, so its points can be prefetched into L2 while the
     // previous kernel of the stream still runs.
-    if (!a.items && !a.single.cloud_off && !a.counter && !a.host_resident &&
+    if (!a.items && !a.single.clouds && !a.counter && !a.host_resident &&
         blockIdx.x * W + w < a.n_items) {
         const ItemDesc d0 = dev::load_item(a, blockIdx.x * W + w);
         const char* g = reinterpret_cast<const char*>(a.xyz + 3 * d0.src);
