@@ -44,6 +44,31 @@ struct __align__(16) Rec {
 };
 static_assert(sizeof(Rec) == 32, "Rec layout");
 
+// Wait for an exchange's records: polls mbarrier.test_wait (no suspension)
+// and reads the clock every 32 polls, giving up after timeout_ns.  While an
+// exchange is pending every warp of the CTA waits on it, so polling takes no
+// issue slot from useful work, and the records are seen as soon as they land.
+__device__ __forceinline__ bool exchange_wait(uint32_t bar, uint32_t parity, uint64_t timeout_ns) {
+    auto test = [&]() {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        return ok != 0;
+    };
+    if (test()) return true;
+    const uint64_t t0 = dev::globaltimer();
+    while (true) {
+        for (int k = 0; k < 32; ++k)
+            if (test()) return true;
+        if (dev::globaltimer() - t0 > timeout_ns) return false;
+    }
+}
+
 template <int P, bool NPDU, bool CLUSTER>
 __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -386,7 +411,7 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
 
             // 3. wait for every record of this exchange
             if (CLUSTER) {
-                xlate = !dev::mbar_wait_bounded(xbar, xb ? xphase1 : xphase0, a.timeout_ns);
+                xlate = !exchange_wait(xbar, xb ? xphase1 : xphase0, a.timeout_ns);
                 if (xlate) dev::record_status(a.status, DEV_TIMEOUT_EXCHANGE);
                 if (xb)
                     xphase1 ^= 1u;
