@@ -265,8 +265,9 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                 if (full_first && t < c) round_any(t++, 0, n - 1);
                 if (LEAN && kl + kr <= 31) {
                     // Narrow window, fewest instructions: the touched rows' cache
-                    // entries are recomputed first (the second row only when the
-                    // window crosses into it), then the sample is the argmax over
+                    // entries are recomputed first (the sample's row, and the
+                    // other row the window crosses into only when its cached
+                    // maximum lies in the window), then the sample is the argmax over
                     // the cache: every lane's best slot (slots ascend, so the
                     // first of equal maxima has the lowest index), two redux.sync
                     // steps.  One row: four redux.sync, two rows: six.  Unrolled
@@ -283,17 +284,29 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                         Ds[j] = fminf(Ds[j], dd);
                         __syncwarp();
                         const int r0 = wl >> 5, r1 = wh >> 5;
+                        const int rp = p >> 5;  // the sample's row
                         {
-                            const unsigned b0 = __float_as_uint(Ds[32 * r0 + lane]);
+                            const unsigned b0 = __float_as_uint(Ds[32 * rp + lane]);
                             unsigned m0, l0;
                             row_max(b0, lane, m0, l0);
-                            set_row<R>(rmb, rmi, r0, m0, (unsigned)(32 * r0) + l0, lane);
+                            set_row<R>(rmb, rmi, rp, m0, (unsigned)(32 * rp) + l0, lane);
                         }
                         if (r1 != r0) {
-                            const unsigned b1 = __float_as_uint(Ds[32 * r1 + lane]);
-                            unsigned m1, l1;
-                            row_max(b1, lane, m1, l1);
-                            set_row<R>(rmb, rmi, r1, m1, (unsigned)(32 * r1) + l1, lane);
+                            // The other touched row keeps its cached maximum and
+                            // index unless that index lies in the window (its
+                            // points only decreased); a warp-uniform test on the
+                            // entry, fetched from its owner lane.
+                            const int ro = r0 + r1 - rp;
+                            unsigned v = rmi[0];
+#pragma unroll
+                            for (int s = 1; s < R; ++s) v = (ro >> 5) == s ? rmi[s] : v;
+                            const unsigned io = __shfl_sync(dev::kFull, v, ro & 31);
+                            if (io - (unsigned)wl <= (unsigned)(wh - wl)) {
+                                const unsigned b1 = __float_as_uint(Ds[32 * ro + lane]);
+                                unsigned m1, l1;
+                                row_max(b1, lane, m1, l1);
+                                set_row<R>(rmb, rmi, ro, m1, (unsigned)(32 * ro) + l1, lane);
+                            }
                         }
                         unsigned cb = rmb[0], ci = rmi[0];
 #pragma unroll
