@@ -252,22 +252,34 @@ __global__ void __launch_bounds__(P >= 16 ? 256 : 1024) afps_cta_kernel(const La
             const float* G = CLUSTER ? a.xyz + 3 * d.src : pts;  // the sector's points
             bool ok = true;  // D is updated in place and reset if the test fails
             // Window u = floor((j + kl - p) / q) is the last one starting at or
-            // before point j; window u - 1 may reach j too, no earlier one can
+            // before point j and always reaches it (j <= s_u + kr - kl);
+            // window u - 1 reaches it when j < s_u, no earlier one can
             // (kl <= kr).  Both candidates' distances are computed and
-            // selected: no branch, one division a point; a point in neither
-            // measures against p (one broadcast load), the clamped index
-            // keeps an empty chunk's loads inside its buffer.
+            // selected, without a branch; a point in neither measures against
+            // p (one broadcast load), the clamped index keeps an empty chunk's
+            // loads inside its buffer.  u goes from one of the thread's points
+            // to the next (T apart) as quotient and remainder of the
+            // non-negative j + kl - p (p <= kl): one division in all.
+            const int x0 = c0 + tid + kl - p;
+            int u = (int)divq((uint32_t)x0);
+            int rem = x0 - u * q;
+            const int uT = (int)divq((uint32_t)T);
+            const int rT = T - uT * q;
 #pragma unroll
             for (int i = 0; i < P; ++i) {
                 const int jl = tid + T * i;
                 const int jlc = max(min(jl, cn - 1), 0);
                 const int j = c0 + jlc;  // sector-local index
                 const float px = pts[3 * jlc], py = pts[3 * jlc + 1], pz = pts[3 * jlc + 2];
-                // unsigned division: j + kl - p >= 0 (p <= kl)
-                const int u = (int)divq((uint32_t)(j + kl - p));
                 const int s1 = p + u * q, s0 = s1 - q;
-                const bool in1 = jl < cn && u < tw && j <= s1 + kr;
-                const bool in0 = jl < cn && u >= 1 && u - 1 < tw && j < s1;
+                const bool in1 = jl < cn && u < tw;
+                const bool in0 = jl < cn && u >= 1 && u <= tw && j < s1;
+                u += uT;  // the quotient of the thread's next point
+                rem += rT;
+                if (rem >= q) {
+                    rem -= q;
+                    ++u;
+                }
                 const int c1 = dev::checked(in1 ? s1 : p, 0, n, a.status);
                 const int c0s = dev::checked(in0 ? s0 : p, 0, n, a.status);
                 const float d1 = dev::sqdist(px, py, pz, G[3 * c1], G[3 * c1 + 1], G[3 * c1 + 2]);

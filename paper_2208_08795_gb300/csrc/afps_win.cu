@@ -168,17 +168,32 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                     const int tn = min(ts, c);      // stride samples emitted
                     const int tw = min(ts, c - 1);  // ... whose window is applied
                     bool ok = true;
+                    // u = floor((j + kl - p) / q) for j = 32 i + lane (a
+                    // non-negative numerator: p <= kl), carried from row to
+                    // row as quotient and remainder instead of one division
+                    // a point.  Window u always reaches j (j <= s_u + kr - kl);
+                    // window u - 1 reaches it when j < s_u (its last point is
+                    // s_u - q + kr = s_u - 1).
+                    const int x0 = lane + kl - p;
+                    int u = (int)divq((uint32_t)x0);
+                    int rem = x0 - u * q;
+                    const int u32 = (int)divq(32u);
+                    const int r32 = 32 - u32 * q;
                     for (int i = 0; i < rows; ++i) {
                         const int j = 32 * i + lane;
                         // both candidate windows' distances are computed (from a
                         // clamped point) and selected, without a branch
                         const int jc = min(j, n - 1);
                         const float px = pts[3 * jc], py = pts[3 * jc + 1], pz = pts[3 * jc + 2];
-                        // unsigned division: jc + kl - p >= 0 (p <= kl)
-                        const int u = (int)divq((uint32_t)(jc + kl - p));
                         const int s1 = p + u * q, s0 = s1 - q;  // windows u and u - 1
-                        const bool in1 = j < n && u < tw && jc <= s1 + kr;
-                        const bool in0 = j < n && u >= 1 && u - 1 < tw && jc <= s0 + kr;
+                        const bool in1 = j < n && u < tw;
+                        const bool in0 = j < n && u >= 1 && u <= tw && j < s1;
+                        u += u32;  // the next row's quotient
+                        rem += r32;
+                        if (rem >= q) {
+                            rem -= q;
+                            ++u;
+                        }
                         const int c1 = dev::checked(in1 ? s1 : jc, 0, n, a.status);
                         const int c0 = dev::checked(in0 ? s0 : jc, 0, n, a.status);
                         const float d1 = dev::sqdist(px, py, pz, pts[3 * c1], pts[3 * c1 + 1],
