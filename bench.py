@@ -472,12 +472,12 @@ def kernel_source_hash() -> str:
 # DRAM traffic of the headline kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch over the ragged batch), valid only for
 # the kernel sources it was taken on (their hash); otherwise reported as null.
-NCU_TRAFFIC = {"source_hash": "835a2e105ed9b383", "bytes_per_launch": 54952704}
+NCU_TRAFFIC = {"source_hash": "f6dfa383e566b02e", "bytes_per_launch": 54947840}
 # warp instructions of one headline launch (ncu smsp__inst_executed.sum), same rule
-NCU_INST = {"source_hash": "835a2e105ed9b383", "warp_inst_per_launch": 56070192}
+NCU_INST = {"source_hash": "f6dfa383e566b02e", "warp_inst_per_launch": 55554431}
 # shared-memory wavefronts of one headline launch (ncu
 # l1tex__data_pipe_lsu_wavefronts_mem_shared.sum; 128 bytes each), same rule
-NCU_SMEM = {"source_hash": "835a2e105ed9b383", "wavefronts_per_launch": 7640838}
+NCU_SMEM = {"source_hash": "f6dfa383e566b02e", "wavefronts_per_launch": 7709770}
 
 
 # ------------------------------------------------------------------ other configs
