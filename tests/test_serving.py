@@ -144,6 +144,43 @@ def test_pinned_frames_without_copy(sampler):
             assert np.array_equal(res["results"][t].levels[l], ref[l]), (t, l)
 
 
+def test_device_timeouts_of_both_streams_reach_the_callers_context():
+    """By default the server alternates its steps between the caller's stream
+    (and context) and a second stream with a second context of its own; a
+    device error on either must reach the caller's context, whose afps_sync
+    reports it.  The copy-stall fault flag (host-side injection: each stage-in
+    waits 1 ms for a copy that is never issued, then the kernels stop) makes
+    every step's sampling time out; the first step runs on the caller's
+    stream, the second on the server's own.  A fresh context serves the same
+    frame exactly afterwards."""
+    build_mod.build()
+    frames = [synth.lidar_frame(s) for s in range(2)]
+    s = B.Sampler(0, timeout_ns=1_000_000, flags=B.AFPS_FLAG_TEST_STALL_COPY)
+    srv = B.Server(s, LEVELS, 32, 16, hbm_budget_bytes=64 << 20)
+    try:
+        for t, f in enumerate(frames):
+            assert srv.submit(f, t) == 0
+            drain(srv, 1)  # one step (admission and every level), this frame only
+            with pytest.raises(B.AfpsError) as ei:
+                s.sync()
+            assert ei.value.code == B.AFPS_ERR_TIMEOUT, t
+        s.sync()  # reported once, then cleared
+    finally:
+        srv.close()
+        s.close()
+    fresh = B.Sampler(0)
+    srv = B.Server(fresh, LEVELS, 32, 16, hbm_budget_bytes=64 << 20)
+    try:
+        assert srv.submit(frames[1], 7) == 0
+        r = drain(srv, 1)[7]
+        ref = oracle.chain(frames[1], LEVELS, 32, 16)
+        for l in range(len(LEVELS)):
+            assert np.array_equal(r.levels[l], ref[l]), l
+    finally:
+        srv.close()
+        fresh.close()
+
+
 def test_cancel_queued_and_admitted(sampler):
     """Withdrawing a queued and an admitted request: the others still match
     the oracle, the withdrawn ones never come back, and all device memory
