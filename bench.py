@@ -648,7 +648,7 @@ def serving_sweep(sampler, seconds_per_rate: float = 0.25):
     try:
         serving.poisson_run(srv, frames, 1000.0, 20, seed=99)  # warm-up
         rows = []
-        for i, rate in enumerate(SERVING_RATES):
+        for i, rate in enumerate(SERVING_RATES + [64000.0, 128000.0]):  # past saturation
             n = int(min(2000, max(100, rate * seconds_per_rate)))
             r = serving.poisson_run(srv, frames, rate, n, seed=i)
             rows.append({k: round(v, 3) if isinstance(v, float) else v for k, v in r.items()})
