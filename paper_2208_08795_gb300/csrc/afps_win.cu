@@ -148,10 +148,7 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                 // link, where each store is a transfer): lane t % 32 keeps
                 // sample t and the warp stores rows of 32.
                 int obuf = lane == 0 ? d.lo + p : 0;
-                // Device indices go out sector-local (lane 0, one store a
-                // sample) and get the sector's offset d.lo once, when the
-                // item is done: an add a sample less.
-                if (lane == 0 && !ROWS) out[0] = p;
+                if (lane == 0 && !ROWS) out[0] = d.lo + p;
                 int t0 = 1;
                 bool fresh = true;  // distances still to be set to 1e10
                 if (!full_first && p <= kl && kl <= kr) {
@@ -219,7 +216,7 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                                 out[r0 + lane] = d.lo + p + (r0 + lane) * q;
                             obuf = d.lo + p + (((tn - 1) & ~31) + lane) * q;
                         } else {
-                            for (int t = 1 + lane; t < tn; t += 32) out[t] = p + t * q;
+                            for (int t = 1 + lane; t < tn; t += 32) out[t] = d.lo + p + t * q;
                         }
                         p += (tn - 1) * q;
                         t0 = tn;  // re-applying the last window is a no-op
@@ -276,7 +273,7 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                         obuf = lane == (t & 31) ? d.lo + p : obuf;
                         if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
                     } else if (lane == 0) {
-                        out[t] = p;
+                        out[t] = d.lo + p;
                     }
                 };
                 int t = t0;
@@ -340,7 +337,7 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                             obuf = lane == (t & 31) ? d.lo + p : obuf;
                             if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
                         } else if (lane == 0) {
-                            out[t] = p;
+                            out[t] = d.lo + p;
                         }
                     }
                 } else if (kl + kr <= 31) {
@@ -396,7 +393,7 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                             obuf = lane == (t & 31) ? d.lo + p : obuf;
                             if ((t & 31) == 31) out[(t & ~31) + lane] = obuf;
                         } else if (lane == 0) {
-                            out[t] = p;
+                            out[t] = d.lo + p;
                         }
                     }
                 } else {
@@ -404,10 +401,6 @@ __global__ void __launch_bounds__(256) afps_win_kernel(const LaunchArgs a) {
                     for (; t < c; ++t) round_any(t, max(p - kl, 0), min(p + kr, n - 1));
                 }
                 if (ROWS && lane <= ((c - 1) & 31)) out[((c - 1) & ~31) + lane] = obuf;
-                if (!ROWS && d.lo != 0) {  // the sector's offset, once per item
-                    __syncwarp();  // lane 0's stores before the other lanes' loads
-                    for (int tt = lane; tt < c; tt += 32) out[tt] += d.lo;
-                }
             }
         }
         item = a.counter ? dev::queue_next(a, nwarps, lane) : item + nwarps;
